@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""BDDC-PCG on one GB300: time to rtol 1e-8 and M^-1 applies/s, mixed vs FP64.
+
+Workload: 3D Q1 heterogeneous diffusion, 96^3 elements on the unit cube,
+12^3 cube subdomains of 8^3 elements, sigma = exp(N(0,1)) per element,
+corner + edge + face constraints, f ~ U[-1,1] per node, one right-hand side
+(synthetic, seeded). One step = one whole BDDC-PCG solve to rtol 1e-8 (all
+hot-path phases: restriction, local and interior solves, coarse residual,
+coarse solve, prolongation, SpMV, dot products), inputs resident in HBM.
+
+`value` is solves per second of the headline mixed form (bf16 local and
+interior operators with float32 accumulation inside flexible PCG; everything
+else float64). The FP64 form and the FP32 form are timed beside it.
+
+`--impl reference` times the CPU oracle (the plain NumPy/SciPy definitions
+of the paper's Sec. 2) on a bounded sample of the same workload: the same
+shape of problem on 32^3 elements with 4^3 subdomains of 8^3 (1/27 of the
+subdomains), its solve time scaled by 27.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDDC-PCG time to rtol 1e-8 & M^-1 applies/s, mixed vs FP64, 1 GB300"
+WORKLOAD = "3d_q1_96cubed_12cubed_subdomains_lognormal_sigma_1rhs"
+RTOL = 1e-8
+SAMPLE_NE, SAMPLE_NSUB, SAMPLE_SCALE = 32, 4, 27
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_solve_time(reps: int = 1):
+    """Oracle (CPU) PCG solve on the 1/27 sample; returns seconds per solve."""
+    import synth
+    from oracle import Oracle
+    p = synth.make_problem(3, SAMPLE_NE, SAMPLE_NSUB, "lognormal", k=2)
+    o = Oracle(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub)
+    b = o.rhs(p.f[:, 0])
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        _, h = o.pcg(b, RTOL)
+        times.append(time.perf_counter() - t0)
+    return times, h[0]["iters"]
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import synth  # noqa: F401
+    t_all, iters = oracle_solve_time(args.warmup + args.steps)
+    t = t_all[args.warmup:]
+    per_solve = SAMPLE_SCALE * float(np.mean(t))
+    value = 1.0 / per_solve
+    cores = os.cpu_count()
+    sample = (f"oracle PCG solve of the same problem family on {SAMPLE_NE}^3 elements with {SAMPLE_NSUB}^3 "
+              f"subdomains of 8^3 (1/{SAMPLE_SCALE} of the workload's subdomains, {iters} iterations), "
+              f"time x {SAMPLE_SCALE}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1/27 scaled"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2410_14786_gb300 import BDDC, build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    build.build()
+
+    p = synth.config(2)
+    f = torch.from_numpy(np.ascontiguousarray(p.f[:, 0])).cuda()
+    forms = {}
+    handles = {}
+    precs = ["fp64", "fp32", "bf16"] if not args.only else [args.only]
+    headline = args.precision if args.precision in precs else precs[-1]
+    for prec in precs:
+        g = BDDC.from_problem(p, precision=prec, nrhs_max=1)
+        handles[prec] = g
+        forms[prec] = {"setup_s": g.info()["setup_seconds"]}
+    g64 = handles.get("fp64", handles[headline])
+    b = g64.rhs(f)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    x_ref = None
+    for prec in precs:
+        g = handles[prec]
+        x = torch.empty_like(b)
+        for _ in range(args.warmup):
+            g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+        barrier()
+        launches0 = g.info()["kernel_launches"]
+        sampler = ClockSampler(local) if prec == headline and rank == 0 else None
+        if sampler:
+            sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            _, res = g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+            iters.append(int(res.iters[0]))
+        e1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1) / args.steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        launches = g.info()["kernel_launches"] - launches0
+        tr = float(((b - g64.matvec(x)).norm() / b.norm()).item())
+        forms[prec].update({"ms_per_solve": ms, "iters": iters[-1], "true_relres": tr,
+                            "launches_per_solve": launches / args.steps})
+        if prec == "fp64":
+            x_ref = x.clone()
+        elif x_ref is not None:
+            forms[prec]["rel_diff_vs_fp64"] = float(((x - x_ref).norm() / x_ref.norm()).item())
+        if clocks is not None:
+            forms[prec]["clocks"] = clocks
+        # standalone apply throughput (inputs larger than L2: operators >= 1 GB)
+        r = torch.rand_like(b)
+        z = torch.empty_like(b)
+        for _ in range(3):
+            g.apply(r, z)
+        n_ap = 20
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n_ap):
+            g.apply(r, z)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1) / n_ap
+        inf = g.info()
+        forms[prec]["apply_ms"] = ams
+        forms[prec]["applies_per_s"] = 1e3 / ams
+        forms[prec]["apply_GBps"] = inf["apply_bytes_1rhs"] / (ams * 1e-3) / 1e9
+        prof = g.profile_apply(r, reps=10)
+        forms[prec]["apply_launch_ms"] = prof
+        forms[prec]["operator_bytes"] = inf["operator_bytes"]
+
+    head = forms[headline]
+    g = handles[headline]
+    inf = g.info()
+    peak, peak_kind = _peaks()
+    prof = head["apply_launch_ms"]
+    op_ms = prof["interior_op"] + prof["interface_op"] + prof["interior_op_final"]
+    op_bytes = (2 * inf["interior_op_bytes"] + inf["interface_op_bytes"]
+                + 8 * 2 * (2 * inf["n_interior"] + inf["n_interface_copies"]))
+    achieved = op_bytes / (op_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_bgemv (3 launches per apply)", "peak_kind": peak_kind,
+                "bytes_per_apply": op_bytes}
+
+    # end to end through the public API with host buffers (pinned)
+    bh = torch.empty(b.numel(), dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.empty_like(bh)
+    bn, xn = bh.numpy(), xh.numpy()
+    for _ in range(2):
+        g.pcg_solve_host(bn, rtol=RTOL, out=xn)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.pcg_solve_host(bn, rtol=RTOL, out=xn)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, it_o = oracle_solve_time(1)
+        per = SAMPLE_SCALE * times[0]
+        cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one oracle PCG solve on {SAMPLE_NE}^3 elements / {SAMPLE_NSUB}^3 subdomains of 8^3 "
+                         f"({it_o} iterations), x {SAMPLE_SCALE} for the 12^3-subdomain workload"}
+
+    ms = head["ms_per_solve"]
+    line = {
+        "metric": METRIC, "value": ws * 1e3 / ms, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+" + headline if headline != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": "96^3", "subdomains": "12^3 of 8^3", "nrhs": 1,
+                   "rtol": RTOL, "mixed_form": headline, "l2": "inputs larger than L2 (operators >= 1 GB)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(b.numel() * 8),
+                "d2h_bytes_per_step": int(b.numel() * 8)},
+        "gpu_launches": int(head["launches_per_solve"] * args.steps),
+        "clocks": head.get("clocks"),
+        "forms": forms,
+        "time_to_rtol_ms": {k: v["ms_per_solve"] for k, v in forms.items()},
+        "applies_per_s": {k: v["applies_per_s"] for k, v in forms.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    for gg in handles.values():
+        gg.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--only", default=None, choices=[None, "fp64", "fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

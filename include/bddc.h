@@ -1,0 +1,200 @@
+/*
+ * bddc.h — C ABI of libbddc: BDDC-preconditioned conjugate gradients for Q1
+ * finite-element diffusion problems on a subdomain decomposition, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Goebel, Cojean, Anzt, "BDDC preconditioning on GPUs for Cardiac
+ * Simulations" (arXiv 2410.14786), Sec. 2:
+ *   A = sum_i R_i^T A_i R_i                          (subassembly)
+ *   [A_i C_i^T; C_i 0][Phi_i; Lambda_i] = [0; I]      (Eq. saddlepoint)
+ *   A_c = sum_i R_ci^T Phi_i^T A_i Phi_i R_ci
+ *   r_c = sum_i R_ci^T Phi_i^T W_i R_i r
+ *   v1  = sum_i R_i^T W_i Phi_i R_ci A_c^-1 r_c        (Eq. coarsegrid)
+ *   [A_i C_i^T; C_i 0][z_i; lambda_i] = [W_i R_i r; 0] (Eq. compzi)
+ *   v2  = sum_i R_i^T W_i z_i                          (Eq. localsubdomain)
+ *   r1  = r - A (v1 + v2)
+ *   v3  = sum_i R_i^T R_Ii^T (R_Ii A_i R_Ii^T)^-1 R_Ii R_i r1   (Eq. inner)
+ *   M^-1 r = v1 + v2 + v3
+ * with corner values and edge / face averages as constraints C_i and weights
+ * W_i = diag(1 / kappa), kappa = number of subdomains sharing a dof (Sec. 2).
+ *
+ * Problem: -div(sigma grad u) = f on the unit square (dim 2) or cube (dim 3),
+ * ne elements per direction, Q1 elements, one conductivity per element,
+ * homogeneous Dirichlet conditions on the whole boundary (those nodes are
+ * eliminated). The library takes the problem unassembled (elements and
+ * their subdomain ids), because the local Neumann matrices A_i cannot be
+ * recovered from an assembled A.
+ *
+ * Numbering: node (ix, iy[, iz]) is ix + (ne+1) * (iy + (ne+1) * iz);
+ * element (ex, ey[, ez]) is ex + ne * (ey + ne * ez).
+ *
+ * Vectors: every vector argument is an array of n_nodes * nrhs doubles,
+ * node-major with the right-hand side index fastest (entry (node, k) at
+ * node * nrhs + k). Entries at Dirichlet nodes are ignored on input and
+ * written as 0 on output. Unless stated otherwise vectors are DEVICE
+ * pointers owned by the caller; they must not alias each other.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream). Calls on one handle are not re-entrant: do not run two
+ * calls on the same handle concurrently, on any streams.
+ *
+ * Errors: every int-returning call returns BDDC_OK (0) on success, a
+ * negative BDDC_ERR_* code on failure, or BDDC_NOT_CONVERGED (positive) from
+ * bddc_pcg_solve. bddc_strerror() gives a message; bddc_last_error() gives
+ * the detail of the most recent failure on the calling thread.
+ */
+#ifndef BDDC_H
+#define BDDC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BDDC_OK               0
+#define BDDC_NOT_CONVERGED    1   /* maxit reached before rtol (solve only) */
+#define BDDC_ERR_INVALID_ARG (-1) /* bad argument: sizes, ids, sigma <= 0, NaN */
+#define BDDC_ERR_OOM         (-2) /* device or host allocation failed */
+#define BDDC_ERR_CUDA        (-3) /* a CUDA runtime call failed */
+#define BDDC_ERR_SINGULAR    (-4) /* non-positive pivot in a setup factorisation */
+#define BDDC_ERR_TIMEOUT     (-5) /* a bounded device wait ran out */
+#define BDDC_ERR_BREAKDOWN   (-6) /* PCG breakdown: p^T A p <= 0 or non-finite */
+#define BDDC_ERR_NO_DEVICE   (-7) /* no CUDA device, or not an sm_103 device */
+
+/* ---- options ---------------------------------------------------------- */
+/* Precision of the batched local and interior operators (the explicit
+ * local constrained-Neumann and interior-Dirichlet operators). Everything
+ * else (outer PCG vectors, dot products, SpMV, setup factorisations, Phi_i,
+ * the coarse solve) is float64 in every mode. FP64 runs standard PCG; the
+ * other modes run flexible PCG. */
+#define BDDC_PREC_FP64  0
+#define BDDC_PREC_FP32  1   /* float32 operators, float32 accumulation */
+#define BDDC_PREC_BF16  2   /* bfloat16 operators, float32 accumulation */
+
+/* Constraint families that become coarse (primal) dofs (Sec. 2). */
+#define BDDC_CORNERS 1u
+#define BDDC_EDGES   2u
+#define BDDC_FACES   4u
+
+typedef struct bddc_handle_s *bddc_handle_t;
+
+typedef struct {
+    int32_t dim;                    /* 2 or 3 */
+    int32_t ne;                     /* elements per direction, >= 1 */
+    const double *elem_sigma;       /* [ne^dim] HOST, finite, > 0 */
+    const int32_t *elem_subdomain;  /* [ne^dim] HOST, each in [0, n_sub) */
+    int32_t n_sub;                  /* number of subdomains, each non-empty */
+} bddc_problem_t;
+
+typedef struct {
+    int32_t precision;     /* BDDC_PREC_* */
+    uint32_t constraints;  /* BDDC_CORNERS | BDDC_EDGES | BDDC_FACES; 0 = all */
+    int32_t nrhs_max;      /* largest nrhs any later call uses, 1..64 */
+    int32_t n_threads;     /* host threads for setup; 0 = all cores */
+    int32_t device;        /* CUDA device ordinal */
+} bddc_options_t;
+
+typedef struct {
+    int64_t n_nodes, n_free, n_interior, n_interface_nodes;
+    int64_t n_sub, n_c;                 /* subdomains, coarse dofs (globs) */
+    int64_t n_corners, n_edges, n_faces;
+    int64_t sum_ni, sum_nI2, sum_nG2;   /* sum n_i, sum n_I^2, sum n_Gamma^2 */
+    int64_t sum_nG_nc;                  /* sum n_Gamma * n_ci */
+    int64_t max_ni;
+    int64_t operator_bytes;             /* device bytes of the local / interior operators */
+    int64_t coarse_bytes;               /* device bytes of the coarse operator */
+    int64_t device_bytes;               /* all device memory the handle holds */
+    int64_t apply_bytes_1rhs;           /* algorithmic HBM bytes of one apply, nrhs = 1 */
+    int64_t interior_op_bytes;          /* bytes of all A_II^-1 blocks as stored */
+    int64_t interface_op_bytes;         /* bytes of all K_GG blocks as stored */
+    int64_t n_interface_copies;         /* sum over subdomains of interface nodes */
+    int64_t kernel_launches;            /* kernels launched by this handle so far */
+    double setup_seconds;               /* wall time of bddc_setup */
+    int32_t precision;
+    int32_t error_subdomain;            /* subdomain of the last SINGULAR error, else -1 */
+} bddc_info_t;
+
+/* Build the preconditioner (all factorisations in float64 on the host,
+ * operators uploaded once to the device). Copies what it needs from
+ * `problem`; the caller keeps ownership of every input. On success *out
+ * holds a new handle (free it with bddc_destroy); on failure *out is NULL.
+ * Errors: INVALID_ARG, SINGULAR (bddc_last_error() names the subdomain),
+ * OOM, CUDA, NO_DEVICE. */
+int bddc_setup(const bddc_problem_t *problem, const bddc_options_t *options,
+               bddc_handle_t *out);
+
+/* z = M^-1 r (Sec. 2: v1 + v2 + v3) for nrhs columns, 1 <= nrhs <=
+ * nrhs_max. r and z are device vectors. Asynchronous on `stream`; allocates
+ * nothing. */
+int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *stream);
+
+/* y = A x (the global stiffness matrix on the free nodes; Dirichlet entries
+ * of y are written 0). Device vectors; asynchronous on `stream`. */
+int bddc_matvec(bddc_handle_t h, const double *x, double *y, int32_t nrhs, void *stream);
+
+/* b = M f restricted to the free nodes: the load vector of the nodal values
+ * f (Q1 interpolant, consistent mass matrix). f holds values at ALL nodes
+ * (Dirichlet ones included). Device vectors; asynchronous on `stream`. */
+int bddc_rhs(bddc_handle_t h, const double *f, double *b, int32_t nrhs, void *stream);
+
+/* Solve A x = b by PCG with M^-1 from the start x0 = P_I b (the interior
+ * correction of b), independently per column, until ||r_k||_2 <= rtol *
+ * ||b||_2 on the updated residual. b, x: device vectors. iters[nrhs] and
+ * relres[nrhs] are HOST arrays (may be NULL) receiving the iteration count
+ * and ||r||/||b|| of each column. Synchronises `stream`. Returns OK,
+ * NOT_CONVERGED or BREAKDOWN. */
+int bddc_pcg_solve(bddc_handle_t h, const double *b, double *x, int32_t nrhs,
+                   double rtol, int32_t maxit, int32_t *iters, double *relres,
+                   void *stream);
+
+/* Same as bddc_pcg_solve with b and x in HOST memory: copies b in, solves
+ * and copies x out inside the call (staging through device buffers the
+ * handle owns). */
+int bddc_pcg_solve_host(bddc_handle_t h, const double *b_host, double *x_host,
+                        int32_t nrhs, double rtol, int32_t maxit, int32_t *iters,
+                        double *relres, void *stream);
+
+/* Copy the coarse residual r_c and the coarse solution u_c = A_c^-1 r_c of
+ * the most recent bddc_apply (n_c * nrhs doubles each, coarse dof major,
+ * coarse dofs ordered by their smallest node id) into device arrays rc / uc
+ * (either may be NULL). Asynchronous on `stream`. */
+int bddc_coarse_vectors(bddc_handle_t h, double *rc, double *uc, int32_t nrhs, void *stream);
+
+/* Sizes, byte counts and timings of a handle. */
+int bddc_query(bddc_handle_t h, bddc_info_t *info);
+
+/* Device time (milliseconds, CUDA events, mean over `reps` applies of the
+ * device vector r on `stream`) of each launch of one apply: out_ms[0..8] =
+ * restriction, interior operator (t_I = A_II^-1 r_I), condensed interface
+ * right-hand side, interface operator (z_G = K_GG y'_G), coarse residual,
+ * coarse solve, prolongation, interior right-hand side, interior operator
+ * (final). For profiling only; z receives M^-1 r. */
+int bddc_profile_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs,
+                       int32_t reps, double *out_ms, void *stream);
+
+/* Host-only run of the setup, for inspection and tests: needs no device.
+ * With numerics = 0 only the topology runs (subdomain node sets, kappa,
+ * globs); otherwise also the float64 local factorisations and the coarse
+ * assembly. Fills the size fields of *info (may be NULL) and, if numerics
+ * and Ac is not NULL, writes the assembled coarse matrix A_c = sum_i
+ * R_ci^T A_ci R_ci (n_c x n_c, row-major, coarse dofs ordered by their
+ * smallest node id) when n_c * n_c <= Ac_capacity, else returns
+ * INVALID_ARG. Same argument checks and errors as bddc_setup. */
+int bddc_setup_inspect(const bddc_problem_t *problem, const bddc_options_t *options,
+                       int32_t numerics, bddc_info_t *info, double *Ac, int64_t Ac_capacity);
+
+/* Free the handle and all device memory it holds. NULL is allowed. */
+void bddc_destroy(bddc_handle_t h);
+
+/* Static message for a status code. */
+const char *bddc_strerror(int status);
+
+/* Detail of the most recent failure on the calling thread ("" if none). */
+const char *bddc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BDDC_H */

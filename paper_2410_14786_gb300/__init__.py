@@ -1,0 +1,154 @@
+"""BDDC-preconditioned CG on one GB300 (sm_103a): Python binding of libbddc.
+
+Every step of the preconditioner and of PCG runs in the library's CUDA
+kernels; this module only marshals arguments (PyTorch tensors for device
+memory and the current CUDA stream, NumPy arrays for host inputs). Method:
+Goebel, Cojean, Anzt, "BDDC preconditioning on GPUs for Cardiac
+Simulations", arXiv 2410.14786, Sec. 2.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64,  # noqa: F401
+                   BDDCError)
+
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16}
+
+
+@dataclass
+class SolveResult:
+    iters: np.ndarray
+    relres: np.ndarray
+    status: int
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, nrhs_expected=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous (node-major, right-hand side fastest)")
+    return C.c_void_p(t.data_ptr())
+
+
+class BDDC:
+    """A BDDC preconditioner for one decomposed Q1 diffusion problem.
+
+    Parameters mirror `bddc_problem_t` / `bddc_options_t`: dim, ne,
+    elem_sigma [ne^dim] float64 > 0, elem_subdomain [ne^dim] int32,
+    n_sub; precision in {"fp64", "fp32", "bf16"}; constraints bitmask of
+    CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup.
+    """
+
+    def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
+                 constraints=0, nrhs_max=1, n_threads=0, device=None):
+        import torch
+        self._L = _lib.lib()
+        self.handle = C.c_void_p()
+        sig = np.ascontiguousarray(elem_sigma, dtype=np.float64)
+        part = np.ascontiguousarray(elem_subdomain, dtype=np.int32)
+        if device is None:
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+        prob = _lib.Problem(int(dim), int(ne), sig.ctypes.data_as(C.POINTER(C.c_double)),
+                            part.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub))
+        opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                            int(constraints), int(nrhs_max), int(n_threads), int(device))
+        _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
+        self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
+        self.n_nodes = (self.ne + 1) ** self.dim
+        self.precision = precision
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        return cls(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self._L.bddc_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = _lib.Info()
+        _lib.check(self._L.bddc_query(self.handle, C.byref(inf)))
+        return {n: getattr(inf, n) for n, _ in _lib.Info._fields_}
+
+    def _nrhs(self, t):
+        return 1 if t.dim() == 1 else int(t.shape[1])
+
+    def empty(self, nrhs=1):
+        import torch
+        shape = (self.n_nodes,) if nrhs == 1 else (self.n_nodes, nrhs)
+        return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+    def apply(self, r, out=None, stream=None):
+        """z = M^-1 r (device tensors [n_nodes] or [n_nodes, nrhs])."""
+        z = out if out is not None else self.empty(self._nrhs(r))
+        _lib.check(self._L.bddc_apply(self.handle, _dev_ptr(r), _dev_ptr(z), self._nrhs(r), _stream_ptr(stream)))
+        return z
+
+    def matvec(self, x, out=None, stream=None):
+        y = out if out is not None else self.empty(self._nrhs(x))
+        _lib.check(self._L.bddc_matvec(self.handle, _dev_ptr(x), _dev_ptr(y), self._nrhs(x), _stream_ptr(stream)))
+        return y
+
+    def rhs(self, f, out=None, stream=None):
+        b = out if out is not None else self.empty(self._nrhs(f))
+        _lib.check(self._L.bddc_rhs(self.handle, _dev_ptr(f), _dev_ptr(b), self._nrhs(f), _stream_ptr(stream)))
+        return b
+
+    def coarse_vectors(self, nrhs=1, stream=None):
+        import torch
+        n_c = self.info()["n_c"]
+        rc = torch.zeros((n_c, nrhs), dtype=torch.float64, device="cuda")
+        uc = torch.zeros_like(rc)
+        _lib.check(self._L.bddc_coarse_vectors(self.handle, _dev_ptr(rc), _dev_ptr(uc), nrhs, _stream_ptr(stream)))
+        return rc, uc
+
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=1000, stream=None) -> tuple:
+        """Solve A x = b; returns (x, SolveResult). Device tensors."""
+        nrhs = self._nrhs(b)
+        x = x if x is not None else self.empty(nrhs)
+        iters = (C.c_int32 * nrhs)()
+        rel = (C.c_double * nrhs)()
+        st = self._L.bddc_pcg_solve(self.handle, _dev_ptr(b), _dev_ptr(x), nrhs, float(rtol), int(maxit),
+                                    iters, rel, _stream_ptr(stream))
+        _lib.check(st, allow=(_lib.OK, _lib.NOT_CONVERGED))
+        return x, SolveResult(np.array(iters[:]), np.array(rel[:]), st)
+
+    def pcg_solve_host(self, b: np.ndarray, rtol=1e-8, maxit=1000, out: np.ndarray | None = None, stream=None):
+        """Same with host (NumPy, ideally pinned) buffers; copies inside the call."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        x = out if out is not None else np.empty_like(b)
+        iters = (C.c_int32 * nrhs)()
+        rel = (C.c_double * nrhs)()
+        st = self._L.bddc_pcg_solve_host(self.handle, C.c_void_p(b.ctypes.data), C.c_void_p(x.ctypes.data), nrhs,
+                                         float(rtol), int(maxit), iters, rel, _stream_ptr(stream))
+        _lib.check(st, allow=(_lib.OK, _lib.NOT_CONVERGED))
+        return x, SolveResult(np.array(iters[:]), np.array(rel[:]), st)
+
+    def profile_apply(self, r, reps=5, stream=None):
+        z = self.empty(self._nrhs(r))
+        out = (C.c_double * 9)()
+        _lib.check(self._L.bddc_profile_apply(self.handle, _dev_ptr(r), _dev_ptr(z), self._nrhs(r), int(reps), out,
+                                              _stream_ptr(stream)))
+        names = ["restrict", "interior_op", "iface_rhs", "interface_op", "coarse_residual", "coarse_solve",
+                 "prolong", "interior_rhs", "interior_op_final"]
+        return dict(zip(names, out[:]))

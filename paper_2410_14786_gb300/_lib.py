@@ -1,0 +1,103 @@
+"""ctypes declarations for libbddc.so (the C ABI in include/bddc.h).
+
+The shared library is built in-tree by `paper_2410_14786_gb300.build`. This
+module raises on import failure: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbddc.so")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_SINGULAR = -4
+ERR_TIMEOUT = -5
+ERR_BREAKDOWN = -6
+ERR_NO_DEVICE = -7
+
+PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+CORNERS, EDGES, FACES = 1, 2, 4
+
+EXPORTED = [
+    "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
+    "bddc_pcg_solve_host", "bddc_coarse_vectors", "bddc_query", "bddc_profile_apply",
+    "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_setup_inspect",
+]
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("ne", C.c_int32), ("elem_sigma", C.POINTER(C.c_double)),
+                ("elem_subdomain", C.POINTER(C.c_int32)), ("n_sub", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
+                ("n_threads", C.c_int32), ("device", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "n_nodes", "n_free", "n_interior", "n_interface_nodes", "n_sub", "n_c",
+        "n_corners", "n_edges", "n_faces", "sum_ni", "sum_nI2", "sum_nG2", "sum_nG_nc",
+        "max_ni", "operator_bytes", "coarse_bytes", "device_bytes", "apply_bytes_1rhs",
+        "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches")] + [
+        ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32)]
+
+
+class BDDCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libbddc status {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libbddc.so not built at {path}; run paper_2410_14786_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, dbl = C.c_void_p, C.c_int32, C.c_double
+    pi32, pdbl = C.POINTER(C.c_int32), C.POINTER(C.c_double)
+    sig = {
+        "bddc_setup": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), C.POINTER(vp)]),
+        "bddc_apply": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_matvec": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_rhs": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_pcg_solve": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
+        "bddc_pcg_solve_host": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
+        "bddc_coarse_vectors": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_query": (C.c_int, [vp, C.POINTER(Info)]),
+        "bddc_profile_apply": (C.c_int, [vp, vp, vp, i32, i32, pdbl, vp]),
+        "bddc_setup_inspect": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), i32, C.POINTER(Info), pdbl,
+                                         C.c_int64]),
+        "bddc_destroy": (None, [vp]),
+        "bddc_strerror": (C.c_char_p, [C.c_int]),
+        "bddc_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def check(code: int, allow=(OK,)) -> int:
+    if code in allow:
+        return code
+    L = lib()
+    detail = L.bddc_last_error().decode() or L.bddc_strerror(code).decode()
+    raise BDDCError(code, detail)

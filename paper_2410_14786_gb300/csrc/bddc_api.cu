@@ -1,0 +1,595 @@
+// C ABI of libbddc: setup upload, apply, matvec, PCG driver.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+#include "internal.hpp"
+#include "kernels.cuh"
+
+using namespace bddc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? BDDC_ERR_OOM : BDDC_ERR_CUDA,               \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(bddc_handle_s* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e == cudaSuccess) {
+    h->allocations.push_back(v);
+    *p = static_cast<T*>(v);
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(bddc_handle_s* h, T** p, const std::vector<T>& v) {
+  cudaError_t e = dev_alloc(h, p, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+int elem_bytes(int precision) {
+  return precision == BDDC_PREC_FP64 ? 8 : precision == BDDC_PREC_FP32 ? 4 : 2;
+}
+
+// leading dimension padded so that every row starts on a 16-byte boundary
+int32_t padded_ld(int n, int eb) {
+  const int v = 16 / eb;
+  return (int32_t)((n + v - 1) / v * v);
+}
+
+// Pack per-subdomain dense operators (float64 on the host) into one arena
+// of the target precision; block starts aligned to 256 bytes.
+template <typename T>
+std::vector<T> pack_arena(const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
+                          std::vector<int64_t>& off, std::vector<int32_t>& ld, T (*cvt)(double)) {
+  const int eb = (int)sizeof(T);
+  const int64_t align = 256 / eb;
+  off.assign(ops.size(), 0);
+  ld.assign(ops.size(), 0);
+  int64_t cur = 0;
+  for (size_t s = 0; s < ops.size(); ++s) {
+    cur = (cur + align - 1) / align * align;
+    off[s] = cur;
+    ld[s] = padded_ld(dims[s], eb);
+    cur += (int64_t)dims[s] * ld[s];
+  }
+  std::vector<T> out((size_t)std::max<int64_t>(cur, 1), cvt(0.0));
+  for (size_t s = 0; s < ops.size(); ++s) {
+    const int n = dims[s];
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) out[off[s] + (int64_t)r * ld[s] + c] = cvt(ops[s][(size_t)r * n + c]);
+  }
+  return out;
+}
+
+double cvt_d(double v) { return v; }
+float cvt_f(double v) { return (float)v; }
+__nv_bfloat16 cvt_b(double v) { return __float2bfloat16_rn((float)v); }
+
+// Row tiles of square operators: (offset, ld, n, x/y offset) per subdomain.
+std::vector<WorkItem> make_items(const std::vector<int64_t>& off, const std::vector<int32_t>& ld,
+                                 const std::vector<int>& dims, const std::vector<int32_t>& voff, int tile) {
+  std::vector<WorkItem> items;
+  for (size_t s = 0; s < dims.size(); ++s)
+    for (int r0 = 0; r0 < dims[s]; r0 += tile)
+      items.push_back(WorkItem{off[s], ld[s], dims[s], r0, std::min(tile, dims[s] - r0), voff[s], voff[s]});
+  // largest operators first: long tiles start early
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem& a, const WorkItem& b) { return a.ncols > b.ncols; });
+  return items;
+}
+
+int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
+  const int S = hs.n_sub;
+  // ---- compact layouts --------------------------------------------------------
+  std::vector<int32_t> ioff(S + 1, 0), goff(S + 1, 0), coff(S + 1, 0);
+  for (int s = 0; s < S; ++s) {
+    ioff[s + 1] = ioff[s] + (int32_t)hs.sub_I[s].size();
+    goff[s + 1] = goff[s] + (int32_t)hs.sub_G[s].size();
+    coff[s + 1] = coff[s] + (int32_t)hs.sub_globs[s].size();
+  }
+  h->nI_tot = ioff[S]; h->nG_tot = goff[S]; h->nC_tot = coff[S]; h->n_c = hs.n_c;
+  h->n_dir = (int64_t)hs.dir_nodes.size();
+  std::vector<int32_t> inode(h->nI_tot), gnode(h->nG_tot), csub(h->nC_tot), ccdof(h->nC_tot), gsub(h->nG_tot);
+  std::vector<double> gw(h->nG_tot);
+  for (int s = 0; s < S; ++s) {
+    std::copy(hs.sub_I[s].begin(), hs.sub_I[s].end(), inode.begin() + ioff[s]);
+    for (size_t l = 0; l < hs.sub_G[s].size(); ++l) {
+      gnode[goff[s] + l] = hs.sub_G[s][l];
+      gw[goff[s] + l] = 1.0 / hs.kappa[hs.sub_G[s][l]];
+      gsub[goff[s] + l] = s;
+    }
+    for (size_t r = 0; r < hs.sub_globs[s].size(); ++r) {
+      csub[coff[s] + r] = s;
+      ccdof[coff[s] + r] = hs.sub_globs[s][r];
+    }
+  }
+  // A_GI with global compact interior columns; A_IG with node-id columns
+  std::vector<int32_t> agi_ptr(h->nG_tot + 1, 0), agi_col, aig_ptr(h->nI_tot + 1, 0), aig_col;
+  std::vector<double> agi_val, aig_val;
+  for (int s = 0; s < S; ++s) {
+    const int nG = (int)hs.sub_G[s].size(), nI = (int)hs.sub_I[s].size();
+    for (int r = 0; r < nG; ++r) {
+      for (int j = hs.agi_ptr[s][r]; j < hs.agi_ptr[s][r + 1]; ++j) {
+        agi_col.push_back(ioff[s] + hs.agi_col[s][j]);
+        agi_val.push_back(hs.agi_val[s][j]);
+      }
+      agi_ptr[goff[s] + r + 1] = (int32_t)agi_col.size();
+    }
+    for (int r = 0; r < nI; ++r) {
+      for (int j = hs.aig_ptr[s][r]; j < hs.aig_ptr[s][r + 1]; ++j) {
+        aig_col.push_back(hs.sub_G[s][hs.aig_col[s][j]]);
+        aig_val.push_back(hs.aig_val[s][j]);
+      }
+      aig_ptr[ioff[s] + r + 1] = (int32_t)aig_col.size();
+    }
+  }
+  // Phi_G (copy rows) and Phi_G^T (constraint rows), float64
+  std::vector<double> phi, phit;
+  std::vector<int64_t> phit_off(S, 0), gcopy_phirow(h->nG_tot, 0);
+  for (int s = 0; s < S; ++s) {
+    const int nG = (int)hs.sub_G[s].size(), nc = (int)hs.sub_globs[s].size();
+    const int64_t po = (int64_t)phi.size();
+    phit_off[s] = (int64_t)phit.size();
+    for (int l = 0; l < nG; ++l) {
+      gcopy_phirow[goff[s] + l] = po + (int64_t)l * nc;
+      for (int c = 0; c < nc; ++c) phi.push_back(hs.Phi[s][(size_t)l * nc + c]);
+    }
+    for (int c = 0; c < nc; ++c)
+      for (int l = 0; l < nG; ++l) phit.push_back(hs.Phi[s][(size_t)l * nc + c]);
+  }
+  // coarse gather map: coarse dof -> local constraint positions
+  std::vector<int32_t> cg_ptr(hs.n_c + 1, 0), cg_idx(h->nC_tot);
+  for (int64_t j = 0; j < h->nC_tot; ++j) cg_ptr[ccdof[j] + 1]++;
+  for (int64_t c = 0; c < hs.n_c; ++c) cg_ptr[c + 1] += cg_ptr[c];
+  {
+    std::vector<int32_t> fill(cg_ptr.begin(), cg_ptr.end() - 1);
+    for (int64_t j = 0; j < h->nC_tot; ++j) cg_idx[fill[ccdof[j]]++] = (int32_t)j;
+  }
+  // unique interface nodes and their copies
+  std::vector<int32_t> gu_node;
+  std::vector<int32_t> node2gu(hs.n_nodes, -1);
+  for (int64_t n = 0; n < hs.n_nodes; ++n)
+    if (hs.kappa[n] >= 2) { node2gu[n] = (int32_t)gu_node.size(); gu_node.push_back((int32_t)n); }
+  h->n_gu = (int64_t)gu_node.size();
+  std::vector<int32_t> gu_ptr(h->n_gu + 1, 0), gu_copy(h->nG_tot);
+  for (int64_t q = 0; q < h->nG_tot; ++q) gu_ptr[node2gu[gnode[q]] + 1]++;
+  for (int64_t u = 0; u < h->n_gu; ++u) gu_ptr[u + 1] += gu_ptr[u];
+  {
+    std::vector<int32_t> fill(gu_ptr.begin(), gu_ptr.end() - 1);
+    for (int64_t q = 0; q < h->nG_tot; ++q) gu_copy[fill[node2gu[gnode[q]]]++] = (int32_t)q;
+  }
+  // ---- operator arenas ----------------------------------------------------------
+  std::vector<int> dI(S), dG(S);
+  for (int s = 0; s < S; ++s) { dI[s] = (int)hs.sub_I[s].size(); dG[s] = (int)hs.sub_G[s].size(); }
+  std::vector<int64_t> offI, offG;
+  std::vector<int32_t> ldI, ldG;
+  const int prec = h->precision;
+  size_t arena_bytes = 0;
+  auto up_arena = [&](const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
+                      std::vector<int64_t>& off, std::vector<int32_t>& ld, void** dst) -> cudaError_t {
+    if (prec == BDDC_PREC_FP64) {
+      auto a = pack_arena<double>(ops, dims, off, ld, cvt_d);
+      arena_bytes += a.size() * sizeof(double);
+      return upload(h, reinterpret_cast<double**>(dst), a);
+    } else if (prec == BDDC_PREC_FP32) {
+      auto a = pack_arena<float>(ops, dims, off, ld, cvt_f);
+      arena_bytes += a.size() * sizeof(float);
+      return upload(h, reinterpret_cast<float**>(dst), a);
+    }
+    auto a = pack_arena<__nv_bfloat16>(ops, dims, off, ld, cvt_b);
+    arena_bytes += a.size() * sizeof(__nv_bfloat16);
+    return upload(h, reinterpret_cast<__nv_bfloat16**>(dst), a);
+  };
+  CUDA_TRY(up_arena(hs.AIIinv, dI, offI, ldI, &h->d_aii));
+  CUDA_TRY(up_arena(hs.Kgg, dG, offG, ldG, &h->d_kgg));
+  const int tile = 64;
+  auto itI = make_items(offI, ldI, dI, ioff, tile);
+  auto itG = make_items(offG, ldG, dG, goff, tile);
+  h->n_wi_I = (int)itI.size();
+  h->n_wi_G = (int)itG.size();
+  h->max_cols_I = ldI.empty() ? 0 : *std::max_element(ldI.begin(), ldI.end());
+  h->max_cols_G = ldG.empty() ? 0 : *std::max_element(ldG.begin(), ldG.end());
+  CUDA_TRY(upload(h, &h->d_wi_I, itI));
+  CUDA_TRY(upload(h, &h->d_wi_G, itG));
+  // coarse inverse, float64, rows padded
+  std::vector<WorkItem> itC;
+  if (hs.n_c) {
+    h->ldc = padded_ld((int)hs.n_c, 8);
+    std::vector<double> ac((size_t)hs.n_c * h->ldc, 0.0);
+    for (int64_t r = 0; r < hs.n_c; ++r)
+      std::memcpy(&ac[(size_t)r * h->ldc], &hs.Acinv[(size_t)r * hs.n_c], sizeof(double) * hs.n_c);
+    CUDA_TRY(upload(h, &h->d_acinv, ac));
+    const int ctile = 16;
+    for (int r0 = 0; r0 < hs.n_c; r0 += ctile)
+      itC.push_back(WorkItem{0, h->ldc, (int32_t)hs.n_c, r0, (int32_t)std::min<int64_t>(ctile, hs.n_c - r0), 0, 0});
+  }
+  h->n_wi_C = (int)itC.size();
+  CUDA_TRY(upload(h, &h->d_wi_C, itC));
+  // ---- index arrays -----------------------------------------------------------------
+  std::vector<double> sigma(P->elem_sigma, P->elem_sigma + hs.n_elems);
+  CUDA_TRY(upload(h, &h->d_sigma, sigma));
+  CUDA_TRY(upload(h, &h->d_dnode, hs.dir_nodes));
+  CUDA_TRY(upload(h, &h->d_inode, inode));
+  CUDA_TRY(upload(h, &h->d_gnode, gnode));
+  CUDA_TRY(upload(h, &h->d_gw, gw));
+  CUDA_TRY(upload(h, &h->d_agi_ptr, agi_ptr));
+  CUDA_TRY(upload(h, &h->d_agi_col, agi_col));
+  CUDA_TRY(upload(h, &h->d_agi_val, agi_val));
+  CUDA_TRY(upload(h, &h->d_aig_ptr, aig_ptr));
+  CUDA_TRY(upload(h, &h->d_aig_col, aig_col));
+  CUDA_TRY(upload(h, &h->d_aig_val, aig_val));
+  CUDA_TRY(upload(h, &h->d_phi, phi));
+  CUDA_TRY(upload(h, &h->d_phit, phit));
+  CUDA_TRY(upload(h, &h->d_sub_phit_off, phit_off));
+  CUDA_TRY(upload(h, &h->d_sub_goff, goff));
+  CUDA_TRY(upload(h, &h->d_sub_coff, coff));
+  CUDA_TRY(upload(h, &h->d_csub, csub));
+  CUDA_TRY(upload(h, &h->d_ccdof, ccdof));
+  CUDA_TRY(upload(h, &h->d_cg_ptr, cg_ptr));
+  CUDA_TRY(upload(h, &h->d_cg_idx, cg_idx));
+  CUDA_TRY(upload(h, &h->d_gu_node, gu_node));
+  CUDA_TRY(upload(h, &h->d_gu_ptr, gu_ptr));
+  CUDA_TRY(upload(h, &h->d_gu_copy, gu_copy));
+  CUDA_TRY(upload(h, &h->d_gcopy_phirow, gcopy_phirow));
+  CUDA_TRY(upload(h, &h->d_gcopy_sub, gsub));
+  // ---- workspace ---------------------------------------------------------------------
+  const int64_t R = h->nrhs_max;
+  CUDA_TRY(dev_alloc(h, &h->w_rI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_tI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_bI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_yG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_zG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_g, h->nC_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_rc, h->n_c * R));
+  CUDA_TRY(dev_alloc(h, &h->w_uc, h->n_c * R));
+  CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
+  CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
+  const int64_t NV = h->n_nodes * R;
+  CUDA_TRY(dev_alloc(h, &h->p_r, NV));
+  CUDA_TRY(dev_alloc(h, &h->p_z, NV));
+  CUDA_TRY(dev_alloc(h, &h->p_zold, NV));
+  CUDA_TRY(dev_alloc(h, &h->p_p, NV));
+  CUDA_TRY(dev_alloc(h, &h->p_q, NV));
+  CUDA_TRY(dev_alloc(h, &h->s_b, NV));
+  CUDA_TRY(dev_alloc(h, &h->s_x, NV));
+  h->n_red_blocks = kRedBlocks;
+  CUDA_TRY(dev_alloc(h, &h->d_partials, (size_t)kRedBlocks * 3 * R));
+  CUDA_TRY(dev_alloc(h, &h->d_scal, (size_t)S_COUNT * R));
+  CUDA_TRY(dev_alloc(h, &h->d_iscal, (size_t)I_COUNT * R + 2));
+  CUDA_TRY(cudaMemset(h->d_scal, 0, sizeof(double) * S_COUNT * R));
+  CUDA_TRY(cudaMemset(h->d_iscal, 0, sizeof(int32_t) * (I_COUNT * R + 2)));
+  CUDA_TRY(cudaMallocHost(&h->h_flags, sizeof(int32_t) * (I_COUNT * R + 2)));
+  // ---- info ------------------------------------------------------------------------
+  bddc_info_t& in = h->info;
+  in.n_nodes = hs.n_nodes;
+  in.n_free = hs.n_nodes - h->n_dir;
+  in.n_interior = h->nI_tot;
+  in.n_interface_nodes = h->n_gu;
+  in.n_sub = S;
+  in.n_c = hs.n_c;
+  for (int k : hs.glob_kind) {
+    if (k == BDDC_CORNERS) in.n_corners++;
+    else if (k == BDDC_EDGES) in.n_edges++;
+    else in.n_faces++;
+  }
+  for (int s = 0; s < S; ++s) {
+    const int64_t nI = dI[s], nG = dG[s], nc = (int64_t)hs.sub_globs[s].size();
+    in.sum_ni += nI + nG;
+    in.sum_nI2 += nI * nI;
+    in.sum_nG2 += nG * nG;
+    in.sum_nG_nc += nG * nc;
+    in.max_ni = std::max(in.max_ni, nI + nG);
+  }
+  in.operator_bytes = (int64_t)arena_bytes;
+  in.coarse_bytes = hs.n_c * (int64_t)h->ldc * 8;
+  const int eb = elem_bytes(prec);
+  // compulsory HBM bytes of one apply (nrhs = 1): operators as stored (A_II^-1
+  // read twice), Phi rows twice, coarse inverse once, the sparse couplings,
+  // the input r and the output z.
+  int64_t ops = 0;
+  for (int s = 0; s < S; ++s) {
+    in.interior_op_bytes += (int64_t)dI[s] * ldI[s] * eb;
+    in.interface_op_bytes += (int64_t)dG[s] * ldG[s] * eb;
+  }
+  in.n_interface_copies = h->nG_tot;
+  ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
+  in.apply_bytes_1rhs = ops + 2 * 8 * in.sum_nG_nc + in.coarse_bytes +
+                        (int64_t)(agi_val.size() + aig_val.size()) * 12 + 8 * (in.n_free + hs.n_nodes);
+  return BDDC_OK;
+}
+
+int check_handle(bddc_handle_t h, int nrhs) {
+  if (!h) return fail(BDDC_ERR_INVALID_ARG, "null handle");
+  if (nrhs < 1 || nrhs > h->nrhs_max)
+    return fail(BDDC_ERR_INVALID_ARG, "nrhs " + std::to_string(nrhs) + " outside [1, nrhs_max=" +
+                                          std::to_string(h->nrhs_max) + "]");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
+  return BDDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bddc_strerror(int status) {
+  switch (status) {
+    case BDDC_OK: return "ok";
+    case BDDC_NOT_CONVERGED: return "PCG did not reach rtol within maxit iterations";
+    case BDDC_ERR_INVALID_ARG: return "invalid argument";
+    case BDDC_ERR_OOM: return "out of memory";
+    case BDDC_ERR_CUDA: return "CUDA runtime error";
+    case BDDC_ERR_SINGULAR: return "singular local or coarse matrix in setup";
+    case BDDC_ERR_TIMEOUT: return "bounded device wait timed out";
+    case BDDC_ERR_BREAKDOWN: return "PCG breakdown (p^T A p <= 0 or non-finite)";
+    case BDDC_ERR_NO_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+const char* bddc_last_error(void) { return g_last_error.c_str(); }
+
+void bddc_destroy(bddc_handle_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  delete h;
+}
+
+int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* out) {
+  g_last_error.clear();
+  if (!P || !O || !out) return fail(BDDC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
+  {
+    std::string verr;
+    int vrc = validate_problem(P, O, verr);
+    if (vrc != BDDC_OK) return fail(vrc, verr);
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BDDC_ERR_NO_DEVICE, "no CUDA device");
+  if (O->device < 0 || O->device >= ndev) return fail(BDDC_ERR_INVALID_ARG, "device ordinal out of range");
+  CUDA_TRY(cudaSetDevice(O->device));
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, O->device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(BDDC_ERR_NO_DEVICE, std::string("device is not sm_103: ") + prop.name);
+
+  HostSetup hs;
+  std::string err;
+  int rc = host_setup(P, O, hs, err);
+  if (rc != BDDC_OK) return fail(rc, err);
+
+  bddc_handle_s* h = new (std::nothrow) bddc_handle_s();
+  if (!h) return fail(BDDC_ERR_OOM, "handle allocation");
+  h->dim = P->dim; h->ne = P->ne; h->n1 = P->ne + 1; h->n_sub = P->n_sub;
+  h->precision = O->precision; h->nrhs_max = O->nrhs_max; h->device = O->device;
+  h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
+  rc = build_device(h, hs, P);
+  if (rc != BDDC_OK) {
+    bddc_destroy(h);
+    return rc;
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    bddc_destroy(h);
+    return fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  h->info.precision = O->precision;
+  h->info.error_subdomain = -1;
+  h->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = h;
+  return BDDC_OK;
+}
+
+int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t numerics, bddc_info_t* info,
+                       double* Ac, int64_t Ac_capacity) {
+  g_last_error.clear();
+  std::string err;
+  int rc = validate_problem(P, O, err);
+  if (rc != BDDC_OK) return fail(rc, err);
+  HostSetup hs;
+  rc = host_setup(P, O, hs, err, /*invert_coarse=*/false, /*numerics=*/numerics != 0);
+  if (rc != BDDC_OK) return fail(rc, err);
+  if (info) {
+    *info = bddc_info_t{};
+    info->n_nodes = hs.n_nodes;
+    info->n_free = hs.n_nodes - (int64_t)hs.dir_nodes.size();
+    info->n_sub = hs.n_sub;
+    info->n_c = hs.n_c;
+    for (int k : hs.glob_kind) {
+      if (k == BDDC_CORNERS) info->n_corners++;
+      else if (k == BDDC_EDGES) info->n_edges++;
+      else info->n_faces++;
+    }
+    for (int s = 0; s < hs.n_sub; ++s) {
+      const int64_t nI = (int64_t)hs.sub_I[s].size(), nG = (int64_t)hs.sub_G[s].size();
+      info->n_interior += nI;
+      info->sum_ni += nI + nG;
+      info->sum_nI2 += nI * nI;
+      info->sum_nG2 += nG * nG;
+      info->sum_nG_nc += nG * (int64_t)hs.sub_globs[s].size();
+      info->max_ni = std::max(info->max_ni, nI + nG);
+    }
+    for (int64_t n = 0; n < hs.n_nodes; ++n) info->n_interface_nodes += hs.kappa[n] >= 2;
+    info->error_subdomain = -1;
+  }
+  if (Ac && numerics) {
+    if (hs.n_c * hs.n_c > Ac_capacity) return fail(BDDC_ERR_INVALID_ARG, "Ac capacity too small");
+    std::memcpy(Ac, hs.Acinv.data(), sizeof(double) * hs.n_c * hs.n_c);
+  }
+  return BDDC_OK;
+}
+
+int bddc_query(bddc_handle_t h, bddc_info_t* info) {
+  if (!h || !info) return fail(BDDC_ERR_INVALID_ARG, "null argument");
+  h->info.kernel_launches = h->launches;
+  *info = h->info;
+  return BDDC_OK;
+}
+
+int bddc_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!r || !z || r == z) return fail(BDDC_ERR_INVALID_ARG, "r and z must be distinct device pointers");
+  CUDA_TRY(launch_apply(h, r, z, nrhs, static_cast<cudaStream_t>(stream)));
+  return BDDC_OK;
+}
+
+int bddc_matvec(bddc_handle_t h, const double* x, double* y, int32_t nrhs, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!x || !y || x == y) return fail(BDDC_ERR_INVALID_ARG, "x and y must be distinct device pointers");
+  CUDA_TRY(launch_matvec(h, x, y, nrhs, static_cast<cudaStream_t>(stream)));
+  return BDDC_OK;
+}
+
+int bddc_rhs(bddc_handle_t h, const double* f, double* b, int32_t nrhs, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!f || !b || f == b) return fail(BDDC_ERR_INVALID_ARG, "f and b must be distinct device pointers");
+  CUDA_TRY(launch_rhs(h, f, b, nrhs, static_cast<cudaStream_t>(stream)));
+  return BDDC_OK;
+}
+
+int bddc_coarse_vectors(bddc_handle_t h, double* rc_out, double* uc_out, int32_t nrhs, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)h->n_c * nrhs * sizeof(double);
+  if (bytes == 0) return BDDC_OK;
+  if (rc_out) CUDA_TRY(cudaMemcpyAsync(rc_out, h->w_rc, bytes, cudaMemcpyDeviceToDevice, st));
+  if (uc_out) CUDA_TRY(cudaMemcpyAsync(uc_out, h->w_uc, bytes, cudaMemcpyDeviceToDevice, st));
+  return BDDC_OK;
+}
+
+int bddc_profile_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs, int32_t reps, double* out_ms,
+                       void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!r || !z || !out_ms || reps < 1) return fail(BDDC_ERR_INVALID_ARG, "bad profile arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[10];
+  for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+  for (int i = 0; i < 9; ++i) out_ms[i] = 0;
+  for (int rep = 0; rep < reps; ++rep) {
+    CUDA_TRY(launch_apply(h, r, z, nrhs, st, ev));
+    CUDA_TRY(cudaEventSynchronize(ev[9]));
+    float ms;
+    for (int i = 0; i < 9; ++i) {
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      out_ms[i] += ms / reps;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return BDDC_OK;
+}
+
+static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, double rtol, int maxit,
+                    int32_t* iters, double* relres, cudaStream_t st) {
+  const int flexible = h->precision != BDDC_PREC_FP64;
+  int32_t* hf = h->h_flags;
+  const int R = h->nrhs_max;
+  // x0 = P_I b ; r0 = b - A x0
+  CUDA_TRY(launch_interior_correction(h, b, x, nrhs, st));
+  CUDA_TRY(launch_matvec(h, x, h->p_q, nrhs, st));
+  CUDA_TRY(launch_residual(h, b, nrhs, st));
+  CUDA_TRY(launch_dots(h, nrhs, b, b, h->p_r, h->p_r, nullptr, nullptr, st));
+  CUDA_TRY(launch_finalize(h, FIN_INIT, nrhs, rtol, flexible, st));
+  CUDA_TRY(cudaMemcpyAsync(hf, h->d_iscal + I_COUNT * R, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  int status = BDDC_OK;
+  if (hf[0] > 0) {
+    CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
+    CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_z, nullptr, nullptr, nullptr, nullptr, st));
+    CUDA_TRY(launch_finalize(h, FIN_RHO, nrhs, rtol, flexible, st));
+    CUDA_TRY(launch_update_p(h, nrhs, st));     // beta = 0: p = z, zold = z
+    int it = 0;
+    for (; it < maxit; ++it) {
+      CUDA_TRY(launch_matvec(h, h->p_p, h->p_q, nrhs, st));
+      CUDA_TRY(launch_dots(h, nrhs, h->p_p, h->p_q, nullptr, nullptr, nullptr, nullptr, st));
+      CUDA_TRY(launch_finalize(h, FIN_ALPHA, nrhs, rtol, flexible, st));
+      CUDA_TRY(launch_update_xr(h, x, nrhs, st));
+      CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_r, nullptr, nullptr, nullptr, nullptr, st));
+      CUDA_TRY(launch_finalize(h, FIN_CONV, nrhs, rtol, flexible, st));
+      CUDA_TRY(cudaMemcpyAsync(hf, h->d_iscal + I_COUNT * R, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      if (hf[0] == 0) break;
+      CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
+      CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, nullptr, nullptr, st));
+      CUDA_TRY(launch_finalize(h, FIN_BETA, nrhs, rtol, flexible, st));
+      CUDA_TRY(launch_update_p(h, nrhs, st));
+    }
+    if (hf[0] > 0) status = BDDC_NOT_CONVERGED;
+  }
+  // per-column results
+  std::vector<int32_t> hi(I_COUNT * R + 2);
+  std::vector<double> hd(S_COUNT * R);
+  CUDA_TRY(cudaMemcpyAsync(hi.data(), h->d_iscal, hi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hd.data(), h->d_scal, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[k] = hi[I_ITERS * R + k];
+    if (relres) relres[k] = hd[S_RELRES * R + k];
+    if (hi[I_STATUS * R + k] == BDDC_ERR_BREAKDOWN) status = BDDC_ERR_BREAKDOWN;
+  }
+  if (status == BDDC_ERR_BREAKDOWN) g_last_error = "PCG breakdown in at least one column";
+  return status;
+}
+
+int bddc_pcg_solve(bddc_handle_t h, const double* b, double* x, int32_t nrhs, double rtol, int32_t maxit,
+                   int32_t* iters, double* relres, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!b || !x || b == x) return fail(BDDC_ERR_INVALID_ARG, "b and x must be distinct device pointers");
+  if (!(rtol > 0.0) || maxit < 0) return fail(BDDC_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
+  return pcg_core(h, b, x, nrhs, rtol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
+}
+
+int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, int32_t nrhs, double rtol,
+                        int32_t maxit, int32_t* iters, double* relres, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!b_host || !x_host) return fail(BDDC_ERR_INVALID_ARG, "null host vector");
+  if (!(rtol > 0.0) || maxit < 0) return fail(BDDC_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)h->n_nodes * nrhs * sizeof(double);
+  CUDA_TRY(cudaMemcpyAsync(h->s_b, b_host, bytes, cudaMemcpyHostToDevice, st));
+  int status = pcg_core(h, h->s_b, h->s_x, nrhs, rtol, maxit, iters, relres, st);
+  if (status < 0) return status;
+  CUDA_TRY(cudaMemcpyAsync(x_host, h->s_x, bytes, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return status;
+}
+
+}  // extern "C"

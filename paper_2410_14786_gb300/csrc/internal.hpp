@@ -1,0 +1,115 @@
+// Internal state of a libbddc handle (host side and device side).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bddc.h"
+
+namespace bddc {
+
+// One row tile of one dense operator in a batched GEMV launch:
+// Y[yoff + row0 + r] = sum_c Op[row0 + r, c] * X[xoff + c], r < nrows.
+struct WorkItem {
+  int64_t moff;    // element offset of the operator (row 0) in its arena
+  int32_t lda;     // leading dimension (elements), padded to 16 bytes
+  int32_t ncols;   // operator columns (= rows of the square operator)
+  int32_t row0;    // first row of this tile
+  int32_t nrows;   // rows in this tile
+  int32_t xoff;    // first entry of the operand in the compact X buffer
+  int32_t yoff;    // first entry of the result in the compact Y buffer
+};
+
+// Host-side results of the topology and numeric setup (float64).
+struct HostSetup {
+  int dim = 0, ne = 0, n1 = 0;
+  int64_t n_nodes = 0, n_elems = 0;
+  double h = 0;
+  int n_sub = 0;
+  // Dirichlet nodes and multiplicity kappa per node (0 on Dirichlet nodes)
+  std::vector<int32_t> dir_nodes;
+  std::vector<uint8_t> kappa;
+  // per subdomain: interior and interface nodes (sorted node ids)
+  std::vector<std::vector<int32_t>> sub_I, sub_G;
+  // globs: members (node ids), sharing subdomains, kind (CORNER/EDGE/FACE)
+  std::vector<std::vector<int32_t>> glob_nodes, glob_subs;
+  std::vector<int> glob_kind;
+  std::vector<std::vector<int32_t>> sub_globs;   // glob ids per subdomain, ascending
+  // per subdomain numeric results
+  std::vector<std::vector<double>> AIIinv;   // nI x nI
+  std::vector<std::vector<double>> Kgg;      // nG x nG: (1,1) block of the constrained Schur KKT inverse
+  std::vector<std::vector<double>> Phi;      // nG x nc: interface rows of Phi_i
+  std::vector<std::vector<double>> Aci;      // nc x nc
+  // sparse couplings, CSR: A_GI (rows: local interface, cols: local interior)
+  std::vector<std::vector<int32_t>> agi_ptr, agi_col, aig_ptr, aig_col;
+  std::vector<std::vector<double>> agi_val, aig_val;
+  // coarse operator
+  int64_t n_c = 0;
+  std::vector<double> Acinv;                 // n_c x n_c, dense SPD inverse
+  int error_subdomain = -1;
+};
+
+// Validate the problem and options (no device checks).
+int validate_problem(const bddc_problem_t* p, const bddc_options_t* o, std::string& err);
+// Topology and float64 numerics; with invert_coarse = false, Acinv holds A_c itself.
+int host_setup(const bddc_problem_t* p, const bddc_options_t* o, HostSetup& hs, std::string& err,
+               bool invert_coarse = true, bool numerics = true);
+
+}  // namespace bddc
+
+struct bddc_handle_s {
+  // problem
+  int dim = 0, ne = 0, n1 = 0, n_sub = 0, precision = 0, nrhs_max = 1, device = 0;
+  int64_t n_nodes = 0, n_elems = 0;
+  double h = 0;
+  // sizes
+  int64_t nI_tot = 0, nG_tot = 0, nC_tot = 0, n_c = 0, n_gu = 0, n_dir = 0;
+  bddc_info_t info{};
+  // --- device data ---------------------------------------------------
+  double* d_sigma = nullptr;          // [n_elems]
+  int32_t* d_dnode = nullptr;         // [n_dir] Dirichlet nodes
+  int32_t* d_inode = nullptr;         // [nI_tot] node of each compact interior entry
+  int32_t* d_gnode = nullptr;         // [nG_tot] node of each interface copy
+  double* d_gw = nullptr;             // [nG_tot] 1/kappa of each interface copy
+  // A_GI: rows = interface copies, cols = compact interior positions
+  int32_t* d_agi_ptr = nullptr; int32_t* d_agi_col = nullptr; double* d_agi_val = nullptr;
+  // A_IG: rows = compact interior positions, cols = node ids (interface nodes)
+  int32_t* d_aig_ptr = nullptr; int32_t* d_aig_col = nullptr; double* d_aig_val = nullptr;
+  // Phi_Gamma^T rows, per subdomain [nc x nG] (coarse residual) and
+  // Phi_Gamma rows [nG x nc] (prolongation), float64
+  double* d_phit = nullptr; double* d_phi = nullptr;
+  int64_t* d_sub_phit_off = nullptr;  // [n_sub] element offset of Phi^T block
+  int32_t* d_sub_goff = nullptr;      // [n_sub + 1] interface copy offsets
+  int32_t* d_sub_coff = nullptr;      // [n_sub + 1] local constraint offsets
+  int32_t* d_csub = nullptr;          // [nC_tot] subdomain of each local constraint
+  int32_t* d_ccdof = nullptr;         // [nC_tot] coarse dof of each local constraint
+  // coarse gather: per coarse dof, the local-constraint positions that sum into it
+  int32_t* d_cg_ptr = nullptr; int32_t* d_cg_idx = nullptr;
+  // prolongation: per unique interface node, its copies
+  int32_t* d_gu_node = nullptr; int32_t* d_gu_ptr = nullptr; int32_t* d_gu_copy = nullptr;
+  int64_t* d_gcopy_phirow = nullptr;  // [nG_tot] element offset of the copy's Phi row
+  int32_t* d_gcopy_sub = nullptr;     // [nG_tot] subdomain of the copy
+  // operators
+  void* d_aii = nullptr;              // interior inverses, precision-typed arena
+  void* d_kgg = nullptr;              // interface operators, precision-typed arena
+  double* d_acinv = nullptr;          // coarse inverse, float64, n_c x ldc
+  int32_t ldc = 0;
+  bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
+  bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
+  bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
+  int max_cols_I = 0, max_cols_G = 0;
+  // apply workspace (nrhs_max columns)
+  double *w_rI = nullptr, *w_tI = nullptr, *w_bI = nullptr;
+  double *w_yG = nullptr, *w_zG = nullptr, *w_g = nullptr, *w_rc = nullptr, *w_uc = nullptr;
+  // PCG workspace
+  double *p_r = nullptr, *p_z = nullptr, *p_zold = nullptr, *p_p = nullptr, *p_q = nullptr;
+  double *s_b = nullptr, *s_x = nullptr;   // staging for host-buffer solves
+  double* d_partials = nullptr;            // [n_red_blocks * nrhs_max * 3]
+  double* d_scal = nullptr;                // per-column PCG scalars
+  int32_t* d_iscal = nullptr;              // per-column flags / counters
+  int32_t* h_flags = nullptr;              // pinned host mirror of the global flags
+  int n_red_blocks = 0;
+  int64_t launches = 0;                    // kernels launched so far
+  std::vector<void*> allocations;
+};

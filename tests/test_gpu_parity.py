@@ -1,0 +1,224 @@
+"""GPU parity: libbddc (through its C ABI) against the CPU oracle on the same
+seeded inputs (arXiv 2410.14786, Sec. 2). FP64 to 1e-11 relative per apply
+and 1e-10 per PCG solution; low-precision forms within bounds derived from
+their unit roundoff."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import CORNER, EDGE, FACE, Oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_14786_gb300 import build
+    build.build()
+
+
+def _oracle(p, mask=0):
+    return Oracle(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub,
+                  constraints=mask or (CORNER | EDGE | FACE))
+
+
+def _bddc(p, precision="fp64", mask=0, nrhs_max=1):
+    from paper_2410_14786_gb300 import BDDC
+    return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max)
+
+
+def _small_voronoi():
+    sub, n, cell = synth.voronoi_partition(12, 8, 91)
+    s = synth.layer_sigma(12, cell)
+    f = synth.uniform(92, 13 ** 3 * 2).reshape(-1, 2)
+    return synth.Problem(3, 12, s, sub, n, f, "voronoi_12_8")
+
+
+CASES = {
+    "cfg1_2d": (lambda: synth.config(1), CORNER | EDGE),
+    "3d_24_3cubed": (lambda: synth.make_problem(3, 24, 3, "lognormal", k=21), 0),
+    "3d_voronoi": (_small_voronoi, 0),
+    "3d_corners_only": (lambda: synth.make_problem(3, 16, 2, "lognormal", k=22), CORNER),
+    "2d_single_sub": (lambda: synth.make_problem(2, 20, 1, "lognormal", k=23), 0),
+}
+_CACHE = {}
+
+
+def _case(name):
+    if name not in _CACHE:
+        make, mask = CASES[name]
+        p = make()
+        _CACHE[name] = (p, mask, _oracle(p, mask))
+    return _CACHE[name]
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matvec_and_rhs(name):
+    p, mask, o = _case(name)
+    g = _bddc(p, mask=mask, nrhs_max=3)
+    x = synth.uniform(31, o.n_nodes * 3).reshape(-1, 3)
+    y = g.matvec(_cuda(x)).cpu().numpy()
+    want = np.stack([o.matvec_nodes(np.where(o.dir, 0, x[:, k])) for k in range(3)], axis=1)
+    assert _rel(y, want) < 1e-13
+    f = synth.uniform(32, o.n_nodes * 3).reshape(-1, 3)
+    b = g.rhs(_cuda(f)).cpu().numpy()
+    assert _rel(b, o.rhs(f)) < 1e-13
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_fp64(name):
+    p, mask, o = _case(name)
+    g = _bddc(p, mask=mask)
+    r = synth.uniform(33, o.n_nodes)
+    r[o.dir] = 0
+    z = g.apply(_cuda(r)).cpu().numpy()
+    parts = o.apply_parts(o.to_free(r))
+    assert _rel(z, o.to_nodes(parts["z"])) < 1e-11
+    assert np.all(z[o.dir] == 0)
+    if o.n_c:
+        rc, uc = g.coarse_vectors()
+        assert _rel(rc.cpu().numpy()[:, 0], parts["rc"]) < 1e-11
+        assert _rel(uc.cpu().numpy()[:, 0], parts["uc"]) < 1e-11
+
+
+def test_apply_ignores_dirichlet_input_and_multi_rhs():
+    p, mask, o = _case("3d_24_3cubed")
+    g = _bddc(p, mask=mask, nrhs_max=5)
+    r = synth.uniform(34, o.n_nodes * 5).reshape(-1, 5)   # nonzero Dirichlet entries
+    z = g.apply(_cuda(r)).cpu().numpy()
+    want = o.apply_nodes(np.where(o.dir[:, None], 0, r))
+    assert _rel(z, want) < 1e-11
+    z1 = g.apply(_cuda(np.ascontiguousarray(r[:, 2]))).cpu().numpy()
+    assert _rel(z1, want[:, 2]) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["cfg1_2d", "3d_24_3cubed", "3d_voronoi"])
+def test_pcg_fp64_matches_oracle(name):
+    p, mask, o = _case(name)
+    g = _bddc(p, mask=mask)
+    b = o.rhs(p.f[:, 0])
+    xo, h = o.pcg(b, 1e-8)
+    x, res = g.pcg_solve(_cuda(b), rtol=1e-8, maxit=500)
+    x = x.cpu().numpy()
+    assert res.status == 0
+    assert int(res.iters[0]) == h[0]["iters"]
+    assert _rel(x, xo) < 1e-10
+    assert abs(res.relres[0] - h[0]["rnorm"][-1] / np.linalg.norm(o.to_free(b))) < 1e-10
+
+
+def test_pcg_multi_rhs_and_zero_column():
+    p, mask, o = _case("cfg1_2d")
+    g = _bddc(p, mask=mask, nrhs_max=3)
+    f = synth.uniform(35, o.n_nodes * 3).reshape(-1, 3)
+    b = o.rhs(f)
+    b[:, 1] = 0.0
+    xo, h = o.pcg(b, 1e-8)
+    x, res = g.pcg_solve(_cuda(b), rtol=1e-8)
+    x = x.cpu().numpy()
+    assert list(res.iters) == [hh["iters"] for hh in h]
+    assert np.all(x[:, 1] == 0)
+    assert _rel(x, xo) < 1e-10
+
+
+def test_pcg_host_buffers():
+    p, mask, o = _case("3d_24_3cubed")
+    g = _bddc(p, mask=mask)
+    b = o.rhs(p.f[:, 0])
+    xo, h = o.pcg(b, 1e-8)
+    x, res = g.pcg_solve_host(b, rtol=1e-8)
+    assert int(res.iters[0]) == h[0]["iters"]
+    assert _rel(x, xo) < 1e-10
+
+
+def test_single_subdomain_converges_in_one_iteration():
+    p, mask, o = _case("2d_single_sub")
+    g = _bddc(p, mask=mask)
+    b = o.rhs(p.f[:, 0])
+    x, res = g.pcg_solve(_cuda(b), rtol=1e-8)
+    assert int(res.iters[0]) <= 1
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
+def test_apply_low_precision_error_bound(prec, tol):
+    # operators rounded to the format's unit roundoff u (fp32 6e-8, bf16 4e-3),
+    # operand rounded as well, float32 accumulation over n <= 729 terms
+    p, mask, o = _case("3d_24_3cubed")
+    g = _bddc(p, precision=prec, mask=mask)
+    r = synth.uniform(36, o.n_nodes)
+    r[o.dir] = 0
+    z = g.apply(_cuda(r)).cpu().numpy()
+    want = o.apply_nodes(r)
+    err = np.linalg.norm(z - want) / np.linalg.norm(want)
+    assert err < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_flexible_pcg_reaches_fp64_accuracy(prec):
+    p, mask, o = _case("3d_24_3cubed")
+    b = o.rhs(p.f[:, 0])
+    x_star, _ = o.pcg(b, 1e-12)
+    g64 = _bddc(p, mask=mask)
+    x64, r64 = g64.pcg_solve(_cuda(b), rtol=1e-8)
+    g = _bddc(p, precision=prec, mask=mask)
+    x, res = g.pcg_solve(_cuda(b), rtol=1e-8, maxit=500)
+    assert res.status == 0
+    xt = _cuda(x.cpu().numpy())
+    true_res = (torch.from_numpy(b).cuda() - g64.matvec(xt)).norm() / torch.from_numpy(b).cuda().norm()
+    assert float(true_res) < 1.5e-8
+    e64 = np.linalg.norm(x64.cpu().numpy() - x_star) / np.linalg.norm(x_star)
+    e = np.linalg.norm(x.cpu().numpy() - x_star) / np.linalg.norm(x_star)
+    assert e < 10 * max(e64, 1e-12)
+    assert int(res.iters[0]) <= 2 * int(r64.iters[0]) + 2
+
+
+def test_full_size_config2_properties():
+    """96^3 elements, 12^3 subdomains (the benchmark workload): properties that
+    hold at any size, since the oracle cannot run this size inside a test."""
+    from oracle import dirichlet_mask
+    p = synth.config(2)
+    g = _bddc(p)
+    inf = g.info()
+    assert inf["n_c"] == 10439 and inf["n_free"] == 857375
+    n1 = p.ne + 1
+    idx = np.arange(g.n_nodes)
+    coords = np.stack([idx % n1, (idx // n1) % n1, idx // (n1 * n1)])
+    dmask = dirichlet_mask(3, p.ne)
+    iface = (np.any(coords % 8 == 0, axis=0)) & ~dmask      # box subdomains of 8^3
+    gen = torch.Generator(device="cuda").manual_seed(5)
+
+    def rand_iface():
+        v = torch.rand(g.n_nodes, dtype=torch.float64, device="cuda", generator=gen) - 0.5
+        v[torch.from_numpy(~iface).cuda()] = 0
+        return v
+
+    # on residuals with zero interior part M^-1 is symmetric positive definite
+    u, v = rand_iface(), rand_iface()
+    Mu, Mv = g.apply(u), g.apply(v)
+    assert abs(float(u @ Mv - v @ Mu)) < 1e-10 * float(u.norm() * Mv.norm())
+    assert float(u @ Mu) > 0 and float(v @ Mv) > 0
+    # PCG reaches rtol with a true residual below the tolerance
+    f = torch.from_numpy(p.f[:, 0].copy()).cuda()
+    b = g.rhs(f)
+    x, res = g.pcg_solve(b, rtol=1e-8, maxit=300)
+    assert res.status == 0 and 5 <= int(res.iters[0]) <= 80
+    tr = (b - g.matvec(x)).norm() / b.norm()
+    assert float(tr) < 1.5e-8
+    # the mixed forms reach the same solution to the solver tolerance
+    for prec in ("fp32", "bf16"):
+        gm = _bddc(p, precision=prec)
+        xm, rm = gm.pcg_solve(b, rtol=1e-8, maxit=300)
+        assert rm.status == 0
+        assert float((xm - x).norm() / x.norm()) < 1e-6
+        gm.close()

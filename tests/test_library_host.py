@@ -1,0 +1,155 @@
+"""Host-side checks of libbddc that need no GPU: exported symbols, argument
+validation, and the float64 setup (globs, Phi_i, A_ci, A_c) against the
+oracle's explicit saddle-point construction (Sec. 2, Eq. saddlepoint)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import CORNER, EDGE, FACE, Oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_14786_gb300 import _lib, build
+    build.build()
+    return _lib.lib()
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bddc_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    from paper_2410_14786_gb300 import _lib
+    names = _declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(_lib.EXPORTED) == names
+
+
+def _structs(p, precision=0, constraints=0, nrhs_max=1):
+    from paper_2410_14786_gb300 import _lib
+    sig = np.ascontiguousarray(p.elem_sigma, dtype=np.float64)
+    part = np.ascontiguousarray(p.elem_subdomain, dtype=np.int32)
+    prob = _lib.Problem(p.dim, p.ne, sig.ctypes.data_as(C.POINTER(C.c_double)),
+                        part.ctypes.data_as(C.POINTER(C.c_int32)), p.n_sub)
+    opts = _lib.Options(precision, constraints, nrhs_max, 4, 0)
+    return prob, opts, (sig, part)
+
+
+def _inspect(L, p, constraints=0):
+    from paper_2410_14786_gb300 import _lib
+    prob, opts, keep = _structs(p, constraints=constraints)
+    info = _lib.Info()
+    rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 1, C.byref(info), None, 0)
+    assert rc == 0, L.bddc_last_error()
+    n = info.n_c
+    Ac = np.zeros(max(1, n * n))
+    rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 1, C.byref(info),
+                              Ac.ctypes.data_as(C.POINTER(C.c_double)), Ac.size)
+    assert rc == 0, L.bddc_last_error()
+    return info, Ac[:n * n].reshape(n, n)
+
+
+CASES = [
+    ("2d_cfg1", lambda: synth.config(1), CORNER | EDGE),
+    ("2d_lognormal_3x3", lambda: synth.make_problem(2, 24, 3, "lognormal", k=11), 0),
+    ("3d_lognormal_3cubed", lambda: synth.make_problem(3, 12, 3, "lognormal", k=12), 0),
+    ("3d_corners_only", lambda: synth.make_problem(3, 8, 2, "lognormal", k=13), CORNER),
+    ("3d_voronoi", lambda: _small_voronoi(), 0),
+]
+
+
+def _small_voronoi():
+    sub, n, cell = synth.voronoi_partition(10, 6, 77)
+    s = synth.layer_sigma(10, cell)
+    f = synth.uniform(78, 11 ** 3).reshape(-1, 1)
+    return synth.Problem(3, 10, s, sub, n, f, "voronoi_10_6")
+
+
+@pytest.mark.parametrize("name,make,mask", CASES, ids=[c[0] for c in CASES])
+def test_coarse_matrix_matches_oracle(L, name, make, mask):
+    p = make()
+    info, Ac = _inspect(L, p, mask)
+    o = Oracle(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub,
+               constraints=mask or (CORNER | EDGE | FACE))
+    assert info.n_c == o.n_c
+    kinds = [g.kind for g in o.globs]
+    assert (info.n_corners, info.n_edges, info.n_faces) == (kinds.count(CORNER), kinds.count(EDGE),
+                                                            kinds.count(FACE))
+    assert info.n_free == o.n_free
+    assert info.n_interior == int(np.sum(o.kappa == 1))
+    Ao = o.Ac.toarray()
+    assert np.abs(Ac - Ao).max() <= 1e-10 * np.abs(Ao).max()
+
+
+def test_structured_sizes_config2_shape(L):
+    # 96^3 grid with 12^3 subdomains: the glob counts of the size table
+    p = synth.make_problem(3, 96, 12, "one")
+    from paper_2410_14786_gb300 import _lib
+    prob, opts, keep = _structs(p)
+    info = _lib.Info()
+    rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0)
+    assert rc == 0
+    assert (info.n_corners, info.n_edges, info.n_faces, info.n_c) == (1331, 4356, 4752, 10439)
+    assert info.n_free == 857375 and info.max_ni == 729
+    assert info.sum_ni == 1191016 and info.sum_nI2 == 1728 * 343 ** 2
+
+
+def _rc(L, p, **kw):
+    prob, opts, keep = _structs(p, **kw)
+    from paper_2410_14786_gb300 import _lib
+    info = _lib.Info()
+    return L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 1, C.byref(info), None, 0), info
+
+
+def test_invalid_arguments(L):
+    base = synth.make_problem(2, 8, 2, "one")
+    bad = synth.make_problem(2, 8, 2, "one")
+    bad.elem_sigma = bad.elem_sigma.copy()
+    bad.elem_sigma[3] = -1.0
+    assert _rc(L, bad)[0] == -1
+    bad.elem_sigma[3] = np.nan
+    assert _rc(L, bad)[0] == -1
+    bad = synth.make_problem(2, 8, 2, "one")
+    bad.elem_subdomain = bad.elem_subdomain.copy()
+    bad.elem_subdomain[0] = 99
+    assert _rc(L, bad)[0] == -1
+    assert b"out of range" in L.bddc_last_error()
+    # an id range with an empty subdomain
+    bad = synth.make_problem(2, 8, 2, "one")
+    bad.n_sub = 5
+    assert _rc(L, bad)[0] == -1
+    assert _rc(L, base, precision=7)[0] == -1
+    assert _rc(L, base, nrhs_max=65)[0] == -1
+    assert _rc(L, base, constraints=8)[0] == -1
+    assert b"constraint" in L.bddc_last_error()
+
+
+def test_floating_subdomain_without_constraints_is_singular(L):
+    # 2D, faces only: no constraints at all; the centre subdomain of 3x3 floats
+    p = synth.make_problem(2, 12, 3, "one")
+    rc, _ = _rc(L, p, constraints=FACE)
+    assert rc == -4
+    assert b"subdomain 4" in L.bddc_last_error()
+
+
+def test_setup_without_device_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    from paper_2410_14786_gb300 import _lib
+    p = synth.make_problem(2, 8, 2, "one")
+    prob, opts, keep = _structs(p)
+    h = C.c_void_p()
+    rc = L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(h))
+    assert rc == -7 and not h.value
