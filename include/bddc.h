@@ -130,6 +130,25 @@ int bddc_setup(const bddc_problem_t *problem, const bddc_options_t *options,
  * nothing. */
 int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *stream);
 
+/* The same z = M^-1 r as bddc_apply, with the apply's temporary vectors in a
+ * fixed 8 MiB array that the library reserves on every GPU it is loaded on
+ * (held until the process exits), instead of in the handle's workspace. The
+ * paper has no counterpart: this is for callers that cannot have device
+ * memory allocated on their behalf, for example a host program whose own
+ * allocator owns the whole device and forbids cudaMalloc / cudaFree from
+ * libraries, or a program that fixes all device memory at start-up. The call
+ * itself never calls cudaMalloc, cudaFree or any allocating routine.
+ * Limit: (3 n_interior + 2 n_interface_copies + sum n_ci + 2 n_c) * nrhs,
+ * each term rounded up to 32, must not exceed 2^20 doubles; larger problems
+ * get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture. Every call on every handle of
+ * a device shares the one array, and no part of it needs to start at zero
+ * (each call writes every element it reads before reading it): calls that
+ * overlap on the GPU, on any streams, race and give wrong results. */
+int bddc_apply_static_scratch(bddc_handle_t h, const double *r, double *z, int32_t nrhs,
+                              void *stream);
+
 /* y = A x (the global stiffness matrix on the free nodes; Dirichlet entries
  * of y are written 0). Device vectors; asynchronous on `stream`. */
 int bddc_matvec(bddc_handle_t h, const double *x, double *y, int32_t nrhs, void *stream);

@@ -28,6 +28,7 @@ EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
     "bddc_pcg_solve_host", "bddc_coarse_vectors", "bddc_query", "bddc_profile_apply",
     "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_setup_inspect",
+    "bddc_apply_static_scratch",
 ]
 
 
@@ -65,6 +66,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "bddc_setup": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), C.POINTER(vp)]),
         "bddc_apply": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_apply_static_scratch": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_matvec": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_rhs": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_pcg_solve": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),

@@ -339,6 +339,8 @@ int check_handle(bddc_handle_t h, int nrhs) {
 
 }  // namespace
 
+int bddc::set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+
 extern "C" {
 
 const char* bddc_strerror(int status) {

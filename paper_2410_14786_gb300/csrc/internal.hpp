@@ -50,6 +50,9 @@ struct HostSetup {
   int error_subdomain = -1;
 };
 
+// Record `msg` for bddc_last_error() on this thread; returns `code`.
+int set_last_error(int code, const std::string& msg);
+
 // Validate the problem and options (no device checks).
 int validate_problem(const bddc_problem_t* p, const bddc_options_t* o, std::string& err);
 // Topology and float64 numerics; with invert_coarse = false, Acinv holds A_c itself.
