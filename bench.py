@@ -304,6 +304,28 @@ def run_gb300(args):
     return 0
 
 
+def run_apply_only(args):
+    """A short command for profilers: setup, N applies, one PCG solve."""
+    import torch
+
+    import synth
+    from paper_2410_14786_gb300 import BDDC, build
+    build.build()
+    p = synth.config(2)
+    g = BDDC.from_problem(p, precision=args.precision, nrhs_max=1)
+    f = torch.from_numpy(np.ascontiguousarray(p.f[:, 0])).cuda()
+    b = g.rhs(f)
+    z = torch.empty_like(b)
+    for _ in range(args.apply_only):
+        g.apply(b, z)
+    x, res = g.pcg_solve(b, rtol=RTOL, maxit=500)
+    torch.cuda.synchronize()
+    print(json.dumps({"apply_only": args.apply_only, "precision": args.precision, "iters": int(res.iters[0]),
+                      "relres": float(res.relres[0])}))
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,11 +335,15 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--only", default=None, choices=[None, "fp64", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", type=int, default=0,
+                    help="profiling aid: set up the headline form, run this many applies and one solve, exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_only:
+        return run_apply_only(args)
     return run_gb300(args)
 
 

@@ -114,6 +114,8 @@ typedef struct {
     double setup_seconds;               /* wall time of bddc_setup */
     int32_t precision;
     int32_t error_subdomain;            /* subdomain of the last SINGULAR error, else -1 */
+    int32_t device_error;               /* BDDC_ERR_TIMEOUT if a bounded device wait of an
+                                           earlier call ran out, else 0 (bddc_query synchronises) */
 } bddc_info_t;
 
 /* Build the preconditioner (all factorisations in float64 on the host,
@@ -138,9 +140,9 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * allocator owns the whole device and forbids cudaMalloc / cudaFree from
  * libraries, or a program that fixes all device memory at start-up. The call
  * itself never calls cudaMalloc, cudaFree or any allocating routine.
- * Limit: (3 n_interior + 2 n_interface_copies + sum n_ci + 2 n_c) * nrhs,
- * each term rounded up to 32, must not exceed 2^20 doubles; larger problems
- * get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
+ * Limit: the temporaries of one apply, (3 n_interior + 3 n_interface_copies
+ * + 2 sum n_ci + (2 + ceil(n_c / 512)) n_c) * nrhs doubles, each term rounded
+ * up to 32, must not exceed 2^20; larger problems get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current); make
  * that first call before any stream capture. Every call on every handle of
  * a device shares the one array, and no part of it needs to start at zero

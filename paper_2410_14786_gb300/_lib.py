@@ -48,7 +48,8 @@ class Info(C.Structure):
         "n_corners", "n_edges", "n_faces", "sum_ni", "sum_nI2", "sum_nG2", "sum_nG_nc",
         "max_ni", "operator_bytes", "coarse_bytes", "device_bytes", "apply_bytes_1rhs",
         "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches")] + [
-        ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32)]
+        ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
+        ("device_error", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

@@ -90,6 +90,44 @@ std::vector<T> pack_arena(const std::vector<std::vector<double>>& ops, const std
   return out;
 }
 
+// Pack per-subdomain rectangular float64 blocks (rows x cols, row-major on
+// the host) with rows padded to 16 bytes and blocks aligned to 256 bytes.
+std::vector<double> pack_rect(const std::vector<std::vector<double>>& src, const std::vector<int>& rows,
+                              const std::vector<int>& cols, bool transpose, std::vector<int64_t>& off,
+                              std::vector<int32_t>& ld) {
+  // transpose: src[s] is cols x rows and the block stores its transpose
+  const size_t S = rows.size();
+  off.assign(S, 0);
+  ld.assign(S, 0);
+  int64_t cur = 0;
+  for (size_t s = 0; s < S; ++s) {
+    cur = (cur + 31) / 32 * 32;
+    off[s] = cur;
+    ld[s] = padded_ld(cols[s], 8);
+    cur += (int64_t)rows[s] * ld[s];
+  }
+  std::vector<double> out((size_t)std::max<int64_t>(cur, 1), 0.0);
+  for (size_t s = 0; s < S; ++s)
+    for (int r = 0; r < rows[s]; ++r)
+      for (int c = 0; c < cols[s]; ++c)
+        out[off[s] + (int64_t)r * ld[s] + c] =
+            transpose ? src[s][(size_t)c * rows[s] + r] : src[s][(size_t)r * cols[s] + c];
+  return out;
+}
+
+// Row tiles of rectangular operators.
+std::vector<WorkItem> make_rect_items(const std::vector<int64_t>& off, const std::vector<int32_t>& ld,
+                                      const std::vector<int>& rows, const std::vector<int>& cols,
+                                      const std::vector<int32_t>& xoff, const std::vector<int32_t>& yoff, int tile) {
+  std::vector<WorkItem> items;
+  for (size_t s = 0; s < rows.size(); ++s)
+    for (int r0 = 0; r0 < rows[s]; r0 += tile)
+      items.push_back(WorkItem{off[s], ld[s], cols[s], r0, std::min(tile, rows[s] - r0), xoff[s], yoff[s]});
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem& a, const WorkItem& b) { return a.ncols > b.ncols; });
+  return items;
+}
+
 double cvt_d(double v) { return v; }
 float cvt_f(double v) { return (float)v; }
 __nv_bfloat16 cvt_b(double v) { return __float2bfloat16_rn((float)v); }
@@ -109,23 +147,24 @@ std::vector<WorkItem> make_items(const std::vector<int64_t>& off, const std::vec
 
 int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   const int S = hs.n_sub;
+  int64_t in_coarse_bytes = 0;
   // ---- compact layouts --------------------------------------------------------
   std::vector<int32_t> ioff(S + 1, 0), goff(S + 1, 0), coff(S + 1, 0);
   for (int s = 0; s < S; ++s) {
     ioff[s + 1] = ioff[s] + (int32_t)hs.sub_I[s].size();
     goff[s + 1] = goff[s] + (int32_t)hs.sub_G[s].size();
     coff[s + 1] = coff[s] + (int32_t)hs.sub_globs[s].size();
+    h->max_nc = std::max(h->max_nc, (int)hs.sub_globs[s].size());
   }
   h->nI_tot = ioff[S]; h->nG_tot = goff[S]; h->nC_tot = coff[S]; h->n_c = hs.n_c;
   h->n_dir = (int64_t)hs.dir_nodes.size();
-  std::vector<int32_t> inode(h->nI_tot), gnode(h->nG_tot), csub(h->nC_tot), ccdof(h->nC_tot), gsub(h->nG_tot);
+  std::vector<int32_t> inode(h->nI_tot), gnode(h->nG_tot), csub(h->nC_tot), ccdof(h->nC_tot);
   std::vector<double> gw(h->nG_tot);
   for (int s = 0; s < S; ++s) {
     std::copy(hs.sub_I[s].begin(), hs.sub_I[s].end(), inode.begin() + ioff[s]);
     for (size_t l = 0; l < hs.sub_G[s].size(); ++l) {
       gnode[goff[s] + l] = hs.sub_G[s][l];
       gw[goff[s] + l] = 1.0 / hs.kappa[hs.sub_G[s][l]];
-      gsub[goff[s] + l] = s;
     }
     for (size_t r = 0; r < hs.sub_globs[s].size(); ++r) {
       csub[coff[s] + r] = s;
@@ -152,20 +191,20 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       aig_ptr[ioff[s] + r + 1] = (int32_t)aig_col.size();
     }
   }
-  // Phi_G (copy rows) and Phi_G^T (constraint rows), float64
-  std::vector<double> phi, phit;
-  std::vector<int64_t> phit_off(S, 0), gcopy_phirow(h->nG_tot, 0);
-  for (int s = 0; s < S; ++s) {
-    const int nG = (int)hs.sub_G[s].size(), nc = (int)hs.sub_globs[s].size();
-    const int64_t po = (int64_t)phi.size();
-    phit_off[s] = (int64_t)phit.size();
-    for (int l = 0; l < nG; ++l) {
-      gcopy_phirow[goff[s] + l] = po + (int64_t)l * nc;
-      for (int c = 0; c < nc; ++c) phi.push_back(hs.Phi[s][(size_t)l * nc + c]);
-    }
-    for (int c = 0; c < nc; ++c)
-      for (int l = 0; l < nG; ++l) phit.push_back(hs.Phi[s][(size_t)l * nc + c]);
-  }
+  // Phi_G^T (n_c x n_G per subdomain: coarse residual) and Phi_G (n_G x n_c:
+  // prolongation), float64, as batched operators of the streamed GEMV
+  std::vector<int> nGv(S), ncv(S);
+  for (int s = 0; s < S; ++s) { nGv[s] = (int)hs.sub_G[s].size(); ncv[s] = (int)hs.sub_globs[s].size(); }
+  std::vector<int64_t> ptoff, poff;
+  std::vector<int32_t> ptld, pld;
+  std::vector<double> phit = pack_rect(hs.Phi, ncv, nGv, true, ptoff, ptld);
+  std::vector<double> phi = pack_rect(hs.Phi, nGv, ncv, false, poff, pld);
+  auto itPT = make_rect_items(ptoff, ptld, ncv, nGv, goff, coff, 128);
+  auto itP = make_rect_items(poff, pld, nGv, ncv, coff, goff, 128);
+  h->n_wi_PT = (int)itPT.size();
+  h->n_wi_P = (int)itP.size();
+  h->max_ld_PT = ptld.empty() ? 0 : *std::max_element(ptld.begin(), ptld.end());
+  h->max_ld_P = pld.empty() ? 0 : *std::max_element(pld.begin(), pld.end());
   // coarse gather map: coarse dof -> local constraint positions
   std::vector<int32_t> cg_ptr(hs.n_c + 1, 0), cg_idx(h->nC_tot);
   for (int64_t j = 0; j < h->nC_tot; ++j) cg_ptr[ccdof[j] + 1]++;
@@ -220,17 +259,46 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   h->max_cols_G = ldG.empty() ? 0 : *std::max_element(ldG.begin(), ldG.end());
   CUDA_TRY(upload(h, &h->d_wi_I, itI));
   CUDA_TRY(upload(h, &h->d_wi_G, itG));
-  // coarse inverse, float64, rows padded
+  h->use_tma = bgemv_tma_supported(prec, h->max_cols_I) && bgemv_tma_supported(prec, h->max_cols_G);
+  {
+    const int ttile = 128;
+    auto tI = make_items(offI, ldI, dI, ioff, ttile);
+    auto tG = make_items(offG, ldG, dG, goff, ttile);
+    h->n_wt_I = (int)tI.size();
+    h->n_wt_G = (int)tG.size();
+    CUDA_TRY(upload(h, &h->d_wt_I, tI));
+    CUDA_TRY(upload(h, &h->d_wt_G, tG));
+  }
+  // coarse inverse, float64, stored as column panels of kPanel columns (each
+  // an n_c x width row-major block, blocks aligned to 256 bytes); the panels'
+  // partial products are summed by a separate kernel
   std::vector<WorkItem> itC;
   if (hs.n_c) {
-    h->ldc = padded_ld((int)hs.n_c, 8);
-    std::vector<double> ac((size_t)hs.n_c * h->ldc, 0.0);
-    for (int64_t r = 0; r < hs.n_c; ++r)
-      std::memcpy(&ac[(size_t)r * h->ldc], &hs.Acinv[(size_t)r * hs.n_c], sizeof(double) * hs.n_c);
+    const int kPanel = 512;
+    const int nc = (int)hs.n_c;
+    h->ldc = kPanel;
+    h->n_cpanels = (nc + kPanel - 1) / kPanel;
+    std::vector<int64_t> poff(h->n_cpanels);
+    std::vector<int32_t> pw(h->n_cpanels), pld(h->n_cpanels);
+    int64_t cur = 0;
+    for (int p = 0; p < h->n_cpanels; ++p) {
+      cur = (cur + 31) / 32 * 32;
+      poff[p] = cur;
+      pw[p] = std::min(kPanel, nc - p * kPanel);
+      pld[p] = padded_ld(pw[p], 8);
+      cur += (int64_t)nc * pld[p];
+    }
+    std::vector<double> ac((size_t)cur, 0.0);
+    for (int p = 0; p < h->n_cpanels; ++p)
+      for (int r = 0; r < nc; ++r)
+        std::memcpy(&ac[poff[p] + (int64_t)r * pld[p]], &hs.Acinv[(size_t)r * nc + (size_t)p * kPanel],
+                    sizeof(double) * pw[p]);
     CUDA_TRY(upload(h, &h->d_acinv, ac));
-    const int ctile = 16;
-    for (int r0 = 0; r0 < hs.n_c; r0 += ctile)
-      itC.push_back(WorkItem{0, h->ldc, (int32_t)hs.n_c, r0, (int32_t)std::min<int64_t>(ctile, hs.n_c - r0), 0, 0});
+    in_coarse_bytes = (int64_t)cur * 8;
+    const int ctile = 128;
+    for (int p = 0; p < h->n_cpanels; ++p)
+      for (int r0 = 0; r0 < nc; r0 += ctile)
+        itC.push_back(WorkItem{poff[p], pld[p], pw[p], r0, std::min(ctile, nc - r0), p * kPanel, p * nc});
   }
   h->n_wi_C = (int)itC.size();
   CUDA_TRY(upload(h, &h->d_wi_C, itC));
@@ -247,9 +315,10 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(upload(h, &h->d_aig_ptr, aig_ptr));
   CUDA_TRY(upload(h, &h->d_aig_col, aig_col));
   CUDA_TRY(upload(h, &h->d_aig_val, aig_val));
-  CUDA_TRY(upload(h, &h->d_phi, phi));
   CUDA_TRY(upload(h, &h->d_phit, phit));
-  CUDA_TRY(upload(h, &h->d_sub_phit_off, phit_off));
+  CUDA_TRY(upload(h, &h->d_phi, phi));
+  CUDA_TRY(upload(h, &h->d_wi_PT, itPT));
+  CUDA_TRY(upload(h, &h->d_wi_P, itP));
   CUDA_TRY(upload(h, &h->d_sub_goff, goff));
   CUDA_TRY(upload(h, &h->d_sub_coff, coff));
   CUDA_TRY(upload(h, &h->d_csub, csub));
@@ -259,8 +328,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(upload(h, &h->d_gu_node, gu_node));
   CUDA_TRY(upload(h, &h->d_gu_ptr, gu_ptr));
   CUDA_TRY(upload(h, &h->d_gu_copy, gu_copy));
-  CUDA_TRY(upload(h, &h->d_gcopy_phirow, gcopy_phirow));
-  CUDA_TRY(upload(h, &h->d_gcopy_sub, gsub));
+
   // ---- workspace ---------------------------------------------------------------------
   const int64_t R = h->nrhs_max;
   CUDA_TRY(dev_alloc(h, &h->w_rI, h->nI_tot * R));
@@ -268,9 +336,12 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(dev_alloc(h, &h->w_bI, h->nI_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w_yG, h->nG_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w_zG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_eG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w_ucl, h->nC_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w_g, h->nC_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w_rc, h->n_c * R));
   CUDA_TRY(dev_alloc(h, &h->w_uc, h->n_c * R));
+  CUDA_TRY(dev_alloc(h, &h->w_cpart, (int64_t)std::max(1, h->n_cpanels) * h->n_c * R));
   CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   const int64_t NV = h->n_nodes * R;
@@ -283,11 +354,16 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(dev_alloc(h, &h->s_x, NV));
   h->n_red_blocks = kRedBlocks;
   CUDA_TRY(dev_alloc(h, &h->d_partials, (size_t)kRedBlocks * 3 * R));
+  CUDA_TRY(dev_alloc(h, &h->d_counter, 1));
+  CUDA_TRY(cudaMemset(h->d_counter, 0, sizeof(unsigned int)));
+  CUDA_TRY(dev_alloc(h, &h->d_stencil, (size_t)stencil_points(h->dim) * h->n_nodes));
+  CUDA_TRY(launch_build_stencil(h, nullptr));
   CUDA_TRY(dev_alloc(h, &h->d_scal, (size_t)S_COUNT * R));
-  CUDA_TRY(dev_alloc(h, &h->d_iscal, (size_t)I_COUNT * R + 2));
+  CUDA_TRY(dev_alloc(h, &h->d_iscal, (size_t)I_COUNT * R + kGlobalFlags));
   CUDA_TRY(cudaMemset(h->d_scal, 0, sizeof(double) * S_COUNT * R));
-  CUDA_TRY(cudaMemset(h->d_iscal, 0, sizeof(int32_t) * (I_COUNT * R + 2)));
-  CUDA_TRY(cudaMallocHost(&h->h_flags, sizeof(int32_t) * (I_COUNT * R + 2)));
+  CUDA_TRY(cudaMemset(h->d_iscal, 0, sizeof(int32_t) * (I_COUNT * R + kGlobalFlags)));
+  CUDA_TRY(cudaMallocHost(&h->h_flags, sizeof(int32_t) * (I_COUNT * R + kGlobalFlags)));
+  h->d_err = h->d_iscal + I_COUNT * R + 2;
   // ---- info ------------------------------------------------------------------------
   bddc_info_t& in = h->info;
   in.n_nodes = hs.n_nodes;
@@ -310,7 +386,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     in.max_ni = std::max(in.max_ni, nI + nG);
   }
   in.operator_bytes = (int64_t)arena_bytes;
-  in.coarse_bytes = hs.n_c * (int64_t)h->ldc * 8;
+  in.coarse_bytes = in_coarse_bytes;
   const int eb = elem_bytes(prec);
   // compulsory HBM bytes of one apply (nrhs = 1): operators as stored (A_II^-1
   // read twice), Phi rows twice, coarse inverse once, the sparse couplings,
@@ -363,6 +439,8 @@ const char* bddc_last_error(void) { return g_last_error.c_str(); }
 void bddc_destroy(bddc_handle_t h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  if (h->iter_graph) cudaGraphExecDestroy(h->iter_graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocations) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   delete h;
@@ -456,6 +534,8 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
 int bddc_query(bddc_handle_t h, bddc_info_t* info) {
   if (!h || !info) return fail(BDDC_ERR_INVALID_ARG, "null argument");
   h->info.kernel_launches = h->launches;
+  CUDA_TRY(cudaSetDevice(h->device));
+  CUDA_TRY(cudaMemcpy(&h->info.device_error, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   *info = h->info;
   return BDDC_OK;
 }
@@ -472,7 +552,7 @@ int bddc_matvec(bddc_handle_t h, const double* x, double* y, int32_t nrhs, void*
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
   if (!x || !y || x == y) return fail(BDDC_ERR_INVALID_ARG, "x and y must be distinct device pointers");
-  CUDA_TRY(launch_matvec(h, x, y, nrhs, static_cast<cudaStream_t>(stream)));
+  CUDA_TRY(launch_spmv(h, x, y, nrhs, -1, 0.0, 0, static_cast<cudaStream_t>(stream)));
   return BDDC_OK;
 }
 
@@ -517,45 +597,94 @@ int bddc_profile_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs
   return BDDC_OK;
 }
 
+// Capture one PCG iteration (apply, beta, p update, SpMV with alpha, x/r
+// update with the stop test, flag read-back) as a CUDA graph for x, nrhs,
+// rtol and the form; reused while those stay the same.
+static int capture_iteration(bddc_handle_t h, double* x, int nrhs, double rtol, int flexible) {
+  if (h->iter_graph && h->graph_x == x && h->graph_nrhs == nrhs && h->graph_rtol == rtol &&
+      h->graph_flexible == flexible)
+    return BDDC_OK;
+  if (h->iter_graph) {
+    cudaGraphExecDestroy(h->iter_graph);
+    h->iter_graph = nullptr;
+  }
+  if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const int R = h->nrhs_max;
+  cudaStream_t cs = h->cap_stream;
+  const int64_t l0 = h->launches;
+  CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = launch_apply(h, h->p_r, h->p_z, nrhs, cs);
+  if (e == cudaSuccess)
+    e = launch_dots_fin(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, FIN_BETA, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_update_p(h, nrhs, cs);
+  if (e == cudaSuccess) e = launch_spmv(h, h->p_p, h->p_q, nrhs, FIN_ALPHA, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_update_xr_conv(h, x, nrhs, rtol, flexible, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_flags, h->d_iscal + I_COUNT * R, kGlobalFlags * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  h->graph_launches = h->launches - l0;
+  h->launches = l0;
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(BDDC_ERR_CUDA, std::string("capture of the PCG iteration: ") +
+                                   cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&h->iter_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->iter_graph = nullptr;
+    return fail(BDDC_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+  }
+  h->graph_x = x; h->graph_nrhs = nrhs; h->graph_rtol = rtol; h->graph_flexible = flexible;
+  return BDDC_OK;
+}
+
 static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, double rtol, int maxit,
                     int32_t* iters, double* relres, cudaStream_t st) {
   const int flexible = h->precision != BDDC_PREC_FP64;
   int32_t* hf = h->h_flags;
   const int R = h->nrhs_max;
+  auto read_flags = [&]() -> int {
+    CUDA_TRY(cudaMemcpyAsync(hf, h->d_iscal + I_COUNT * R, kGlobalFlags * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (hf[2]) return fail(BDDC_ERR_TIMEOUT, "a bounded device wait ran out");
+    return BDDC_OK;
+  };
   // x0 = P_I b ; r0 = b - A x0
   CUDA_TRY(launch_interior_correction(h, b, x, nrhs, st));
-  CUDA_TRY(launch_matvec(h, x, h->p_q, nrhs, st));
+  CUDA_TRY(launch_spmv(h, x, h->p_q, nrhs, -1, rtol, flexible, st));
   CUDA_TRY(launch_residual(h, b, nrhs, st));
-  CUDA_TRY(launch_dots(h, nrhs, b, b, h->p_r, h->p_r, nullptr, nullptr, st));
-  CUDA_TRY(launch_finalize(h, FIN_INIT, nrhs, rtol, flexible, st));
-  CUDA_TRY(cudaMemcpyAsync(hf, h->d_iscal + I_COUNT * R, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(launch_dots_fin(h, nrhs, b, b, h->p_r, h->p_r, FIN_INIT, rtol, flexible, st));
+  int rc = read_flags();
+  if (rc) return rc;
   int status = BDDC_OK;
-  if (hf[0] > 0) {
+  if (hf[0] > 0 && maxit > 0) {
+    // first iteration launched directly, the rest replay a captured graph
     CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
-    CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_z, nullptr, nullptr, nullptr, nullptr, st));
-    CUDA_TRY(launch_finalize(h, FIN_RHO, nrhs, rtol, flexible, st));
+    CUDA_TRY(launch_dots_fin(h, nrhs, h->p_r, h->p_z, nullptr, nullptr, FIN_RHO, rtol, flexible, st));
     CUDA_TRY(launch_update_p(h, nrhs, st));     // beta = 0: p = z, zold = z
-    int it = 0;
-    for (; it < maxit; ++it) {
-      CUDA_TRY(launch_matvec(h, h->p_p, h->p_q, nrhs, st));
-      CUDA_TRY(launch_dots(h, nrhs, h->p_p, h->p_q, nullptr, nullptr, nullptr, nullptr, st));
-      CUDA_TRY(launch_finalize(h, FIN_ALPHA, nrhs, rtol, flexible, st));
-      CUDA_TRY(launch_update_xr(h, x, nrhs, st));
-      CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_r, nullptr, nullptr, nullptr, nullptr, st));
-      CUDA_TRY(launch_finalize(h, FIN_CONV, nrhs, rtol, flexible, st));
-      CUDA_TRY(cudaMemcpyAsync(hf, h->d_iscal + I_COUNT * R, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      CUDA_TRY(cudaStreamSynchronize(st));
-      if (hf[0] == 0) break;
-      CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
-      CUDA_TRY(launch_dots(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, nullptr, nullptr, st));
-      CUDA_TRY(launch_finalize(h, FIN_BETA, nrhs, rtol, flexible, st));
-      CUDA_TRY(launch_update_p(h, nrhs, st));
+    CUDA_TRY(launch_spmv(h, h->p_p, h->p_q, nrhs, FIN_ALPHA, rtol, flexible, st));
+    CUDA_TRY(launch_update_xr_conv(h, x, nrhs, rtol, flexible, st));
+    if ((rc = read_flags())) return rc;
+    int it = 1;
+    if (hf[0] > 0 && it < maxit) {
+      if ((rc = capture_iteration(h, x, nrhs, rtol, flexible))) return rc;
+      for (; it < maxit && hf[0] > 0; ++it) {
+        CUDA_TRY(cudaGraphLaunch(h->iter_graph, st));
+        h->launches += h->graph_launches;
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (hf[2]) return fail(BDDC_ERR_TIMEOUT, "a bounded device wait ran out");
+      }
     }
     if (hf[0] > 0) status = BDDC_NOT_CONVERGED;
+  } else if (hf[0] > 0) {
+    status = BDDC_NOT_CONVERGED;
   }
   // per-column results
-  std::vector<int32_t> hi(I_COUNT * R + 2);
+  std::vector<int32_t> hi(I_COUNT * R + kGlobalFlags);
   std::vector<double> hd(S_COUNT * R);
   CUDA_TRY(cudaMemcpyAsync(hi.data(), h->d_iscal, hi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(hd.data(), h->d_scal, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));

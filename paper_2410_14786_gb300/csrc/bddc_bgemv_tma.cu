@@ -1,0 +1,367 @@
+// Batched dense GEMV / skinny GEMM over many small operators, streamed from
+// HBM with bulk asynchronous copies (cp.async.bulk, the TMA's 1D form) into
+// a ring of shared-memory stages (sm_103a).
+//
+// Used for the local operators of the apply (A_II^-1 and K_GG of every
+// subdomain): y = Op x with Op row-major, rows padded to 16 bytes. A work
+// item is a run of consecutive rows of one operator, which is one contiguous
+// byte range in the arena, so one bulk copy moves a whole stage of rows.
+//
+// Block layout: 8 consumer warps and 1 producer warp. The producer's lane 0
+// walks the same (item, stage) sequence as the consumers and keeps up to
+// kStages bulk copies in flight; `full[s]` completes when stage s has
+// landed (transaction bytes), `empty[s]` when all 8 consumer warps are done
+// with it. Consumers split each warp into groups of `lpr` lanes, one row per
+// group, read the operator row from shared memory in 16-byte vectors, and
+// reduce within the group. The operand x of the item is staged in shared
+// memory (double buffered, one named barrier per item).
+//
+// Every mbarrier wait is bounded (kWaitCycles); on timeout the waiting
+// thread sets *err and leaves its loop, and the producer waits (bounded) for
+// its own copies in flight before the block exits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace bddc {
+
+namespace {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kTmaThreads = (kConsumerWarps + 1) * 32;
+constexpr int kStages = 4;
+constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
+}
+
+template <typename T> struct Op;
+template <> struct Op<double> {
+  static constexpr int V = 2;
+  using Acc = double;
+  __device__ static void load(const double* p, double o[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <> struct Op<float> {
+  static constexpr int V = 4;
+  using Acc = float;
+  __device__ static void load(const float* p, float o[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct Op<__nv_bfloat16> {
+  static constexpr int V = 8;
+  using Acc = float;
+  __device__ static void load(const __nv_bfloat16* p, float o[8]) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[2 * i] = __uint_as_float(w[i] << 16);
+      o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+  }
+};
+
+// Lanes per row: the smallest power of two in [4, 32] that leaves each lane
+// at most 8 vectors of the row.
+__host__ __device__ __forceinline__ int lanes_per_row(int lda, int V) {
+  const int nvec = (lda + V - 1) / V;
+  int l = 4;
+  while (l < 32 && nvec > 8 * l) l <<= 1;
+  return l;
+}
+// Rows per stage: as many as fit, rounded down to whole consumer rounds.
+__host__ __device__ __forceinline__ int rows_per_stage(int row_bytes, int stage_bytes, int lpr) {
+  int rps = stage_bytes / row_bytes;
+  const int round = kConsumerWarps * (32 / lpr);
+  if (rps >= round) rps = rps / round * round;
+  return rps < 1 ? 1 : rps;
+}
+
+template <typename T, int NRB>
+__global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __restrict__ items, int n_items,
+                                                           const T* __restrict__ arena, const double* __restrict__ X,
+                                                           double* __restrict__ Y,
+                                                           const int32_t* __restrict__ yscatter, int nrhs,
+                                                           int stage_bytes, int max_lda, int32_t* __restrict__ err) {
+  using Acc = typename Op<T>::Acc;
+  constexpr int V = Op<T>::V;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stages = smem;
+  Acc* xbuf = reinterpret_cast<Acc*>(smem + (size_t)kStages * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 2 * (size_t)max_lda * NRB);
+  uint64_t* empty = full + kStages;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int nrb = (nrhs + NRB - 1) / NRB;
+  const int total = n_items * nrb;
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    int slot = 0;
+    uint32_t phase = 0;
+    bool pending[kStages];
+    uint32_t pend_parity[kStages];
+    for (int s = 0; s < kStages; ++s) pending[s] = false;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const WorkItem w = items[u / nrb];
+      const int row_bytes = w.lda * (int)sizeof(T);
+      const int rps = rows_per_stage(row_bytes, stage_bytes, lanes_per_row(w.lda, V));
+      for (int r0 = 0; r0 < w.nrows; r0 += rps) {
+        if (!mbar_wait(&empty[slot], phase ^ 1u) || *(volatile int*)&abort_flag) {
+          atomicExch(err, BDDC_ERR_TIMEOUT);
+          abort_flag = 1;
+          ok = false;
+          break;
+        }
+        const int nr = min(rps, w.nrows - r0);
+        const uint32_t bytes = (uint32_t)nr * (uint32_t)row_bytes;
+        mbar_expect_tx(&full[slot], bytes);
+        bulk_load(stages + (size_t)slot * stage_bytes, arena + w.moff + (int64_t)(w.row0 + r0) * w.lda, bytes,
+                  &full[slot]);
+        pending[slot] = true;
+        pend_parity[slot] = phase;
+        if (++slot == kStages) { slot = 0; phase ^= 1u; }
+      }
+    }
+    // every copy this block issued must land before the block exits
+    for (int s = 0; s < kStages; ++s)
+      if (pending[s] && !mbar_wait(&full[s], pend_parity[s])) atomicExch(err, BDDC_ERR_TIMEOUT);
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  // After a timeout a warp keeps walking the same units and reaches every
+  // consumer barrier (so no other warp waits for it forever), but it no
+  // longer waits on stages nor computes.
+  // The operand of the next unit is loaded into registers while the current
+  // unit is computed (kPf values per thread), so staging it costs no global
+  // memory latency; operands larger than that are staged directly.
+  constexpr int kPf = 8;
+  constexpr int kCT = kConsumerWarps * 32;
+  const int tid = threadIdx.x;
+  const bool prefetch = max_lda * NRB <= kPf * kCT;
+  int slot = 0;
+  uint32_t phase = 0;
+  int buf = 0;
+  bool aborted = false;
+  double pf[kPf];
+  auto load_operand = [&](int uu) {
+    const WorkItem wn = items[uu / nrb];
+    const int r0n = (uu % nrb) * NRB, nrn = min(NRB, nrhs - r0n);
+#pragma unroll
+    for (int j = 0; j < kPf; ++j) {
+      const int i = tid + j * kCT;
+      const int c = i / NRB, k = i - c * NRB;
+      pf[j] = (c < wn.ncols && k < nrn) ? X[(int64_t)(wn.xoff + c) * nrhs + r0n + k] : 0.0;
+    }
+  };
+  if (prefetch && blockIdx.x < total) load_operand(blockIdx.x);
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const WorkItem w = items[u / nrb];
+    const int rhs0 = (u % nrb) * NRB;
+    const int nr_rhs = min(NRB, nrhs - rhs0);
+    Acc* xs = xbuf + (size_t)buf * max_lda * NRB;
+    if (prefetch) {
+#pragma unroll
+      for (int j = 0; j < kPf; ++j) {
+        const int i = tid + j * kCT;
+        if (i < w.lda * NRB) xs[i] = (Acc)pf[j];
+      }
+      if (u + (int)gridDim.x < total) load_operand(u + gridDim.x);
+    } else {
+      for (int i = tid; i < w.lda * NRB; i += kCT) {
+        const int c = i / NRB, k = i - c * NRB;
+        double v = 0.0;
+        if (c < w.ncols && k < nr_rhs) v = X[(int64_t)(w.xoff + c) * nrhs + rhs0 + k];
+        xs[i] = (Acc)v;
+      }
+    }
+    consumer_sync();
+    const int lpr = lanes_per_row(w.lda, V);
+    const int gpw = 32 / lpr;                 // rows per warp per round
+    const int group = lane / lpr, gl = lane - group * lpr;
+    const int row_bytes = w.lda * (int)sizeof(T);
+    const int rps = rows_per_stage(row_bytes, stage_bytes, lpr);
+    for (int r0 = 0; r0 < w.nrows; r0 += rps) {
+      if (!aborted && (*(volatile int*)&abort_flag || !mbar_wait(&full[slot], phase))) {
+        if (lane == 0) atomicExch(err, BDDC_ERR_TIMEOUT);
+        abort_flag = 1;
+        aborted = true;
+      }
+      if (aborted) continue;
+      const int nr = min(rps, w.nrows - r0);
+      const T* tile = reinterpret_cast<const T*>(stages + (size_t)slot * stage_bytes);
+      for (int base = warp * gpw; base < nr; base += kConsumerWarps * gpw) {
+        const int rr = base + group;
+        Acc acc[NRB];
+#pragma unroll
+        for (int k = 0; k < NRB; ++k) acc[k] = Acc(0);
+        if (rr < nr) {
+          const T* a = tile + (size_t)rr * w.lda;
+#pragma unroll 2
+          for (int c0 = gl * V; c0 < w.lda; c0 += lpr * V) {
+            Acc av[V];
+            Op<T>::load(a + c0, av);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+              for (int k = 0; k < NRB; ++k) acc[k] = fma(av[v], xs[(c0 + v) * NRB + k], acc[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NRB; ++k)
+          for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (rr < nr && gl < nr_rhs) {
+          Acc out = acc[0];
+#pragma unroll
+          for (int k = 1; k < NRB; ++k)
+            if (gl == k) out = acc[k];
+          const int64_t j = (int64_t)w.yoff + w.row0 + r0 + rr;
+          const int64_t dst = yscatter ? (int64_t)yscatter[j] : j;
+          Y[dst * nrhs + rhs0 + gl] = (double)out;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == kStages) { slot = 0; phase ^= 1u; }
+    }
+    buf ^= 1;
+  }
+}
+
+int g_num_sms = 0;
+
+// Stage size: about 12 KB of rows of the widest operator (at least one row),
+// so that four blocks fit on an SM: measured on GB300 with 1728 bf16
+// operators of 343 x 344, four 12 KB stages per block and four blocks per SM
+// streamed faster than fewer, larger stages.
+template <typename T, int NRB>
+int stage_size(int max_lda) {
+  using Acc = typename Op<T>::Acc;
+  const long long row = (long long)max_lda * (long long)sizeof(T);
+  const long long xs = 2LL * max_lda * NRB * (long long)sizeof(Acc) + 2 * kStages * 8;
+  const long long cap = (200LL * 1024 - xs) / kStages;
+  long long st = std::max<long long>(row, std::min<long long>(std::max<long long>(12 * 1024 / row, 1) * row, cap));
+  return (int)((st + 127) / 128 * 128);
+}
+
+template <typename T, int NRB>
+cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* arena, const double* X, double* Y,
+                    const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
+  using Acc = typename Op<T>::Acc;
+  const int stage_bytes = stage_size<T, NRB>(max_lda);
+  const size_t smem = (size_t)kStages * stage_bytes + 2 * (size_t)max_lda * NRB * sizeof(Acc) +
+                      2 * kStages * sizeof(uint64_t);
+  auto kern = k_bgemv_tma<T, NRB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (!g_num_sms) {
+    int dev;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, per_sm);
+  const int units = n_items * ((nrhs + NRB - 1) / NRB);
+  const int grid = std::max(1, std::min(units, g_num_sms * per_sm));
+  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, nrhs, stage_bytes, max_lda, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void* arena, const double* X, double* Y,
+                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
+  using Acc = typename Op<T>::Acc;
+  const T* A = static_cast<const T*>(arena);
+  const size_t row = ((size_t)max_lda * sizeof(T) + 127) / 128 * 128;
+  auto fits = [&](int nrb) { return kStages * row + 2 * (size_t)max_lda * nrb * sizeof(Acc) + 64 <= 200 * 1024; };
+  if (nrhs >= 8 && fits(8)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (nrhs >= 4 && fits(4)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (nrhs >= 2 && fits(2)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (fits(1)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool bgemv_tma_supported(int precision, int max_lda) {
+  const size_t eb = precision == BDDC_PREC_FP64 ? 8 : precision == BDDC_PREC_FP32 ? 4 : 2;
+  const size_t acc = precision == BDDC_PREC_FP64 ? 8 : 4;
+  const size_t row = ((size_t)max_lda * eb + 127) / 128 * 128;
+  return kStages * row + 2 * (size_t)max_lda * acc + 64 <= 200 * 1024;
+}
+
+cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
+                             const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
+                             cudaStream_t st) {
+  if (n_items == 0) return cudaSuccess;
+  switch (precision) {
+    case BDDC_PREC_FP64: return dispatch<double>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
+    case BDDC_PREC_FP32: return dispatch<float>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
+    default: return dispatch<__nv_bfloat16>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
+  }
+}
+
+}  // namespace bddc

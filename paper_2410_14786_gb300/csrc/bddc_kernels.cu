@@ -164,27 +164,6 @@ __global__ void k_iface_rhs(int64_t nG, int nrhs, const int32_t* __restrict__ pt
   }
 }
 
-// g[pos, k] = sum_l Phi_G^T[c, l] y'_G[l, k] (one warp per local constraint)
-__global__ void k_coarse_local(int64_t nC, int nrhs, const int32_t* __restrict__ csub,
-                               const int32_t* __restrict__ coff, const int32_t* __restrict__ goff,
-                               const int64_t* __restrict__ phit_off, const double* __restrict__ phit,
-                               const double* __restrict__ yG, double* __restrict__ g) {
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= nC) return;
-  const int s = csub[wid];
-  const int c = (int)(wid - coff[s]);
-  const int g0 = goff[s], nG = goff[s + 1] - g0;
-  const double* row = phit + phit_off[s] + (int64_t)c * nG;
-  for (int k = 0; k < nrhs; ++k) {
-    double acc = 0.0;
-    for (int l = lane; l < nG; l += 32) acc = fma(row[l], yG[(int64_t)(g0 + l) * nrhs + k], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) g[wid * nrhs + k] = acc;
-  }
-}
-
 // r_c[c, k] = sum over the local constraints that map to coarse dof c
 __global__ void k_coarse_gather(int64_t n_c, int nrhs, const int32_t* __restrict__ ptr,
                                 const int32_t* __restrict__ idx, const double* __restrict__ g,
@@ -200,14 +179,22 @@ __global__ void k_coarse_gather(int64_t n_c, int nrhs, const int32_t* __restrict
   }
 }
 
-// z[node] = sum over the copies q of the node: W_q (z_G[q] + Phi_G[q, :] u_c[R_c])
-__global__ void k_prolong(int64_t n_gu, int nrhs, const int32_t* __restrict__ gu_node,
-                          const int32_t* __restrict__ gu_ptr, const int32_t* __restrict__ gu_copy,
-                          const double* __restrict__ gw, const double* __restrict__ zG,
-                          const int64_t* __restrict__ phirow, const int32_t* __restrict__ gsub,
-                          const int32_t* __restrict__ coff, const int32_t* __restrict__ ccdof,
-                          const double* __restrict__ phi, const double* __restrict__ uc,
-                          double* __restrict__ z) {
+// u_c per local constraint (the values Phi_G multiplies in the prolongation)
+__global__ void k_coarse_scatter(int64_t nC, int nrhs, const int32_t* __restrict__ ccdof, const double* __restrict__ uc,
+                                 double* __restrict__ ucl) {
+  const int64_t total = nC * nrhs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i / nrhs;
+    ucl[i] = uc[(int64_t)ccdof[j] * nrhs + (i - j * nrhs)];
+  }
+}
+
+// z[node] = sum over the copies q of the node of W_q (z_G[q] + (Phi_G u_c)[q])
+__global__ void k_prolong_gather(int64_t n_gu, int nrhs, const int32_t* __restrict__ gu_node,
+                                 const int32_t* __restrict__ gu_ptr, const int32_t* __restrict__ gu_copy,
+                                 const double* __restrict__ gw, const double* __restrict__ zG,
+                                 const double* __restrict__ eG, double* __restrict__ z) {
   const int64_t total = n_gu * nrhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -215,13 +202,8 @@ __global__ void k_prolong(int64_t n_gu, int nrhs, const int32_t* __restrict__ gu
     const int k = (int)(i - u * nrhs);
     double v = 0.0;
     for (int j = gu_ptr[u]; j < gu_ptr[u + 1]; ++j) {
-      const int q = gu_copy[j];
-      const int s = gsub[q];
-      const int c0 = coff[s], nc = coff[s + 1] - c0;
-      const double* prow = phi + phirow[q];
-      double e = zG[(int64_t)q * nrhs + k];
-      for (int c = 0; c < nc; ++c) e = fma(prow[c], uc[(int64_t)ccdof[c0 + c] * nrhs + k], e);
-      v = fma(gw[q], e, v);
+      const int64_t q = (int64_t)gu_copy[j] * nrhs + k;
+      v = fma(gw[gu_copy[j]], zG[q] + eG[q], v);
     }
     z[(int64_t)gu_node[u] * nrhs + k] = v;
   }
@@ -240,6 +222,15 @@ __global__ void k_interior_rhs(int64_t nI, int nrhs, const int32_t* __restrict__
     double s = rI[i];
     for (int j = ptr[p]; j < ptr[p + 1]; ++j) s = fma(-val[j], z[(int64_t)col[j] * nrhs + k], s);
     bI[i] = s;
+  }
+}
+
+// u_c = sum of the per-panel partial products of A_c^-1 r_c
+__global__ void k_panel_sum(int64_t n, int npanels, const double* __restrict__ part, double* __restrict__ uc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < npanels; ++p) s += part[(int64_t)p * n + i];
+    uc[i] = s;
   }
 }
 
@@ -305,116 +296,6 @@ __global__ void k_q1_apply(int ne, int nrhs, const double* __restrict__ sigma, d
 // ---------------------------------------------------------------------------
 // PCG vector kernels
 // ---------------------------------------------------------------------------
-// per-column partial sums; block b writes partials[(b * 3 + slot) * nrhs + k]
-__global__ void k_dots(int64_t n_nodes, int nrhs, const double* __restrict__ a0, const double* __restrict__ b0,
-                       const double* __restrict__ a1, const double* __restrict__ b1,
-                       const double* __restrict__ a2, const double* __restrict__ b2,
-                       double* __restrict__ partials) {
-  __shared__ double red[3][kThreads];
-  const int per = kThreads / nrhs;         // nodes per block step
-  const int tid = threadIdx.x;
-  const bool live = tid < per * nrhs;
-  const int k = tid % nrhs, sub = tid / nrhs;
-  double s0 = 0, s1 = 0, s2 = 0;
-  if (live) {
-    for (int64_t nd = blockIdx.x * (int64_t)per + sub; nd < n_nodes; nd += (int64_t)gridDim.x * per) {
-      const int64_t i = nd * nrhs + k;
-      s0 = fma(a0[i], b0[i], s0);
-      if (a1) s1 = fma(a1[i], b1[i], s1);
-      if (a2) s2 = fma(a2[i], b2[i], s2);
-    }
-  }
-  red[0][tid] = s0; red[1][tid] = s1; red[2][tid] = s2;
-  __syncthreads();
-  if (tid < nrhs) {
-    double t0 = 0, t1 = 0, t2 = 0;
-    for (int j = 0; j < per; ++j) {
-      t0 += red[0][j * nrhs + tid];
-      t1 += red[1][j * nrhs + tid];
-      t2 += red[2][j * nrhs + tid];
-    }
-    partials[(blockIdx.x * 3 + 0) * nrhs + tid] = t0;
-    partials[(blockIdx.x * 3 + 1) * nrhs + tid] = t1;
-    partials[(blockIdx.x * 3 + 2) * nrhs + tid] = t2;
-  }
-}
-
-__global__ void k_finalize(int op, int nrhs, int nblocks, const double* __restrict__ partials,
-                           double* __restrict__ scal, int32_t* __restrict__ iscal, int nrhs_max,
-                           double rtol, int flexible) {
-  const int k = threadIdx.x;
-  double t[3] = {0, 0, 0};
-  if (k < nrhs)
-    for (int b = 0; b < nblocks; ++b)
-      for (int s = 0; s < 3; ++s) t[s] += partials[(b * 3 + s) * nrhs + k];
-  double* rho = scal + S_RHO * nrhs_max;
-  double* alpha = scal + S_ALPHA * nrhs_max;
-  double* beta = scal + S_BETA * nrhs_max;
-  double* bb = scal + S_BB * nrhs_max;
-  double* rr = scal + S_RR * nrhs_max;
-  double* relres = scal + S_RELRES * nrhs_max;
-  int32_t* active = iscal + I_ACTIVE * nrhs_max;
-  int32_t* iters = iscal + I_ITERS * nrhs_max;
-  int32_t* status = iscal + I_STATUS * nrhs_max;
-  int32_t* flags = iscal + I_COUNT * nrhs_max;      // [0] active count, [1] breakdown
-  __shared__ int cnt, brk;
-  if (k == 0) { cnt = 0; brk = 0; }
-  __syncthreads();
-  if (k < nrhs) {
-    if (op == FIN_INIT) {            // t0 = b.b, t1 = r.r
-      bb[k] = t[0]; rr[k] = t[1];
-      const double bn = sqrt(t[0]), rn = sqrt(t[1]);
-      relres[k] = bn > 0 ? rn / bn : 0.0;
-      active[k] = (bn > 0 && !(rn <= rtol * bn)) ? 1 : 0;
-      iters[k] = 0; status[k] = 0;
-      alpha[k] = 0; beta[k] = 0;
-    } else if (op == FIN_RHO) {      // t0 = r.z
-      rho[k] = t[0];
-    } else if (op == FIN_ALPHA) {    // t0 = p.q
-      if (active[k]) {
-        if (!(t[0] > 0.0) || !isfinite(t[0]) || !isfinite(rho[k])) {
-          active[k] = 0; status[k] = BDDC_ERR_BREAKDOWN; alpha[k] = 0; atomicAdd(&brk, 1);
-        } else {
-          alpha[k] = rho[k] / t[0];
-        }
-      } else {
-        alpha[k] = 0;
-      }
-    } else if (op == FIN_CONV) {     // t0 = r.r
-      if (active[k]) {
-        iters[k] += 1;
-        rr[k] = t[0];
-        const double bn = sqrt(bb[k]), rn = sqrt(t[0]);
-        relres[k] = rn / bn;
-        if (rn <= rtol * bn) active[k] = 0;
-        else if (!isfinite(rn)) { active[k] = 0; status[k] = BDDC_ERR_BREAKDOWN; atomicAdd(&brk, 1); }
-      }
-    } else if (op == FIN_BETA) {     // t0 = r.z_new, t1 = r.z_old
-      if (active[k]) {
-        const double num = flexible ? t[0] - t[1] : t[0];
-        beta[k] = num / rho[k];
-        rho[k] = t[0];
-      } else {
-        beta[k] = 0;
-      }
-    }
-    if (active[k]) atomicAdd(&cnt, 1);
-  }
-  __syncthreads();
-  if (k == 0) { flags[0] = cnt; flags[1] = brk; }
-}
-
-__global__ void k_update_xr(int64_t n, int nrhs, const double* __restrict__ alpha, const double* __restrict__ p,
-                            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
-  const int64_t total = n * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = alpha[i % nrhs];
-    x[i] = fma(a, p[i], x[i]);
-    r[i] = fma(-a, q[i], r[i]);
-  }
-}
-
 __global__ void k_update_p(int64_t n, int nrhs, const double* __restrict__ beta, const double* __restrict__ z,
                            double* __restrict__ p, double* __restrict__ zold) {
   const int64_t total = n * nrhs;
@@ -467,6 +348,19 @@ cudaError_t bgemv(int precision, const WorkItem* items, int n_items, int max_lda
   }
 }
 
+// One batched application of the interior (A_II^-1) or interface (K_GG)
+// operators of all subdomains.
+cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
+                     cudaStream_t st) {
+  if (h->use_tma)
+    return interior ? launch_bgemv_tma(h->precision, h->d_wt_I, h->n_wt_I, h->max_cols_I, h->d_aii, X, Y, yscatter,
+                                       nrhs, h->d_err, st)
+                    : launch_bgemv_tma(h->precision, h->d_wt_G, h->n_wt_G, h->max_cols_G, h->d_kgg, X, Y, yscatter,
+                                       nrhs, h->d_err, st);
+  return interior ? bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, X, Y, yscatter, nrhs, st)
+                  : bgemv(h->precision, h->d_wi_G, h->n_wi_G, h->max_cols_G, h->d_kgg, X, Y, yscatter, nrhs, st);
+}
+
 }  // namespace
 
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,
@@ -477,8 +371,7 @@ cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double
                                                                 h->n_dir, x);
   if (h->n_gu)
     k_zero_nodes<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, x);
-  cudaError_t e = bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, h->w_rI, x,
-                        h->d_inode, nrhs, st);
+  cudaError_t e = local_op(h, true, h->w_rI, x, h->d_inode, nrhs, st);
   h->launches += 1 + (h->n_gu > 0) + (h->n_wi_I > 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -498,9 +391,7 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   h->launches++;
   mark(1);
   // t_I = A_II^-1 r_I
-  if ((e = bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, h->w_rI, h->w_tI, nullptr,
-                 nrhs, st)) != cudaSuccess)
-    return e;
+  if ((e = local_op(h, true, h->w_rI, h->w_tI, nullptr, nrhs, st)) != cudaSuccess) return e;
   h->launches += h->n_wi_I > 0;
   mark(2);
   if (h->nG_tot) {
@@ -512,35 +403,46 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   }
   mark(3);
   if (h->nG_tot) {
-    if ((e = bgemv(h->precision, h->d_wi_G, h->n_wi_G, h->max_cols_G, h->d_kgg, h->w_yG, h->w_zG, nullptr,
-                   nrhs, st)) != cudaSuccess)
-      return e;
+    if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, st)) != cudaSuccess) return e;
     h->launches++;
   }
   mark(4);
   if (h->n_c) {
     // coarse residual r_c = sum R_ci^T Phi_G^T y'_G
-    k_coarse_local<<<blocks_for(h->nC_tot * 32), kThreads, 0, st>>>(h->nC_tot, nrhs, h->d_csub, h->d_sub_coff,
-                                                                    h->d_sub_goff, h->d_sub_phit_off, h->d_phit,
-                                                                    h->w_yG, h->w_g);
+    if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, h->w_yG, h->w_g,
+                              nullptr, nrhs, h->d_err, st)) != cudaSuccess)
+      return e;
     k_coarse_gather<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx,
                                                                     h->w_g, h->w_rc);
     h->launches += 2;
   }
   mark(5);
   if (h->n_c) {
-    // u_c = A_c^-1 r_c
-    if ((e = bgemv(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, h->w_rc, h->w_uc, nullptr, nrhs,
-                   st)) != cudaSuccess)
+    // u_c = A_c^-1 r_c: per-panel products, then their sum
+    if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, h->w_rc, h->w_cpart,
+                              nullptr, nrhs, h->d_err, st)) != cudaSuccess)
       return e;
-    h->launches++;
+    k_panel_sum<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c * nrhs, h->n_cpanels, h->w_cpart, h->w_uc);
+    h->launches += 2;
   }
   mark(6);
   if (h->n_gu) {
-    k_prolong<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr,
-                                                               h->d_gu_copy, h->d_gw, h->w_zG, h->d_gcopy_phirow,
-                                                               h->d_gcopy_sub, h->d_sub_coff, h->d_ccdof,
-                                                               h->d_phi, h->w_uc, z);
+    // v_G = sum R^T W (z_G + Phi_G u_c)
+    const double* eG = nullptr;
+    if (h->n_c) {
+      k_coarse_scatter<<<blocks_for(h->nC_tot * nrhs), kThreads, 0, st>>>(h->nC_tot, nrhs, h->d_ccdof, h->w_uc,
+                                                                          h->w_ucl);
+      if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_P, h->n_wi_P, h->max_ld_P, h->d_phi, h->w_ucl, h->w_eG,
+                                nullptr, nrhs, h->d_err, st)) != cudaSuccess)
+        return e;
+      eG = h->w_eG;
+      h->launches += 2;
+    } else {
+      cudaMemsetAsync(h->w_eG, 0, sizeof(double) * h->nG_tot * nrhs, st);
+      eG = h->w_eG;
+    }
+    k_prolong_gather<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr,
+                                                                      h->d_gu_copy, h->d_gw, h->w_zG, eG, z);
     h->launches++;
   }
   mark(7);
@@ -550,9 +452,7 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
                                                                     h->w_bI);
   h->launches++;
   mark(8);
-  if ((e = bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, h->w_bI, z, h->d_inode, nrhs,
-                 st)) != cudaSuccess)
-    return e;
+  if ((e = local_op(h, true, h->w_bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
   h->launches += h->n_wi_I > 0;
   mark(9);
   return cudaGetLastError();
@@ -568,18 +468,6 @@ static void q1_coefs(int dim, double h, bool mass, double c[4]) {
   }
 }
 
-cudaError_t launch_matvec(bddc_handle_s* h, const double* x, double* y, int nrhs, cudaStream_t st) {
-  double c[4];
-  q1_coefs(h->dim, h->h, false, c);
-  if (h->dim == 2)
-    k_q1_apply<2><<<blocks_for(h->n_nodes), kThreads, 0, st>>>(h->ne, nrhs, h->d_sigma, c[0], c[1], c[2], c[3],
-                                                               1, 1, x, y);
-  else
-    k_q1_apply<3><<<blocks_for(h->n_nodes), kThreads, 0, st>>>(h->ne, nrhs, h->d_sigma, c[0], c[1], c[2], c[3],
-                                                               1, 1, x, y);
-  h->launches++;
-  return cudaGetLastError();
-}
 
 cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, cudaStream_t st) {
   double c[4];
@@ -594,26 +482,8 @@ cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_dots(bddc_handle_s* h, int nrhs, const double* a0, const double* b0, const double* a1,
-                        const double* b1, const double* a2, const double* b2, cudaStream_t st) {
-  k_dots<<<h->n_red_blocks, kThreads, 0, st>>>(h->n_nodes, nrhs, a0, b0, a1, b1, a2, b2, h->d_partials);
-  h->launches++;
-  return cudaGetLastError();
-}
 
-cudaError_t launch_finalize(bddc_handle_s* h, int op, int nrhs, double rtol, int flexible, cudaStream_t st) {
-  k_finalize<<<1, 64, 0, st>>>(op, nrhs, h->n_red_blocks, h->d_partials, h->d_scal, h->d_iscal, h->nrhs_max,
-                               rtol, flexible);
-  h->launches++;
-  return cudaGetLastError();
-}
 
-cudaError_t launch_update_xr(bddc_handle_s* h, double* x, int nrhs, cudaStream_t st) {
-  k_update_xr<<<blocks_for(h->n_nodes * nrhs), kThreads, 0, st>>>(h->n_nodes, nrhs, h->d_scal + S_ALPHA * h->nrhs_max,
-                                                                  h->p_p, h->p_q, x, h->p_r);
-  h->launches++;
-  return cudaGetLastError();
-}
 
 cudaError_t launch_update_p(bddc_handle_s* h, int nrhs, cudaStream_t st) {
   k_update_p<<<blocks_for(h->n_nodes * nrhs), kThreads, 0, st>>>(h->n_nodes, nrhs, h->d_scal + S_BETA * h->nrhs_max,

@@ -1,6 +1,8 @@
 // Internal state of a libbddc handle (host side and device side).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -79,10 +81,12 @@ struct bddc_handle_s {
   int32_t* d_agi_ptr = nullptr; int32_t* d_agi_col = nullptr; double* d_agi_val = nullptr;
   // A_IG: rows = compact interior positions, cols = node ids (interface nodes)
   int32_t* d_aig_ptr = nullptr; int32_t* d_aig_col = nullptr; double* d_aig_val = nullptr;
-  // Phi_Gamma^T rows, per subdomain [nc x nG] (coarse residual) and
-  // Phi_Gamma rows [nG x nc] (prolongation), float64
-  double* d_phit = nullptr; double* d_phi = nullptr;
-  int64_t* d_sub_phit_off = nullptr;  // [n_sub] element offset of Phi^T block
+  // Phi_Gamma^T [nc x nG] (coarse residual) and Phi_Gamma [nG x nc]
+  // (prolongation) per subdomain, float64, with their work lists
+  double* d_phit = nullptr;
+  double* d_phi = nullptr;
+  bddc::WorkItem* d_wi_PT = nullptr; int n_wi_PT = 0; int max_ld_PT = 0;
+  bddc::WorkItem* d_wi_P = nullptr; int n_wi_P = 0; int max_ld_P = 0;
   int32_t* d_sub_goff = nullptr;      // [n_sub + 1] interface copy offsets
   int32_t* d_sub_coff = nullptr;      // [n_sub + 1] local constraint offsets
   int32_t* d_csub = nullptr;          // [nC_tot] subdomain of each local constraint
@@ -91,20 +95,27 @@ struct bddc_handle_s {
   int32_t* d_cg_ptr = nullptr; int32_t* d_cg_idx = nullptr;
   // prolongation: per unique interface node, its copies
   int32_t* d_gu_node = nullptr; int32_t* d_gu_ptr = nullptr; int32_t* d_gu_copy = nullptr;
-  int64_t* d_gcopy_phirow = nullptr;  // [nG_tot] element offset of the copy's Phi row
-  int32_t* d_gcopy_sub = nullptr;     // [nG_tot] subdomain of the copy
   // operators
   void* d_aii = nullptr;              // interior inverses, precision-typed arena
   void* d_kgg = nullptr;              // interface operators, precision-typed arena
-  double* d_acinv = nullptr;          // coarse inverse, float64, n_c x ldc
-  int32_t ldc = 0;
+  double* d_acinv = nullptr;          // coarse inverse, float64, in column panels
+  int32_t ldc = 0;                    // panel width (columns), the last panel may be narrower
+  int32_t n_cpanels = 0;              // number of column panels of A_c^-1
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
+  // larger row tiles for the streamed (bulk-copy) GEMV
+  bddc::WorkItem* d_wt_I = nullptr; int n_wt_I = 0;
+  bddc::WorkItem* d_wt_G = nullptr; int n_wt_G = 0;
+  bool use_tma = false;
   bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
   int max_cols_I = 0, max_cols_G = 0;
+  int max_nc = 0;                     // most constraints of one subdomain
   // apply workspace (nrhs_max columns)
   double *w_rI = nullptr, *w_tI = nullptr, *w_bI = nullptr;
   double *w_yG = nullptr, *w_zG = nullptr, *w_g = nullptr, *w_rc = nullptr, *w_uc = nullptr;
+  double* w_cpart = nullptr;          // per-panel partial coarse solutions
+  double* w_eG = nullptr;             // Phi_G u_c per interface copy
+  double* w_ucl = nullptr;            // u_c per local constraint
   // PCG workspace
   double *p_r = nullptr, *p_z = nullptr, *p_zold = nullptr, *p_p = nullptr, *p_q = nullptr;
   double *s_b = nullptr, *s_x = nullptr;   // staging for host-buffer solves
@@ -112,7 +123,17 @@ struct bddc_handle_s {
   double* d_scal = nullptr;                // per-column PCG scalars
   int32_t* d_iscal = nullptr;              // per-column flags / counters
   int32_t* h_flags = nullptr;              // pinned host mirror of the global flags
+  int32_t* d_err = nullptr;                // device error flag (inside d_iscal)
   int n_red_blocks = 0;
+  double* d_stencil = nullptr;             // [stencil points][n_nodes] assembled Q1 stencil
+  unsigned int* d_counter = nullptr;       // blocks finished in the current reducing kernel
+  // one PCG iteration captured as a CUDA graph, valid for (x, nrhs, rtol, form)
+  cudaGraphExec_t iter_graph = nullptr;
+  const double* graph_x = nullptr;
+  int graph_nrhs = 0, graph_flexible = -1;
+  double graph_rtol = 0.0;
+  int64_t graph_launches = 0;              // kernels in one replay
+  cudaStream_t cap_stream = nullptr;       // private stream used only for capture
   int64_t launches = 0;                    // kernels launched so far
   std::vector<void*> allocations;
 };

@@ -14,38 +14,49 @@ namespace bddc {
 cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs, cudaStream_t st,
                          cudaEvent_t* prof_events = nullptr);
 
+// Batched GEMV over row tiles of many operators, streamed by bulk async
+// copies through shared memory (bddc_bgemv_tma.cu). err receives
+// BDDC_ERR_TIMEOUT if a bounded wait runs out.
+bool bgemv_tma_supported(int precision, int max_lda);
+cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
+                             const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
+                             cudaStream_t st);
+
 // x = P_I b: interior correction of b (zero on interface and Dirichlet nodes).
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,
                                        cudaStream_t st);
 
-// y = A x (matrix-free Q1 stiffness on the free nodes).
-cudaError_t launch_matvec(bddc_handle_s* h, const double* x, double* y, int nrhs, cudaStream_t st);
-
-// b = (M f) on the free nodes.
+// b = (M f) on the free nodes (matrix-free Q1 mass matrix).
 cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, cudaStream_t st);
 
-// Partial per-column sums of up to three elementwise products over all
-// nodes, into h->d_partials[block][slot][k].
-cudaError_t launch_dots(bddc_handle_s* h, int nrhs, const double* a0, const double* b0,
-                        const double* a1, const double* b1, const double* a2, const double* b2,
-                        cudaStream_t st);
-
-// PCG scalar updates (one block; fixed summation order over the partials).
+// PCG scalar updates applied by the last block of a reducing kernel.
 enum FinalizeOp { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3, FIN_BETA = 4 };
-cudaError_t launch_finalize(bddc_handle_s* h, int op, int nrhs, double rtol, int flexible,
-                            cudaStream_t st);
 
-// x += alpha p; r -= alpha q (per-column alpha on the device).
-cudaError_t launch_update_xr(bddc_handle_s* h, double* x, int nrhs, cudaStream_t st);
+// Global SpMV (bddc_pcg.cu): coefficients of the assembled Q1 stencil,
+// built once per handle; y = A x, and with op >= 0 also x.y per column
+// followed by the PCG scalar update `op`.
+int stencil_points(int dim);
+cudaError_t launch_build_stencil(bddc_handle_s* h, cudaStream_t st);
+cudaError_t launch_spmv(bddc_handle_s* h, const double* x, double* y, int nrhs, int op, double rtol, int flexible,
+                        cudaStream_t st);
+// x += alpha p; r -= alpha q; r.r; stop test.
+cudaError_t launch_update_xr_conv(bddc_handle_s* h, double* x, int nrhs, double rtol, int flexible,
+                                  cudaStream_t st);
+// a0.b0 (and a1.b1) per column, then the PCG scalar update `op`.
+cudaError_t launch_dots_fin(bddc_handle_s* h, int nrhs, const double* a0, const double* b0, const double* a1,
+                            const double* b1, int op, double rtol, int flexible, cudaStream_t st);
+
 // p = z + beta p; zold = z.
 cudaError_t launch_update_p(bddc_handle_s* h, int nrhs, cudaStream_t st);
-// r = b - q (initial residual, q = A x0).
+// r = b - q; p = 0; zold = 0 (start of PCG, q = A x0).
 cudaError_t launch_residual(bddc_handle_s* h, const double* b, int nrhs, cudaStream_t st);
 
 // Offsets of the per-column PCG scalars inside h->d_scal (times nrhs_max).
 enum ScalarSlot { S_RHO = 0, S_ALPHA, S_BETA, S_BB, S_RR, S_RELRES, S_COUNT };
 enum IntSlot { I_ACTIVE = 0, I_ITERS, I_STATUS, I_COUNT };
-// global int flags after the per-column ones: [0] active columns, [1] breakdown
+// global int flags after the per-column ones: [0] active columns, [1] breakdown,
+// [2] device error (BDDC_ERR_TIMEOUT from a bounded wait), sticky until setup
+constexpr int kGlobalFlags = 3;
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs for the dot-product partials
 
 }  // namespace bddc
