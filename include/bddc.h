@@ -73,6 +73,15 @@ extern "C" {
 #define BDDC_PREC_FP32  1   /* float32 operators, float32 accumulation */
 #define BDDC_PREC_BF16  2   /* bfloat16 operators, float32 accumulation */
 
+/* Coarse solve (always exact, float64). DENSE: the explicit inverse of A_c,
+ * applied as one matrix-vector product (n_c^2 float64 multiply-adds).
+ * SPARSE: a nested-dissection supernodal Cholesky factorisation applied by
+ * level-scheduled sweeps (far fewer operations and bytes; needed when the
+ * dense inverse does not fit). AUTO: DENSE up to n_c = 16384, else SPARSE. */
+#define BDDC_COARSE_AUTO    0
+#define BDDC_COARSE_DENSE   1
+#define BDDC_COARSE_SPARSE  2
+
 /* Constraint families that become coarse (primal) dofs (Sec. 2). */
 #define BDDC_CORNERS 1u
 #define BDDC_EDGES   2u
@@ -94,6 +103,7 @@ typedef struct {
     int32_t nrhs_max;      /* largest nrhs any later call uses, 1..64 */
     int32_t n_threads;     /* host threads for setup; 0 = all cores */
     int32_t device;        /* CUDA device ordinal */
+    int32_t coarse;        /* BDDC_COARSE_* */
 } bddc_options_t;
 
 typedef struct {
@@ -111,6 +121,10 @@ typedef struct {
     int64_t interface_op_bytes;         /* bytes of all K_GG blocks as stored */
     int64_t n_interface_copies;         /* sum over subdomains of interface nodes */
     int64_t kernel_launches;            /* kernels launched by this handle so far */
+    int64_t coarse_factor_entries;      /* stored entries of the coarse operator (dense inverse
+                                           or the sparse factor's sweep matrices) */
+    int64_t coarse_update_total;        /* sum of the coarse supernodes' update-set sizes */
+    int64_t coarse_levels;              /* levels of the coarse elimination tree (0: dense) */
     double setup_seconds;               /* wall time of bddc_setup */
     int32_t precision;
     int32_t error_subdomain;            /* subdomain of the last SINGULAR error, else -1 */
@@ -141,8 +155,10 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * libraries, or a program that fixes all device memory at start-up. The call
  * itself never calls cudaMalloc, cudaFree or any allocating routine.
  * Limit: the temporaries of one apply, (3 n_interior + 3 n_interface_copies
- * + 2 sum n_ci + (2 + ceil(n_c / 512)) n_c) * nrhs doubles, each term rounded
- * up to 32, must not exceed 2^20; larger problems get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
+ * + 2 sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
+ * the dense coarse solve and 2 n_c + coarse_update_total for the sparse one
+ * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
+ * larger problems get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current); make
  * that first call before any stream capture. Every call on every handle of
  * a device shares the one array, and no part of it needs to start at zero

@@ -18,6 +18,7 @@ from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64,  # no
                    BDDCError)
 
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16}
+COARSE = {"auto": _lib.COARSE_AUTO, "dense": _lib.COARSE_DENSE, "sparse": _lib.COARSE_SPARSE}
 
 
 @dataclass
@@ -48,11 +49,12 @@ class BDDC:
     Parameters mirror `bddc_problem_t` / `bddc_options_t`: dim, ne,
     elem_sigma [ne^dim] float64 > 0, elem_subdomain [ne^dim] int32,
     n_sub; precision in {"fp64", "fp32", "bf16"}; constraints bitmask of
-    CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup.
+    CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup;
+    coarse in {"auto", "dense", "sparse"} (exact float64 coarse solve either way).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
-                 constraints=0, nrhs_max=1, n_threads=0, device=None):
+                 constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto"):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -63,7 +65,8 @@ class BDDC:
         prob = _lib.Problem(int(dim), int(ne), sig.ctypes.data_as(C.POINTER(C.c_double)),
                             part.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub))
         opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                            int(constraints), int(nrhs_max), int(n_threads), int(device))
+                            int(constraints), int(nrhs_max), int(n_threads), int(device),
+                            COARSE[coarse] if isinstance(coarse, str) else int(coarse))
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim

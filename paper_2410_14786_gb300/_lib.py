@@ -23,6 +23,7 @@ ERR_NO_DEVICE = -7
 
 PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
 CORNERS, EDGES, FACES = 1, 2, 4
+COARSE_AUTO, COARSE_DENSE, COARSE_SPARSE = 0, 1, 2
 
 EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
@@ -39,7 +40,7 @@ class Problem(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
-                ("n_threads", C.c_int32), ("device", C.c_int32)]
+                ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -47,7 +48,8 @@ class Info(C.Structure):
         "n_nodes", "n_free", "n_interior", "n_interface_nodes", "n_sub", "n_c",
         "n_corners", "n_edges", "n_faces", "sum_ni", "sum_nI2", "sum_nG2", "sum_nG_nc",
         "max_ni", "operator_bytes", "coarse_bytes", "device_bytes", "apply_bytes_1rhs",
-        "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches")] + [
+        "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches",
+        "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
         ("device_error", C.c_int32)]
 

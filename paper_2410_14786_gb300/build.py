@@ -14,8 +14,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbddc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["bddc_kernels.cu", "bddc_bgemv_tma.cu", "bddc_pcg.cu", "bddc_api.cu", "bddc_static_scratch.cu"]
-CXX_SOURCES = ["bddc_setup.cpp"]
+CU_SOURCES = ["bddc_kernels.cu", "bddc_bgemv_tma.cu", "bddc_pcg.cu", "coarse_solve.cu", "bddc_api.cu",
+              "bddc_static_scratch.cu"]
+CXX_SOURCES = ["bddc_setup.cpp", "coarse_sparse.cpp"]
 HEADERS = ["dense.hpp", "internal.hpp", "kernels.cuh"]
 
 

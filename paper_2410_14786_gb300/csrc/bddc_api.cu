@@ -269,11 +269,12 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     CUDA_TRY(upload(h, &h->d_wt_I, tI));
     CUDA_TRY(upload(h, &h->d_wt_G, tG));
   }
-  // coarse inverse, float64, stored as column panels of kPanel columns (each
-  // an n_c x width row-major block, blocks aligned to 256 bytes); the panels'
-  // partial products are summed by a separate kernel
-  std::vector<WorkItem> itC;
-  if (hs.n_c) {
+  h->coarse_dense = hs.coarse_dense;
+  if (hs.n_c && hs.coarse_dense) {
+    // A_c^-1, float64, stored as column panels of kPanel columns (each an
+    // n_c x width row-major block, blocks aligned to 256 bytes); the panels'
+    // partial products are summed by a separate kernel
+    std::vector<WorkItem> itC;
     const int kPanel = 512;
     const int nc = (int)hs.n_c;
     h->ldc = kPanel;
@@ -293,15 +294,21 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       for (int r = 0; r < nc; ++r)
         std::memcpy(&ac[poff[p] + (int64_t)r * pld[p]], &hs.Acinv[(size_t)r * nc + (size_t)p * kPanel],
                     sizeof(double) * pw[p]);
+    std::vector<double>().swap(hs.Acinv);
     CUDA_TRY(upload(h, &h->d_acinv, ac));
-    in_coarse_bytes = (int64_t)cur * 8;
+    in_coarse_bytes = cur * 8;
+    h->c_nnz = cur;
     const int ctile = 128;
     for (int p = 0; p < h->n_cpanels; ++p)
       for (int r0 = 0; r0 < nc; r0 += ctile)
         itC.push_back(WorkItem{poff[p], pld[p], pw[p], r0, std::min(ctile, nc - r0), p * kPanel, p * nc});
+    h->n_wi_C = (int)itC.size();
+    CUDA_TRY(upload(h, &h->d_wi_C, itC));
+  } else if (hs.n_c) {
+    // sparse Cholesky factorisation of A_c: supernode matrices and level lists
+    CUDA_TRY(build_coarse_device(h, hs.cfac));
+    in_coarse_bytes = h->c_nnz * 8;
   }
-  h->n_wi_C = (int)itC.size();
-  CUDA_TRY(upload(h, &h->d_wi_C, itC));
   // ---- index arrays -----------------------------------------------------------------
   std::vector<double> sigma(P->elem_sigma, P->elem_sigma + hs.n_elems);
   CUDA_TRY(upload(h, &h->d_sigma, sigma));
@@ -341,7 +348,13 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(dev_alloc(h, &h->w_g, h->nC_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w_rc, h->n_c * R));
   CUDA_TRY(dev_alloc(h, &h->w_uc, h->n_c * R));
-  CUDA_TRY(dev_alloc(h, &h->w_cpart, (int64_t)std::max(1, h->n_cpanels) * h->n_c * R));
+  if (h->coarse_dense) {
+    CUDA_TRY(dev_alloc(h, &h->w_cpart, (int64_t)std::max(1, h->n_cpanels) * h->n_c * R));
+  } else {
+    CUDA_TRY(dev_alloc(h, &h->w_cr, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w_cy, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w_cc, std::max<int64_t>(1, h->c_update_total) * R));
+  }
   CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   const int64_t NV = h->n_nodes * R;
@@ -397,6 +410,9 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     in.interface_op_bytes += (int64_t)dG[s] * ldG[s] * eb;
   }
   in.n_interface_copies = h->nG_tot;
+  in.coarse_factor_entries = h->c_nnz;
+  in.coarse_update_total = h->c_update_total;
+  in.coarse_levels = h->coarse_dense ? 0 : h->c_levels;
   ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
   in.apply_bytes_1rhs = ops + 2 * 8 * in.sum_nG_nc + in.coarse_bytes +
                         (int64_t)(agi_val.size() + aig_val.size()) * 12 + 8 * (in.n_free + hs.n_nodes);
@@ -526,7 +542,9 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
   }
   if (Ac && numerics) {
     if (hs.n_c * hs.n_c > Ac_capacity) return fail(BDDC_ERR_INVALID_ARG, "Ac capacity too small");
-    std::memcpy(Ac, hs.Acinv.data(), sizeof(double) * hs.n_c * hs.n_c);
+    std::fill(Ac, Ac + hs.n_c * hs.n_c, 0.0);
+    for (int64_t r = 0; r < hs.n_c; ++r)
+      for (int64_t j = hs.Ac_ptr[r]; j < hs.Ac_ptr[r + 1]; ++j) Ac[r * hs.n_c + hs.Ac_col[j]] = hs.Ac_val[j];
   }
   return BDDC_OK;
 }

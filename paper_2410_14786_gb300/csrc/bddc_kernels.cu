@@ -418,12 +418,18 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   }
   mark(5);
   if (h->n_c) {
-    // u_c = A_c^-1 r_c: per-panel products, then their sum
-    if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, h->w_rc, h->w_cpart,
-                              nullptr, nrhs, h->d_err, st)) != cudaSuccess)
-      return e;
-    k_panel_sum<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c * nrhs, h->n_cpanels, h->w_cpart, h->w_uc);
-    h->launches += 2;
+    if (h->coarse_dense) {
+      // u_c = A_c^-1 r_c: per-panel products of the explicit inverse, then their sum
+      if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, h->w_rc, h->w_cpart,
+                                nullptr, nrhs, h->d_err, st)) != cudaSuccess)
+        return e;
+      k_panel_sum<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c * nrhs, h->n_cpanels, h->w_cpart,
+                                                                  h->w_uc);
+      h->launches += 2;
+    } else {
+      // u_c = A_c^-1 r_c: sparse Cholesky forward and backward sweeps
+      if ((e = launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st)) != cudaSuccess) return e;
+    }
   }
   mark(6);
   if (h->n_gu) {

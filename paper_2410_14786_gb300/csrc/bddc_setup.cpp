@@ -69,6 +69,7 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
   if (O->precision < BDDC_PREC_FP64 || O->precision > BDDC_PREC_BF16) { err = "unknown precision"; return BDDC_ERR_INVALID_ARG; }
   if (O->nrhs_max < 1 || O->nrhs_max > 64) { err = "nrhs_max must be in [1, 64]"; return BDDC_ERR_INVALID_ARG; }
   if (O->constraints & ~7u) { err = "unknown constraint bits"; return BDDC_ERR_INVALID_ARG; }
+  if (O->coarse < BDDC_COARSE_AUTO || O->coarse > BDDC_COARSE_SPARSE) { err = "unknown coarse mode"; return BDDC_ERR_INVALID_ARG; }
   const int64_t ne = P->ne;
   const int64_t n_el = P->dim == 2 ? ne * ne : ne * ne * ne;
   for (int64_t e = 0; e < n_el; ++e) {
@@ -86,7 +87,7 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
 }
 
 int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, std::string& err,
-               bool invert_coarse, bool numerics) {
+               bool factor_coarse, bool numerics) {
   const int dim = P->dim, ne = P->ne;
   hs.dim = dim; hs.ne = ne; hs.n1 = ne + 1;
   const int64_t n1 = ne + 1;
@@ -340,19 +341,63 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
     return BDDC_ERR_SINGULAR;
   }
 
-  // ---- coarse matrix and its inverse ------------------------------------------
+  // ---- coarse matrix (sparse) and its factorisation -------------------------------
   const int64_t nC = hs.n_c;
   if (nC > 0) {
-    hs.Acinv.assign((size_t)nC * nC, 0.0);
-    for (int s = 0; s < hs.n_sub; ++s) {
-      const auto& gl = hs.sub_globs[s];
-      const int nc = (int)gl.size();
-      for (int r = 0; r < nc; ++r)
-        for (int c = 0; c < nc; ++c) hs.Acinv[(size_t)gl[r] * nC + gl[c]] += hs.Aci[s][(size_t)r * nc + c];
+    // CSR of A_c = sum_i R_ci^T A_ci R_ci: rows gathered from the subdomains
+    // holding each coarse dof, duplicates summed
+    std::vector<std::vector<int32_t>> dof_subs(nC);
+    for (int s = 0; s < hs.n_sub; ++s)
+      for (int r = 0; r < (int)hs.sub_globs[s].size(); ++r) dof_subs[hs.sub_globs[s][r]].push_back(s);
+    hs.Ac_ptr.assign(nC + 1, 0);
+    std::vector<int32_t> where(nC, -1);
+    std::vector<int32_t> cols;
+    std::vector<double> vals;
+    for (int64_t g = 0; g < nC; ++g) {
+      cols.clear();
+      vals.clear();
+      for (int s : dof_subs[g]) {
+        const auto& gl = hs.sub_globs[s];
+        const int nc = (int)gl.size();
+        const int r = (int)(std::lower_bound(gl.begin(), gl.end(), (int32_t)g) - gl.begin());
+        for (int c = 0; c < nc; ++c) {
+          const int32_t w = gl[c];
+          if (where[w] < 0) { where[w] = (int32_t)cols.size(); cols.push_back(w); vals.push_back(0.0); }
+          vals[where[w]] += hs.Aci[s][(size_t)r * nc + c];
+        }
+      }
+      std::vector<int> idx(cols.size());
+      std::iota(idx.begin(), idx.end(), 0);
+      std::sort(idx.begin(), idx.end(), [&](int a, int b) { return cols[a] < cols[b]; });
+      for (int i : idx) {
+        hs.Ac_col.push_back(cols[i]);
+        hs.Ac_val.push_back(vals[i]);
+        where[cols[i]] = -1;
+      }
+      hs.Ac_ptr[g + 1] = (int64_t)hs.Ac_col.size();
     }
-    if (invert_coarse && dense::spd_inverse((int)nC, hs.Acinv.data(), nC, threads) >= 0) {
-      err = "coarse matrix A_c is not positive definite";
-      return BDDC_ERR_SINGULAR;
+    hs.coarse_dense = O->coarse == BDDC_COARSE_DENSE || (O->coarse == BDDC_COARSE_AUTO && nC <= 16384);
+    if (factor_coarse && hs.coarse_dense) {
+      hs.Acinv.assign((size_t)nC * nC, 0.0);
+      for (int64_t r = 0; r < nC; ++r)
+        for (int64_t j = hs.Ac_ptr[r]; j < hs.Ac_ptr[r + 1]; ++j) hs.Acinv[(size_t)r * nC + hs.Ac_col[j]] = hs.Ac_val[j];
+      if (dense::spd_inverse((int)nC, hs.Acinv.data(), nC, threads) >= 0) {
+        err = "coarse matrix A_c is not positive definite";
+        return BDDC_ERR_SINGULAR;
+      }
+    } else if (factor_coarse) {
+      // glob centroids in grid units for the nested dissection
+      std::vector<double> xyz(3 * nC, 0.0);
+      for (int64_t g = 0; g < nC; ++g) {
+        for (int32_t nd : hs.glob_nodes[g]) {
+          xyz[3 * g] += (double)(nd % n1);
+          xyz[3 * g + 1] += (double)((nd / n1) % n1);
+          xyz[3 * g + 2] += dim == 3 ? (double)(nd / (n1 * n1)) : 0.0;
+        }
+        for (int d = 0; d < 3; ++d) xyz[3 * g + d] /= (double)hs.glob_nodes[g].size();
+      }
+      const int rc = coarse_factor(nC, hs.Ac_ptr, hs.Ac_col, hs.Ac_val, xyz, hs.cfac, err);
+      if (rc != BDDC_OK) return rc;
     }
   }
   return BDDC_OK;

@@ -11,6 +11,22 @@
 
 namespace bddc {
 
+// One row tile of one supernode matrix in a coarse-solve level launch.
+struct CItem {
+  int64_t moff;     // element offset of the node's matrix
+  int32_t node;     // supernode index
+  int32_t ld;       // leading dimension (even, 16-byte rows)
+  int32_t ncols;    // operand length (p forward, p+u backward)
+  int32_t row0, nrows;
+  int32_t pad;
+};
+struct CNodeDev {
+  int32_t p, u;     // pivots, update-set size
+  int32_t piv_off;  // offset of the node's pivot dofs
+  int32_t upd_off;  // offset of the node's update dofs
+  int32_t c_off;    // offset of the node's contributions
+};
+
 // One row tile of one dense operator in a batched GEMV launch:
 // Y[yoff + row0 + r] = sum_c Op[row0 + r, c] * X[xoff + c], r < nrows.
 struct WorkItem {
@@ -22,6 +38,27 @@ struct WorkItem {
   int32_t xoff;    // first entry of the operand in the compact X buffer
   int32_t yoff;    // first entry of the result in the compact Y buffer
 };
+
+// One supernode of the sparse Cholesky factorisation of A_c (coarse_sparse.cpp).
+struct CoarseNode {
+  std::vector<int32_t> piv;     // pivot coarse dofs (the separator, or a leaf's set)
+  std::vector<int32_t> upd;     // update set: later coarse dofs coupled to the subtree
+  std::vector<int> children;
+  int parent = -1, first = 0, last = -1, height = 0, p = 0, u = 0;
+  std::vector<double> Fm;       // (p+u) x p: [L_PP^-1 ; M],   M = L_UP L_PP^-1
+  std::vector<double> Bm;       // p x (p+u): [L_PP^-T , -M^T]
+};
+struct CoarseFactor {
+  int64_t n = 0;
+  std::vector<CoarseNode> nodes; // post-order
+  int n_levels = 0;              // 1 + largest node height (leaves have height 0)
+  int64_t nnz = 0;               // stored entries of one sweep's matrices
+};
+// Nested-dissection supernodal Cholesky of the SPD matrix (rp, ci, val)
+// (CSR, both triangles); xyz: 3 coordinates per dof for the dissection.
+int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                  const std::vector<double>& val, const std::vector<double>& xyz, CoarseFactor& cf,
+                  std::string& err);
 
 // Host-side results of the topology and numeric setup (float64).
 struct HostSetup {
@@ -48,7 +85,12 @@ struct HostSetup {
   std::vector<std::vector<double>> agi_val, aig_val;
   // coarse operator
   int64_t n_c = 0;
-  std::vector<double> Acinv;                 // n_c x n_c, dense SPD inverse
+  bool coarse_dense = true;                  // dense inverse (else the sparse factor)
+  std::vector<double> Acinv;                 // n_c x n_c dense inverse (dense mode)
+  std::vector<int64_t> Ac_ptr;               // A_c in CSR (both triangles)
+  std::vector<int32_t> Ac_col;
+  std::vector<double> Ac_val;
+  CoarseFactor cfac;                         // its sparse Cholesky factorisation
   int error_subdomain = -1;
 };
 
@@ -57,9 +99,10 @@ int set_last_error(int code, const std::string& msg);
 
 // Validate the problem and options (no device checks).
 int validate_problem(const bddc_problem_t* p, const bddc_options_t* o, std::string& err);
-// Topology and float64 numerics; with invert_coarse = false, Acinv holds A_c itself.
+// Topology and float64 numerics; with factor_coarse = false A_c is assembled
+// but not factorised.
 int host_setup(const bddc_problem_t* p, const bddc_options_t* o, HostSetup& hs, std::string& err,
-               bool invert_coarse = true, bool numerics = true);
+               bool factor_coarse = true, bool numerics = true);
 
 }  // namespace bddc
 
@@ -98,22 +141,38 @@ struct bddc_handle_s {
   // operators
   void* d_aii = nullptr;              // interior inverses, precision-typed arena
   void* d_kgg = nullptr;              // interface operators, precision-typed arena
-  double* d_acinv = nullptr;          // coarse inverse, float64, in column panels
-  int32_t ldc = 0;                    // panel width (columns), the last panel may be narrower
-  int32_t n_cpanels = 0;              // number of column panels of A_c^-1
+  // dense coarse solve: A_c^-1 in column panels, streamed GEMV + panel sum
+  bool coarse_dense = true;
+  double* d_acinv = nullptr;
+  int32_t ldc = 0, n_cpanels = 0;
+  bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
+  double* w_cpart = nullptr;          // per-panel partial products
+  // sparse coarse solve (coarse_solve.cu): supernode matrices, level lists
+  double* d_cF = nullptr;             // forward matrices [L_PP^-1 ; M]
+  double* d_cB = nullptr;             // backward matrices [L_PP^-T , -M^T]
+  bddc::CItem* d_citems_f = nullptr;
+  bddc::CItem* d_citems_b = nullptr;
+  bddc::CNodeDev* d_cnodes = nullptr;
+  int32_t* d_cpiv = nullptr; int32_t* d_cupd = nullptr;
+  int32_t* d_clvl = nullptr;          // per-level item and receive offsets, then n_c
+  int32_t* d_crecv_dof = nullptr; int32_t* d_crecv_ptr = nullptr; int32_t* d_crecv_slot = nullptr;
+  unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
+  int c_levels = 0, c_max_ld_f = 0, c_max_ld_b = 0, c_grid = 0;
+  int64_t c_nnz = 0, c_update_total = 0;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
   // larger row tiles for the streamed (bulk-copy) GEMV
   bddc::WorkItem* d_wt_I = nullptr; int n_wt_I = 0;
   bddc::WorkItem* d_wt_G = nullptr; int n_wt_G = 0;
   bool use_tma = false;
-  bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
   int max_cols_I = 0, max_cols_G = 0;
   int max_nc = 0;                     // most constraints of one subdomain
   // apply workspace (nrhs_max columns)
   double *w_rI = nullptr, *w_tI = nullptr, *w_bI = nullptr;
   double *w_yG = nullptr, *w_zG = nullptr, *w_g = nullptr, *w_rc = nullptr, *w_uc = nullptr;
-  double* w_cpart = nullptr;          // per-panel partial coarse solutions
+  double* w_cr = nullptr;             // r' of the coarse forward sweep
+  double* w_cy = nullptr;             // forward-sweep result of the coarse solve
+  double* w_cc = nullptr;             // supernode contributions of the forward sweep
   double* w_eG = nullptr;             // Phi_G u_c per interface copy
   double* w_ucl = nullptr;            // u_c per local constraint
   // PCG workspace

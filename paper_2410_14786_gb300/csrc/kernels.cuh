@@ -22,6 +22,11 @@ cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, 
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
                              cudaStream_t st);
 
+// Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
+// u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
+cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);
+cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st);
+
 // x = P_I b: interior correction of b (zero on interface and Dirichlet nodes).
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,
                                        cudaStream_t st);

@@ -24,9 +24,9 @@ def _oracle(p, mask=0):
                   constraints=mask or (CORNER | EDGE | FACE))
 
 
-def _bddc(p, precision="fp64", mask=0, nrhs_max=1):
+def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto"):
     from paper_2410_14786_gb300 import BDDC
-    return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max)
+    return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max, coarse=coarse)
 
 
 def _small_voronoi():
@@ -91,6 +91,32 @@ def test_apply_fp64(name):
         rc, uc = g.coarse_vectors()
         assert _rel(rc.cpu().numpy()[:, 0], parts["rc"]) < 1e-11
         assert _rel(uc.cpu().numpy()[:, 0], parts["uc"]) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["cfg1_2d", "3d_24_3cubed", "3d_voronoi", "3d_corners_only"])
+def test_apply_sparse_coarse(name):
+    """The supernodal (nested-dissection) coarse factorisation gives the same
+    exact coarse solve as the dense inverse."""
+    p, mask, o = _case(name)
+    g = _bddc(p, mask=mask, nrhs_max=3, coarse="sparse")
+    assert g.info()["coarse_levels"] >= 1
+    r = synth.uniform(37, o.n_nodes * 3).reshape(-1, 3)
+    r[o.dir] = 0
+    z = g.apply(_cuda(r)).cpu().numpy()
+    assert _rel(z, o.apply_nodes(r)) < 1e-11
+    rc, uc = g.coarse_vectors(3)
+    want = np.stack([o.apply_parts(o.to_free(r[:, k]))["uc"] for k in range(3)], axis=1)
+    assert _rel(uc.cpu().numpy(), want) < 1e-11
+
+
+def test_pcg_sparse_coarse_matches_oracle():
+    p, mask, o = _case("3d_voronoi")
+    g = _bddc(p, mask=mask, coarse="sparse")
+    b = o.rhs(p.f[:, 0])
+    xo, h = o.pcg(b, 1e-8)
+    x, res = g.pcg_solve(_cuda(b), rtol=1e-8)
+    assert int(res.iters[0]) == h[0]["iters"]
+    assert _rel(x.cpu().numpy(), xo) < 1e-10
 
 
 def test_apply_ignores_dirichlet_input_and_multi_rhs():
@@ -215,6 +241,17 @@ def test_full_size_config2_properties():
     assert res.status == 0 and 5 <= int(res.iters[0]) <= 80
     tr = (b - g.matvec(x)).norm() / b.norm()
     assert float(tr) < 1.5e-8
+    # the sparse coarse factorisation agrees with the dense inverse at this size
+    gs = _bddc(p, coarse="sparse")
+    assert gs.info()["coarse_levels"] > 3
+    r = rand_iface()
+    z_d = g.apply(r)
+    _, uc_d = g.coarse_vectors()
+    z_s = gs.apply(r)
+    _, uc_s = gs.coarse_vectors()
+    assert float((uc_s - uc_d).abs().max() / uc_d.abs().max()) < 1e-11
+    assert float((z_s - z_d).abs().max() / z_d.abs().max()) < 1e-11
+    gs.close()
     # the mixed forms reach the same solution to the solver tolerance
     for prec in ("fp32", "bf16"):
         gm = _bddc(p, precision=prec)
