@@ -77,7 +77,7 @@ extern "C" {
  * applied as one matrix-vector product (n_c^2 float64 multiply-adds).
  * SPARSE: a nested-dissection supernodal Cholesky factorisation applied by
  * level-scheduled sweeps (far fewer operations and bytes; needed when the
- * dense inverse does not fit). AUTO: DENSE up to n_c = 16384, else SPARSE. */
+ * dense inverse does not fit). AUTO = SPARSE. */
 #define BDDC_COARSE_AUTO    0
 #define BDDC_COARSE_DENSE   1
 #define BDDC_COARSE_SPARSE  2
@@ -156,7 +156,7 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * itself never calls cudaMalloc, cudaFree or any allocating routine.
  * Limit: the temporaries of one apply, (3 n_interior + 3 n_interface_copies
  * + 2 sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
- * the dense coarse solve and 2 n_c + coarse_update_total for the sparse one
+ * the dense coarse solve and 2 n_c for the sparse one
  * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
  * larger problems get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current); make

@@ -353,7 +353,6 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   } else {
     CUDA_TRY(dev_alloc(h, &h->w_cr, h->n_c * R));
     CUDA_TRY(dev_alloc(h, &h->w_cy, h->n_c * R));
-    CUDA_TRY(dev_alloc(h, &h->w_cc, std::max<int64_t>(1, h->c_update_total) * R));
   }
   CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));

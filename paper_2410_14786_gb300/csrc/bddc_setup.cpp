@@ -376,7 +376,7 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
       }
       hs.Ac_ptr[g + 1] = (int64_t)hs.Ac_col.size();
     }
-    hs.coarse_dense = O->coarse == BDDC_COARSE_DENSE || (O->coarse == BDDC_COARSE_AUTO && nC <= 16384);
+    hs.coarse_dense = O->coarse == BDDC_COARSE_DENSE;
     if (factor_coarse && hs.coarse_dense) {
       hs.Acinv.assign((size_t)nC * nC, 0.0);
       for (int64_t r = 0; r < nC; ++r)

@@ -57,10 +57,9 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   const long long R = nrhs;
   const long long nI = round_up(h->nI_tot * R), nG = round_up(h->nG_tot * R);
   const long long nC = round_up(h->nC_tot * R), nc = round_up(h->n_c * R);
-  // coarse temporaries: the panel products (dense mode) or r', y and the
-  // supernode contributions (sparse mode)
-  const long long ncoarse = h->coarse_dense ? round_up((long long)h->n_cpanels * h->n_c * R)
-                                            : 2 * nc + round_up(h->c_update_total * R);
+  // coarse temporaries: the panel products (dense mode) or r' and y
+  // (sparse mode)
+  const long long ncoarse = h->coarse_dense ? round_up((long long)h->n_cpanels * h->n_c * R) : 2 * nc;
   const long long need = 3 * nI + 3 * nG + 2 * nC + 2 * nc + ncoarse;
   if (need > kScratchDoubles)
     return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
@@ -76,8 +75,8 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   // Calls on a handle are not re-entrant, and the launches below capture
   // the pointer values when they are enqueued, so the handle's own
   // workspace pointers are restored right after.
-  double* saved[14] = {h->w_rI, h->w_tI, h->w_bI, h->w_yG, h->w_zG, h->w_eG,
-                       h->w_g,  h->w_ucl, h->w_rc, h->w_uc, h->w_cr, h->w_cy, h->w_cc, h->w_cpart};
+  double* saved[13] = {h->w_rI, h->w_tI, h->w_bI, h->w_yG, h->w_zG, h->w_eG,
+                       h->w_g,  h->w_ucl, h->w_rc, h->w_uc, h->w_cr, h->w_cy, h->w_cpart};
   double* p = base;
   h->w_rI = p; p += nI;
   h->w_tI = p; p += nI;
@@ -93,13 +92,12 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
     h->w_cpart = p;
   } else {
     h->w_cr = p; p += nc;
-    h->w_cy = p; p += nc;
-    h->w_cc = p;
+    h->w_cy = p;
   }
   cudaError_t e = bddc::launch_apply(h, r, z, nrhs, static_cast<cudaStream_t>(stream));
   h->w_rI = saved[0]; h->w_tI = saved[1]; h->w_bI = saved[2]; h->w_yG = saved[3]; h->w_zG = saved[4];
   h->w_eG = saved[5]; h->w_g = saved[6]; h->w_ucl = saved[7]; h->w_rc = saved[8]; h->w_uc = saved[9];
-  h->w_cr = saved[10]; h->w_cy = saved[11]; h->w_cc = saved[12]; h->w_cpart = saved[13];
+  h->w_cr = saved[10]; h->w_cy = saved[11]; h->w_cpart = saved[12];
   if (e != cudaSuccess) return bddc::set_last_error(BDDC_ERR_CUDA, cudaGetErrorString(e));
   return BDDC_OK;
 }

@@ -1,18 +1,20 @@
 // Coarse solve u_c = A_c^-1 r_c on the GPU from the supernodal factorisation
 // of coarse_sparse.cpp (float64 throughout).
 //
-// Forward sweep, supernodes by increasing height (leaves first): for node t,
-//   [y_P; c_t] = [L_PP^-1 ; M] r'_P,
-// where r' starts as r_c and, after each level, every coarse dof that
-// receives contributions from that level's nodes subtracts their sum
-// (gathered through fixed lists, so the summation order never changes and
-// results are reproducible). Backward sweep, by decreasing height:
-//   u_P = [L_PP^-T , -M^T] [y_P ; u_U].
+// Vectors r' (forward right-hand side) and y (forward result) are kept in
+// elimination order, so the pivots of every supernode are contiguous.
+// Forward sweep, supernodes by increasing height (leaves first); for a node t
+// with pivots P and update set U, [y_P; c_t] = [L_PP^-1 ; M] r'_P, and the
+// contributions c_t are subtracted from r'_U. Backward sweep, by decreasing
+// height: u_P = [L_PP^-T , -M^T] [y_P ; u_U].
 //
-// The whole solve is one persistent cooperative kernel: blocks take the row
-// tiles of a level round robin, then meet at a grid-wide barrier before the
-// next phase. A barrier wait is bounded; on timeout the block records
-// BDDC_ERR_TIMEOUT in the error flag and every block leaves at its next
+// Every output value of a level is one warp unit: a row of L_PP^-1 (lower
+// triangular: only its nonzero part is read), all contributions of the
+// level to one later dof (its M rows summed in a fixed order, so results are
+// reproducible), or a row of the backward matrix. All units of a level run
+// at once across the GPU. The solve is one persistent cooperative kernel:
+// levels are separated by grid-wide barriers whose waits are bounded; on
+// timeout a block records BDDC_ERR_TIMEOUT and all blocks leave at their next
 // barrier. Values written by other blocks are read through L2 (__ldcg).
 #include <cuda_runtime.h>
 
@@ -28,30 +30,25 @@ namespace bddc {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRowTile = 16;
+constexpr int kThreads = 1024;
 constexpr long long kBarrierCycles = 4000000000LL;   // about 2 s at 2 GHz
 
 struct CoarseArgs {
-  const CItem* items_f;
-  const CItem* items_b;
   const CNodeDev* nodes;
+  const CUnit* units;
+  const CContrib* list;      // contributions of the receiving units
+  const int32_t* upd;        // update-set dofs
+  const int32_t* order;      // position -> dof
+  const int32_t* lvl;        // unit offsets [L+1 forward][L+1 backward], then n_c
   const double* F;
   const double* B;
-  const int32_t* piv;
-  const int32_t* upd;
-  const int32_t* lvl;        // [L+1 forward item offsets][L+1 backward][L+1 receive][n_c]
-  const int32_t* recv_dof;
-  const int32_t* recv_ptr;   // per receive entry, its range of recv_slot
-  const int32_t* recv_slot;
-  const double* r;           // r_c
-  double* rp;                // r'
-  double* y;
-  double* c;
-  double* u;                 // u_c
+  const double* r;           // r_c (dof order)
+  double* rp;                // r' (elimination order)
+  double* y;                 // y (elimination order)
+  double* u;                 // u_c (dof order)
   unsigned int* bar;         // [0] arrivals, [1] generation
   int32_t* err;
-  int levels, nrhs, nb;
+  int levels, nrhs;
 };
 
 // Grid-wide barrier; false when a wait ran out (here or in another block).
@@ -85,93 +82,124 @@ __device__ bool grid_barrier(const CoarseArgs& a) {
   return ok != 0;
 }
 
-// One row tile of a supernode matrix: stage the operand, one row per warp.
-template <bool FWD>
-__device__ void row_tile(const CoarseArgs& a, const CItem& it, double* xs) {
-  const CNodeDev nd = a.nodes[it.node];
-  const double* mat = FWD ? a.F : a.B;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nrhs = a.nrhs, nb = a.nb;
-  for (int k0 = 0; k0 < nrhs; k0 += nb) {
-    const int kn = min(nb, nrhs - k0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < it.ld * nb; i += kThreads) {
-      const int j = i / nb, k = i - j * nb;
-      double v = 0.0;
-      if (k < kn && j < it.ncols) {
-        const int col = k0 + k;
-        if (FWD) {
-          v = __ldcg(&a.rp[(int64_t)a.piv[nd.piv_off + j] * nrhs + col]);
-        } else {
-          v = j < nd.p ? __ldcg(&a.y[(int64_t)a.piv[nd.piv_off + j] * nrhs + col])
-                       : __ldcg(&a.u[(int64_t)a.upd[nd.upd_off + j - nd.p] * nrhs + col]);
-        }
-      }
-      xs[i] = v;
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum_j row[j] * x[j * nrhs + k] over j in [j0, j1), one warp. Four
+// elements per lane are loaded before they are used, so a row costs about
+// (j1 - j0) / 128 rounds of memory latency instead of one per 32 elements.
+__device__ __forceinline__ double warp_dot(const double* __restrict__ row, const double* x, int j0, int j1,
+                                           int nrhs, int k, int lane) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = j0 + lane; j < j1; j += 128) {
+    const bool b1 = j + 32 < j1, b2 = j + 64 < j1, b3 = j + 96 < j1;
+    const double r0 = __ldg(&row[j]);
+    const double r1 = b1 ? __ldg(&row[j + 32]) : 0.0;
+    const double r2 = b2 ? __ldg(&row[j + 64]) : 0.0;
+    const double r3 = b3 ? __ldg(&row[j + 96]) : 0.0;
+    const double x0 = __ldcg(&x[(int64_t)j * nrhs + k]);
+    const double x1 = b1 ? __ldcg(&x[(int64_t)(j + 32) * nrhs + k]) : 0.0;
+    const double x2 = b2 ? __ldcg(&x[(int64_t)(j + 64) * nrhs + k]) : 0.0;
+    const double x3 = b3 ? __ldcg(&x[(int64_t)(j + 96) * nrhs + k]) : 0.0;
+    s0 = fma(r0, x0, s0);
+    s1 = fma(r1, x1, s1);
+    s2 = fma(r2, x2, s2);
+    s3 = fma(r3, x3, s3);
+  }
+  return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+// The same with x gathered: x[idx[j]] (the backward sweep's u_U).
+__device__ __forceinline__ double warp_dot_gather(const double* __restrict__ row, const double* x,
+                                                  const int32_t* __restrict__ idx, int n, int nrhs, int k,
+                                                  int lane) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = lane; j < n; j += 128) {
+    const bool b1 = j + 32 < n, b2 = j + 64 < n, b3 = j + 96 < n;
+    const int i0 = __ldg(&idx[j]);
+    const int i1 = b1 ? __ldg(&idx[j + 32]) : 0;
+    const int i2 = b2 ? __ldg(&idx[j + 64]) : 0;
+    const int i3 = b3 ? __ldg(&idx[j + 96]) : 0;
+    const double r0 = __ldg(&row[j]);
+    const double r1 = b1 ? __ldg(&row[j + 32]) : 0.0;
+    const double r2 = b2 ? __ldg(&row[j + 64]) : 0.0;
+    const double r3 = b3 ? __ldg(&row[j + 96]) : 0.0;
+    const double x0 = __ldcg(&x[(int64_t)i0 * nrhs + k]);
+    const double x1 = b1 ? __ldcg(&x[(int64_t)i1 * nrhs + k]) : 0.0;
+    const double x2 = b2 ? __ldcg(&x[(int64_t)i2 * nrhs + k]) : 0.0;
+    const double x3 = b3 ? __ldcg(&x[(int64_t)i3 * nrhs + k]) : 0.0;
+    s0 = fma(r0, x0, s0);
+    s1 = fma(r1, x1, s1);
+    s2 = fma(r2, x2, s2);
+    s3 = fma(r3, x3, s3);
+  }
+  return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+__device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
+  const int nrhs = a.nrhs;
+  if (w.kind == 0) {
+    // y[pos0 + i] = sum_{j <= i} L_PP^-1[i, j] r'[pos0 + j]
+    const CNodeDev nd = a.nodes[w.a];
+    const double* row = a.F + nd.foff + (int64_t)w.row * nd.fld;
+    const double* x = a.rp + (int64_t)nd.pos0 * nrhs;
+    for (int k = 0; k < nrhs; ++k) {
+      const double s = warp_dot(row, x, 0, w.row + 1, nrhs, k, lane);
+      if (lane == 0) a.y[(int64_t)(nd.pos0 + w.row) * nrhs + k] = s;
     }
-    __syncthreads();
-    for (int rr = warp; rr < it.nrows; rr += kThreads / 32) {
-      const int row = it.row0 + rr;
-      const double* m = mat + it.moff + (int64_t)row * it.ld;
-      double acc[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] = 0.0;
-      for (int c0 = lane * 2; c0 < it.ld; c0 += 64) {
-        const double2 mv = __ldg(reinterpret_cast<const double2*>(m + c0));
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < kn) acc[k] = fma(mv.x, xs[c0 * nb + k], fma(mv.y, xs[(c0 + 1) * nb + k], acc[k]));
+  } else {
+    // r'[a] -= sum over the listed contributions, in list order, of
+    // M_row . r'_P(node)
+    for (int k = 0; k < nrhs; ++k) {
+      double s = 0.0;
+      for (int q = w.b; q < w.e; ++q) {
+        const CContrib c = a.list[q];
+        s += warp_dot(a.F + c.row_off, a.rp + (int64_t)c.x_off * nrhs, 0, c.len, nrhs, k, lane);
       }
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-      double out = acc[0];
-#pragma unroll
-      for (int k = 1; k < 8; ++k)
-        if (lane == k) out = acc[k];
-      if (lane < kn) {
-        const int col = k0 + lane;
-        if (FWD) {
-          if (row < nd.p) a.y[(int64_t)a.piv[nd.piv_off + row] * nrhs + col] = out;
-          else a.c[(int64_t)(nd.c_off + row - nd.p) * nrhs + col] = out;
-        } else {
-          a.u[(int64_t)a.piv[nd.piv_off + row] * nrhs + col] = out;
-        }
+      if (lane == 0) {
+        double* dst = &a.rp[(int64_t)w.a * nrhs + k];
+        *dst = __ldcg(dst) - s;
       }
     }
   }
 }
 
+__device__ void backward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
+  // u[dof of pos0 + i] = sum_{j >= i} L_PP^-T[i, j] y[pos0 + j] - sum_b M[b, i] u[upd_b]
+  const int nrhs = a.nrhs;
+  const CNodeDev nd = a.nodes[w.a];
+  const double* row = a.B + nd.boff + (int64_t)w.row * nd.bld;
+  const double* yp = a.y + (int64_t)nd.pos0 * nrhs;
+  for (int k = 0; k < nrhs; ++k) {
+    const double s = warp_dot(row, yp, w.row, nd.p, nrhs, k, lane) +
+                     warp_dot_gather(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, nrhs, k, lane);
+    if (lane == 0) a.u[(int64_t)a.order[nd.pos0 + w.row] * nrhs + k] = s;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_coarse_solve(CoarseArgs a) {
-  extern __shared__ double xs[];
   const int L = a.levels;
   const int32_t* off_f = a.lvl;
   const int32_t* off_b = a.lvl + (L + 1);
-  const int32_t* off_r = a.lvl + 2 * (L + 1);
-  const int64_t n_c = a.lvl[3 * (L + 1)];
-  const int64_t tid = blockIdx.x * (int64_t)kThreads + threadIdx.x;
-  const int64_t nthreads = (int64_t)gridDim.x * kThreads;
-  for (int64_t i = tid; i < n_c * a.nrhs; i += nthreads) a.rp[i] = a.r[i];   // r' = r_c
+  const int64_t n_c = a.lvl[2 * (L + 1)];
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5);
+  const int nw = (int)(((int64_t)gridDim.x * kThreads) >> 5);
+  // r' = r_c in elimination order
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_c * a.nrhs; i += (int64_t)gridDim.x * kThreads) {
+    const int64_t pos = i / a.nrhs;
+    a.rp[i] = a.r[(int64_t)a.order[pos] * a.nrhs + (i - pos * a.nrhs)];
+  }
   if (!grid_barrier(a)) return;
   for (int lv = 0; lv < L; ++lv) {
-    for (int t = off_f[lv] + blockIdx.x; t < off_f[lv + 1]; t += gridDim.x) row_tile<true>(a, a.items_f[t], xs);
+    for (int t = off_f[lv] + gw; t < off_f[lv + 1]; t += nw) forward_unit(a, a.units[t], lane);
     if (!grid_barrier(a)) return;
-    if (off_r[lv + 1] > off_r[lv]) {
-      const int64_t ne = (int64_t)(off_r[lv + 1] - off_r[lv]) * a.nrhs;
-      for (int64_t i = tid; i < ne; i += nthreads) {
-        const int e = off_r[lv] + (int)(i / a.nrhs);
-        const int k = (int)(i % a.nrhs);
-        double s = 0.0;
-        for (int q = a.recv_ptr[e]; q < a.recv_ptr[e + 1]; ++q) s += __ldcg(&a.c[(int64_t)a.recv_slot[q] * a.nrhs + k]);
-        double* dst = &a.rp[(int64_t)a.recv_dof[e] * a.nrhs + k];
-        *dst = __ldcg(dst) - s;
-      }
-      if (!grid_barrier(a)) return;
-    }
   }
   for (int lv = L - 1; lv >= 0; --lv) {
-    for (int t = off_b[lv] + blockIdx.x; t < off_b[lv + 1]; t += gridDim.x) row_tile<false>(a, a.items_b[t], xs);
+    for (int t = off_b[lv] + gw; t < off_b[lv + 1]; t += nw) backward_unit(a, a.units[t], lane);
     if (lv > 0 && !grid_barrier(a)) return;
   }
 }
@@ -195,124 +223,116 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   if (cf.n == 0) return cudaSuccess;
   const int nn = (int)cf.nodes.size();
   std::vector<CNodeDev> nodes(nn);
-  std::vector<int32_t> piv, upd;
-  std::vector<int64_t> foff(nn), boff(nn);
-  std::vector<int32_t> fld(nn), bld(nn);
-  int64_t fcur = 0, bcur = 0, ccur = 0;
+  std::vector<int32_t> upd;
+  int64_t fcur = 0, bcur = 0, ucur = 0;
   for (int t = 0; t < nn; ++t) {
     const CoarseNode& T = cf.nodes[t];
-    nodes[t] = CNodeDev{T.p, T.u, (int32_t)piv.size(), (int32_t)upd.size(), (int32_t)ccur};
-    piv.insert(piv.end(), T.piv.begin(), T.piv.end());
-    upd.insert(upd.end(), T.upd.begin(), T.upd.end());
-    ccur += T.u;
-    fld[t] = (T.p + 1) / 2 * 2;
-    bld[t] = (T.p + T.u + 1) / 2 * 2;
+    CNodeDev d{};
+    d.p = T.p;
+    d.u = T.u;
+    d.pos0 = T.last - T.p + 1;
+    d.upd_off = (int32_t)upd.size();
+    d.fld = std::max(T.p, 1);
+    d.bld = std::max(T.p + T.u, 1);
     fcur = (fcur + 31) / 32 * 32;
-    foff[t] = fcur;
-    fcur += (int64_t)(T.p + T.u) * fld[t];
+    d.foff = fcur;
+    fcur += (int64_t)(T.p + T.u) * d.fld;
     bcur = (bcur + 31) / 32 * 32;
-    boff[t] = bcur;
-    bcur += (int64_t)T.p * bld[t];
+    d.boff = bcur;
+    bcur += (int64_t)T.p * d.bld;
+    upd.insert(upd.end(), T.upd.begin(), T.upd.end());
+    ucur += T.u;
+    nodes[t] = d;
   }
   std::vector<double> F((size_t)std::max<int64_t>(fcur, 1), 0.0), B((size_t)std::max<int64_t>(bcur, 1), 0.0);
   for (int t = 0; t < nn; ++t) {
     const CoarseNode& T = cf.nodes[t];
     const int f = T.p + T.u;
     for (int r = 0; r < f; ++r)
-      std::memcpy(&F[foff[t] + (int64_t)r * fld[t]], &T.Fm[(size_t)r * T.p], sizeof(double) * T.p);
+      std::memcpy(&F[nodes[t].foff + (int64_t)r * nodes[t].fld], &T.Fm[(size_t)r * T.p], sizeof(double) * T.p);
     for (int r = 0; r < T.p; ++r)
-      std::memcpy(&B[boff[t] + (int64_t)r * bld[t]], &T.Bm[(size_t)r * f], sizeof(double) * f);
+      std::memcpy(&B[nodes[t].boff + (int64_t)r * nodes[t].bld], &T.Bm[(size_t)r * f], sizeof(double) * f);
   }
-  // level table, work items and receive lists (per level: the dofs that the
-  // level's nodes contribute to, each with its contribution slots in node
-  // order; nodes without pivots contribute nothing)
-  std::vector<int32_t> lvl(3 * (L + 1) + 1, 0);
-  std::vector<CItem> itf, itb;
-  std::vector<int32_t> recv_dof, recv_ptr(1, 0), recv_slot;
-  std::vector<std::vector<int32_t>> slots_of(cf.n);
+  std::vector<int32_t> pos(cf.n);
+  for (int64_t i = 0; i < cf.n; ++i) pos[cf.order[i]] = (int32_t)i;
+  // warp units: forward levels (L_PP^-1 rows, then one unit per receiving
+  // position with its (node, M row) pairs in node order), then backward levels
+  std::vector<CUnit> units;
+  std::vector<CContrib> list;
+  std::vector<int32_t> lvl(2 * (L + 1) + 1, 0);
+  std::vector<std::vector<int32_t>> contrib(cf.n);
   std::vector<int32_t> touched;
   for (int lv = 0; lv < L; ++lv) {
-    lvl[lv] = (int)itf.size();
-    lvl[(L + 1) + lv] = (int)itb.size();
-    lvl[2 * (L + 1) + lv] = (int)recv_dof.size();
+    lvl[lv] = (int)units.size();
     touched.clear();
     for (int t = 0; t < nn; ++t) {
       const CoarseNode& T = cf.nodes[t];
       if (T.height != lv || T.p == 0) continue;
-      for (int r0 = 0; r0 < T.p + T.u; r0 += kRowTile)
-        itf.push_back(CItem{foff[t], t, fld[t], T.p, r0, std::min(kRowTile, T.p + T.u - r0), 0});
-      for (int r0 = 0; r0 < T.p; r0 += kRowTile)
-        itb.push_back(CItem{boff[t], t, bld[t], T.p + T.u, r0, std::min(kRowTile, T.p - r0), 0});
-      h->c_max_ld_f = std::max(h->c_max_ld_f, fld[t]);
-      h->c_max_ld_b = std::max(h->c_max_ld_b, bld[t]);
-      for (int a = 0; a < T.u; ++a) {
-        const int32_t w = T.upd[a];
-        if (slots_of[w].empty()) touched.push_back(w);
-        slots_of[w].push_back(nodes[t].c_off + a);
+      for (int i = 0; i < T.p; ++i) units.push_back(CUnit{0, t, i, 0, 0});
+      for (int b = 0; b < T.u; ++b) {
+        const int32_t w = pos[T.upd[b]];
+        if (contrib[w].empty()) touched.push_back(w);
+        contrib[w].push_back(t);
+        contrib[w].push_back(b);
       }
     }
     std::sort(touched.begin(), touched.end());
     for (int32_t w : touched) {
-      recv_dof.push_back(w);
-      recv_slot.insert(recv_slot.end(), slots_of[w].begin(), slots_of[w].end());
-      recv_ptr.push_back((int32_t)recv_slot.size());
-      slots_of[w].clear();
+      const int32_t b0 = (int32_t)list.size();
+      for (size_t q = 0; q < contrib[w].size(); q += 2) {
+        const CNodeDev& nd = nodes[contrib[w][q]];
+        list.push_back(CContrib{nd.foff + (int64_t)(nd.p + contrib[w][q + 1]) * nd.fld, nd.pos0, nd.p, 0});
+      }
+      units.push_back(CUnit{1, w, 0, b0, (int32_t)list.size()});
+      contrib[w].clear();
     }
   }
-  lvl[L] = (int)itf.size();
-  lvl[(L + 1) + L] = (int)itb.size();
-  lvl[2 * (L + 1) + L] = (int)recv_dof.size();
-  lvl[3 * (L + 1)] = (int32_t)cf.n;
+  lvl[L] = (int)units.size();
+  for (int lv = 0; lv < L; ++lv) {
+    lvl[(L + 1) + lv] = (int)units.size();
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      if (T.height != lv || T.p == 0) continue;
+      for (int i = 0; i < T.p; ++i) units.push_back(CUnit{2, t, i, 0, 0});
+    }
+  }
+  lvl[(L + 1) + L] = (int)units.size();
+  lvl[2 * (L + 1)] = (int32_t)cf.n;
   h->c_nnz = fcur + bcur;
-  h->c_update_total = ccur;
+  h->c_update_total = ucur;
   cudaError_t e;
   if ((e = up(h, &h->d_cF, F)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_cB, B)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_citems_f, itf)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_citems_b, itb)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_cnodes, nodes)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cpiv, piv)) != cudaSuccess) return e;
+  if ((e = up(h, &h->d_cunits, units)) != cudaSuccess) return e;
+  if ((e = up(h, &h->d_clist, list)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_cupd, upd)) != cudaSuccess) return e;
+  if ((e = up(h, &h->d_corder, cf.order)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_clvl, lvl)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_crecv_dof, recv_dof)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_crecv_ptr, recv_ptr)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_crecv_slot, recv_slot)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
-  // cooperative grid: all blocks resident at once
-  int dev = 0, sms = 0, coop = 0;
+  // cooperative grid: every block resident at once
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop) return cudaErrorNotSupported;
-  const int max_ld = std::max(h->c_max_ld_f, h->c_max_ld_b);
-  int per_sm = 0;
-  const size_t smem = (size_t)max_ld * 8 * sizeof(double);   // room for 8 right-hand sides
-  if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)std::min<size_t>(smem, 200 * 1024))) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve, kThreads, 0)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve, kThreads,
-                                                         std::min<size_t>(smem, 200 * 1024))) != cudaSuccess)
-    return e;
-  h->c_grid = sms * std::max(1, std::min(per_sm, 2));
+  if (per_sm < 1) return cudaErrorNotSupported;
+  h->c_grid = sms * std::min(per_sm, 2);
   return cudaSuccess;
 }
 
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st) {
   if (h->n_c == 0) return cudaSuccess;
-  const int max_ld = std::max(h->c_max_ld_f, h->c_max_ld_b);
-  int nb = std::min(nrhs, 8);
-  while (nb > 1 && (size_t)max_ld * nb * sizeof(double) > 200 * 1024) nb >>= 1;
-  const size_t smem = (size_t)max_ld * nb * sizeof(double);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  CoarseArgs a{h->d_citems_f, h->d_citems_b, h->d_cnodes, h->d_cF, h->d_cB, h->d_cpiv, h->d_cupd, h->d_clvl,
-               h->d_crecv_dof, h->d_crecv_ptr, h->d_crecv_slot, rc, h->w_cr, h->w_cy, h->w_cc, uc, h->d_cbar,
-               h->d_err, h->c_levels, nrhs, nb};
+  CoarseArgs a{h->d_cnodes, h->d_cunits, h->d_clist, h->d_cupd, h->d_corder, h->d_clvl, h->d_cF, h->d_cB,
+               rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err, h->c_levels, nrhs};
   cudaError_t e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->c_grid);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

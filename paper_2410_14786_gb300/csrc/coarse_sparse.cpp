@@ -32,7 +32,7 @@ namespace bddc {
 
 namespace {
 
-constexpr int kLeaf = 48;   // vertex sets up to this size are not split
+constexpr int kLeaf = 384;  // vertex sets up to this size are not split
 
 struct Dissection {
   const std::vector<int64_t>& rp;
@@ -153,6 +153,7 @@ int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
   nd.build(std::move(all), 0);
   std::vector<int32_t> pos(n);
   for (int64_t i = 0; i < n; ++i) pos[nd.order[i]] = (int32_t)i;
+  cf.order = nd.order;
   const int nn = (int)cf.nodes.size();   // nodes are in post-order (children before parents)
 
   // ---- symbolic: update sets --------------------------------------------------------

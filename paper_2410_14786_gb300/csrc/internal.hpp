@@ -11,20 +11,27 @@
 
 namespace bddc {
 
-// One row tile of one supernode matrix in a coarse-solve level launch.
-struct CItem {
-  int64_t moff;     // element offset of the node's matrix
-  int32_t node;     // supernode index
-  int32_t ld;       // leading dimension (even, 16-byte rows)
-  int32_t ncols;    // operand length (p forward, p+u backward)
-  int32_t row0, nrows;
-  int32_t pad;
-};
 struct CNodeDev {
+  int64_t foff;     // offset of the node's forward matrix [L_PP^-1 ; M]
+  int64_t boff;     // offset of the node's backward matrix [L_PP^-T , -M^T]
   int32_t p, u;     // pivots, update-set size
-  int32_t piv_off;  // offset of the node's pivot dofs
-  int32_t upd_off;  // offset of the node's update dofs
-  int32_t c_off;    // offset of the node's contributions
+  int32_t pos0;     // elimination position of the first pivot (pivots are contiguous)
+  int32_t upd_off;  // offset of the node's update-set dofs
+  int32_t fld, bld; // leading dimensions of the two matrices
+};
+// One warp's unit of a coarse-sweep level: kind 0 = row `row` of L_PP^-1 of
+// node `a` (forward), kind 1 = all contributions to the dof at elimination
+// position `a` from this level (contributions [b, e)), kind 2 = row `row` of
+// the backward matrix of node `a`.
+struct CUnit {
+  int32_t kind, a, row, b, e;
+};
+// One contribution to a receiving dof: an M row of a node and its operand.
+struct CContrib {
+  int64_t row_off;  // offset of the M row in the forward matrices
+  int32_t x_off;    // elimination position of the node's first pivot
+  int32_t len;      // p of the node
+  int64_t pad;
 };
 
 // One row tile of one dense operator in a batched GEMV launch:
@@ -51,6 +58,7 @@ struct CoarseNode {
 struct CoarseFactor {
   int64_t n = 0;
   std::vector<CoarseNode> nodes; // post-order
+  std::vector<int32_t> order;    // elimination position -> coarse dof
   int n_levels = 0;              // 1 + largest node height (leaves have height 0)
   int64_t nnz = 0;               // stored entries of one sweep's matrices
 };
@@ -150,14 +158,14 @@ struct bddc_handle_s {
   // sparse coarse solve (coarse_solve.cu): supernode matrices, level lists
   double* d_cF = nullptr;             // forward matrices [L_PP^-1 ; M]
   double* d_cB = nullptr;             // backward matrices [L_PP^-T , -M^T]
-  bddc::CItem* d_citems_f = nullptr;
-  bddc::CItem* d_citems_b = nullptr;
   bddc::CNodeDev* d_cnodes = nullptr;
-  int32_t* d_cpiv = nullptr; int32_t* d_cupd = nullptr;
-  int32_t* d_clvl = nullptr;          // per-level item and receive offsets, then n_c
-  int32_t* d_crecv_dof = nullptr; int32_t* d_crecv_ptr = nullptr; int32_t* d_crecv_slot = nullptr;
+  bddc::CUnit* d_cunits = nullptr;    // warp units, forward levels then backward levels
+  bddc::CContrib* d_clist = nullptr;  // contributions of the receiving units
+  int32_t* d_cupd = nullptr;          // update-set dofs of every node
+  int32_t* d_corder = nullptr;        // elimination position -> coarse dof
+  int32_t* d_clvl = nullptr;          // unit offsets: [L+1 forward][L+1 backward], then n_c
   unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
-  int c_levels = 0, c_max_ld_f = 0, c_max_ld_b = 0, c_grid = 0;
+  int c_levels = 0, c_grid = 0, c_block = 0;
   int64_t c_nnz = 0, c_update_total = 0;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
@@ -170,9 +178,8 @@ struct bddc_handle_s {
   // apply workspace (nrhs_max columns)
   double *w_rI = nullptr, *w_tI = nullptr, *w_bI = nullptr;
   double *w_yG = nullptr, *w_zG = nullptr, *w_g = nullptr, *w_rc = nullptr, *w_uc = nullptr;
-  double* w_cr = nullptr;             // r' of the coarse forward sweep
-  double* w_cy = nullptr;             // forward-sweep result of the coarse solve
-  double* w_cc = nullptr;             // supernode contributions of the forward sweep
+  double* w_cr = nullptr;             // r' of the coarse forward sweep (elimination order)
+  double* w_cy = nullptr;             // forward-sweep result (elimination order)
   double* w_eG = nullptr;             // Phi_G u_c per interface copy
   double* w_ucl = nullptr;            // u_c per local constraint
   // PCG workspace
