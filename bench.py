@@ -170,7 +170,7 @@ def run_gb300(args):
     precs = ["fp64", "fp32", "bf16"] if not args.only else [args.only]
     headline = args.precision if args.precision in precs else precs[-1]
     for prec in precs:
-        g = BDDC.from_problem(p, precision=prec, nrhs_max=1)
+        g = BDDC.from_problem(p, precision=prec, nrhs_max=1, graph=not args.no_graph)
         handles[prec] = g
         forms[prec] = {"setup_s": g.info()["setup_seconds"]}
     g64 = handles.get("fp64", handles[headline])
@@ -312,7 +312,7 @@ def run_apply_only(args):
     from paper_2410_14786_gb300 import BDDC, build
     build.build()
     p = synth.config(2)
-    g = BDDC.from_problem(p, precision=args.precision, nrhs_max=1)
+    g = BDDC.from_problem(p, precision=args.precision, nrhs_max=1, graph=not args.no_graph)
     f = torch.from_numpy(np.ascontiguousarray(p.f[:, 0])).cuda()
     b = g.rhs(f)
     z = torch.empty_like(b)
@@ -335,6 +335,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--only", default=None, choices=[None, "fp64", "fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch each PCG iteration's kernels directly (for profilers); not for timing")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling aid: set up the headline form, run this many applies and one solve, exit")
     args = ap.parse_args()

@@ -104,6 +104,8 @@ typedef struct {
     int32_t n_threads;     /* host threads for setup; 0 = all cores */
     int32_t device;        /* CUDA device ordinal */
     int32_t coarse;        /* BDDC_COARSE_* */
+    int32_t no_graph;      /* 1: launch every PCG iteration's kernels directly instead of
+                              replaying a captured CUDA graph (for profilers) */
 } bddc_options_t;
 
 typedef struct {

@@ -50,11 +50,12 @@ class BDDC:
     elem_sigma [ne^dim] float64 > 0, elem_subdomain [ne^dim] int32,
     n_sub; precision in {"fp64", "fp32", "bf16"}; constraints bitmask of
     CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup;
-    coarse in {"auto", "dense", "sparse"} (exact float64 coarse solve either way).
+    coarse in {"auto", "dense", "sparse"} (exact float64 coarse solve either way);
+    graph=False launches each PCG iteration directly (for profilers).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
-                 constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto"):
+                 constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -66,7 +67,7 @@ class BDDC:
                             part.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub))
         opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
-                            COARSE[coarse] if isinstance(coarse, str) else int(coarse))
+                            COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1)
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim

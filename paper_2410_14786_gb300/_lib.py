@@ -40,7 +40,8 @@ class Problem(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
-                ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32)]
+                ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
+                ("no_graph", C.c_int32)]
 
 
 class Info(C.Structure):

@@ -489,6 +489,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   if (!h) return fail(BDDC_ERR_OOM, "handle allocation");
   h->dim = P->dim; h->ne = P->ne; h->n1 = P->ne + 1; h->n_sub = P->n_sub;
   h->precision = O->precision; h->nrhs_max = O->nrhs_max; h->device = O->device;
+  h->use_graph = O->no_graph == 0;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -687,7 +688,7 @@ static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, doubl
     CUDA_TRY(launch_update_xr_conv(h, x, nrhs, rtol, flexible, st));
     if ((rc = read_flags())) return rc;
     int it = 1;
-    if (hf[0] > 0 && it < maxit) {
+    if (hf[0] > 0 && it < maxit && h->use_graph) {
       if ((rc = capture_iteration(h, x, nrhs, rtol, flexible))) return rc;
       for (; it < maxit && hf[0] > 0; ++it) {
         CUDA_TRY(cudaGraphLaunch(h->iter_graph, st));
@@ -695,6 +696,15 @@ static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, doubl
         CUDA_TRY(cudaStreamSynchronize(st));
         if (hf[2]) return fail(BDDC_ERR_TIMEOUT, "a bounded device wait ran out");
       }
+    }
+    for (; it < maxit && hf[0] > 0; ++it) {
+      // the same iteration, launched directly
+      CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
+      CUDA_TRY(launch_dots_fin(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, FIN_BETA, rtol, flexible, st));
+      CUDA_TRY(launch_update_p(h, nrhs, st));
+      CUDA_TRY(launch_spmv(h, h->p_p, h->p_q, nrhs, FIN_ALPHA, rtol, flexible, st));
+      CUDA_TRY(launch_update_xr_conv(h, x, nrhs, rtol, flexible, st));
+      if ((rc = read_flags())) return rc;
     }
     if (hf[0] > 0) status = BDDC_NOT_CONVERGED;
   } else if (hf[0] > 0) {

@@ -117,6 +117,7 @@ int host_setup(const bddc_problem_t* p, const bddc_options_t* o, HostSetup& hs, 
 struct bddc_handle_s {
   // problem
   int dim = 0, ne = 0, n1 = 0, n_sub = 0, precision = 0, nrhs_max = 1, device = 0;
+  bool use_graph = true;
   int64_t n_nodes = 0, n_elems = 0;
   double h = 0;
   // sizes

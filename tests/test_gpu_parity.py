@@ -158,6 +158,23 @@ def test_pcg_multi_rhs_and_zero_column():
     assert _rel(x, xo) < 1e-10
 
 
+def test_graph_and_direct_launches_are_bitwise_identical():
+    """The captured-graph iteration and directly launched kernels compute the
+    same thing, and reductions have a fixed order: solutions agree bit for bit,
+    run after run."""
+    p, mask, o = _case("3d_24_3cubed")
+    b = _cuda(o.rhs(p.f[:, 0]))
+    from paper_2410_14786_gb300 import BDDC
+    xs = []
+    for graph in (True, True, False):
+        g = BDDC.from_problem(p, precision="bf16", constraints=mask, graph=graph)
+        x, res = g.pcg_solve(b, rtol=1e-8)
+        xs.append((x.cpu().numpy(), int(res.iters[0])))
+        g.close()
+    assert xs[0][1] == xs[1][1] == xs[2][1]
+    assert np.array_equal(xs[0][0], xs[1][0]) and np.array_equal(xs[0][0], xs[2][0])
+
+
 def test_pcg_host_buffers():
     p, mask, o = _case("3d_24_3cubed")
     g = _bddc(p, mask=mask)

@@ -42,7 +42,7 @@ def _structs(p, precision=0, constraints=0, nrhs_max=1):
     part = np.ascontiguousarray(p.elem_subdomain, dtype=np.int32)
     prob = _lib.Problem(p.dim, p.ne, sig.ctypes.data_as(C.POINTER(C.c_double)),
                         part.ctypes.data_as(C.POINTER(C.c_int32)), p.n_sub)
-    opts = _lib.Options(precision, constraints, nrhs_max, 4, 0, 0)
+    opts = _lib.Options(precision, constraints, nrhs_max, 4, 0, 0, 0)
     return prob, opts, (sig, part)
 
 
