@@ -271,14 +271,14 @@ __global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __res
 #pragma unroll
         for (int k = 0; k < NRB; ++k)
           for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        // every lane of the group holds all NRB sums; lane gl writes the
+        // columns k = gl, gl + lpr, ... (a group may have fewer lanes than NRB)
         if (rr < nr && gl < nr_rhs) {
-          Acc out = acc[0];
-#pragma unroll
-          for (int k = 1; k < NRB; ++k)
-            if (gl == k) out = acc[k];
           const int64_t j = (int64_t)w.yoff + w.row0 + r0 + rr;
           const int64_t dst = yscatter ? (int64_t)yscatter[j] : j;
-          Y[dst * nrhs + rhs0 + gl] = (double)out;
+#pragma unroll
+          for (int k = 0; k < NRB; ++k)
+            if (k < nr_rhs && (k & (lpr - 1)) == gl) Y[dst * nrhs + rhs0 + k] = (double)acc[k];
         }
       }
       __syncwarp();
