@@ -73,6 +73,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory");
 }
@@ -108,34 +113,92 @@ template <> struct Op<__nv_bfloat16> {
   }
 };
 
-// Lanes per row: the smallest power of two in [4, 32] that leaves each lane
-// at most 8 vectors of the row.
-__host__ __device__ __forceinline__ int lanes_per_row(int lda, int V) {
+// One 16-byte shared-memory load of accumulator-typed values.
+__device__ __forceinline__ void load16(const float* p, float o[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load16(const double* p, double o[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x; o[1] = v.y;
+}
+
+// Register blocking for a block of NRB right-hand sides. With NRB >= 4 a
+// group of kWideLanes lanes computes kRowsWide consecutive rows at once, so
+// each x value read from shared memory feeds kRowsWide FMAs.
+constexpr int kWideLanes = 16;
+constexpr int kRowsWide = 4;
+template <int NRB> struct Blocking {
+  static constexpr bool wide = NRB >= 4;
+  static constexpr int R = wide ? kRowsWide : 1;     // rows per lane group
+};
+
+// Lanes per row: for NRB >= 4 a fixed 16; otherwise the smallest power of
+// two in [4, 32] that leaves each lane at most 8 vectors of the row.
+__host__ __device__ __forceinline__ int lanes_per_row(int lda, int V, int nrb) {
+  if (nrb >= 4) return kWideLanes;
   const int nvec = (lda + V - 1) / V;
   int l = 4;
   while (l < 32 && nvec > 8 * l) l <<= 1;
   return l;
 }
-// Rows per stage: as many as fit, rounded down to whole consumer rounds.
-__host__ __device__ __forceinline__ int rows_per_stage(int row_bytes, int stage_bytes, int lpr) {
+// Rows per stage: as many as fit, rounded down to whole warp groups (the
+// rows one consumer warp computes in one pass: 32 / lpr groups of R rows).
+__host__ __device__ __forceinline__ int rows_per_stage(int row_bytes, int stage_bytes, int wgr) {
   int rps = stage_bytes / row_bytes;
-  const int round = kConsumerWarps * (32 / lpr);
-  if (rps >= round) rps = rps / round * round;
+  if (rps >= wgr) rps = rps / wgr * wgr;
   return rps < 1 ? 1 : rps;
 }
 
+// Shared-memory layout of the operand x of one unit: columns in blocks of V
+// (one 16-byte operator vector), each block holding its V x NRB values
+// column-major by right-hand side, blocks padded to an odd number of 16-byte
+// units. The lanes of a row group read consecutive blocks in the same
+// instruction, and an odd stride puts the 8 lanes of each quarter warp on
+// distinct banks.
+template <typename Acc, int V, int NRB> struct XLayout {
+  static constexpr int Q = 16 / (int)sizeof(Acc);   // values per 16-byte load
+  static constexpr int U = V * NRB / Q;             // 16-byte loads per block
+  static constexpr int XB = (U % 2 ? U : U + 1) * Q; // block stride (values)
+  __host__ __device__ static constexpr size_t bytes(int lda) {
+    return (size_t)((lda + V - 1) / V) * XB * sizeof(Acc);
+  }
+  __device__ static int index(int c, int k) { return (c / V) * XB + (c % V) * NRB + k; }
+};
+
+// Sum of the N accumulators of a row group over its L lanes, left
+// distributed: after log2(L) halving exchanges, lane gl holds the sums of
+// the flattened entries [gl * N / L, (gl + 1) * N / L) in v[0 .. N / L).
+template <int N, int L, typename Acc>
+__device__ __forceinline__ void reduce_scatter(Acc (&v)[N], int gl) {
+  static_assert(N >= L && (L & (L - 1)) == 0, "reduce_scatter needs N >= L, L a power of two");
+#pragma unroll
+  for (int o = L / 2, n = N; o >= 1; o >>= 1, n >>= 1) {
+    const bool upper = (gl & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const Acc send = upper ? v[i] : v[i + n / 2];
+      const Acc keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
 template <typename T, int NRB>
-__global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(kTmaThreads) __maxnreg__(Blocking<NRB>::wide ? 112 : (NRB == 1 ? 56 : 72)) k_bgemv_tma(const WorkItem* __restrict__ items, int n_items,
                                                            const T* __restrict__ arena, const double* __restrict__ X,
                                                            double* __restrict__ Y,
                                                            const int32_t* __restrict__ yscatter, int nrhs,
                                                            int stage_bytes, int max_lda, int32_t* __restrict__ err) {
   using Acc = typename Op<T>::Acc;
   constexpr int V = Op<T>::V;
+  using XL = XLayout<Acc, V, NRB>;
+  constexpr int R = Blocking<NRB>::R;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stages = smem;
-  Acc* xbuf = reinterpret_cast<Acc*>(smem + (size_t)kStages * stage_bytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(xbuf + 2 * (size_t)max_lda * NRB);
+  Acc* xs = reinterpret_cast<Acc*>(smem + (size_t)kStages * stage_bytes);
+  double* xraw = reinterpret_cast<double*>(smem + (size_t)kStages * stage_bytes + XL::bytes(max_lda));
+  uint64_t* full = reinterpret_cast<uint64_t*>(xraw + (size_t)max_lda * NRB);
   uint64_t* empty = full + kStages;
   __shared__ int abort_flag;
 
@@ -165,7 +228,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __res
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
       const WorkItem w = items[u / nrb];
       const int row_bytes = w.lda * (int)sizeof(T);
-      const int rps = rows_per_stage(row_bytes, stage_bytes, lanes_per_row(w.lda, V));
+      const int wgr = (32 / lanes_per_row(w.lda, V, NRB)) * R;
+      const int rps = rows_per_stage(row_bytes, stage_bytes, wgr);
       for (int r0 = 0; r0 < w.nrows; r0 += rps) {
         if (!mbar_wait(&empty[slot], phase ^ 1u) || *(volatile int*)&abort_flag) {
           atomicExch(err, BDDC_ERR_TIMEOUT);
@@ -193,55 +257,52 @@ __global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __res
   // After a timeout a warp keeps walking the same units and reaches every
   // consumer barrier (so no other warp waits for it forever), but it no
   // longer waits on stages nor computes.
-  // The operand of the next unit is loaded into registers while the current
-  // unit is computed (kPf values per thread), so staging it costs no global
-  // memory latency; operands larger than that are staged directly.
-  constexpr int kPf = 8;
+  // The fp64 operand of the next unit is copied into `xraw` with cp.async
+  // while the current unit is computed, and converted into the padded
+  // accumulator-typed layout `xs` when that unit starts, so staging the
+  // operand costs no exposed global-memory latency.
+  // The warp groups of a stage (wgr rows each) are dealt round-robin over the
+  // consumer warps, continuing from the previous stage, so that every warp
+  // has work even when a stage holds fewer rows than one pass of all warps.
   constexpr int kCT = kConsumerWarps * 32;
   const int tid = threadIdx.x;
-  const bool prefetch = max_lda * NRB <= kPf * kCT;
   int slot = 0;
   uint32_t phase = 0;
-  int buf = 0;
+  int turn = 0;   // consumer warp that takes the next warp group
   bool aborted = false;
-  double pf[kPf];
-  auto load_operand = [&](int uu) {
+  auto prefetch_operand = [&](int uu) {
     const WorkItem wn = items[uu / nrb];
     const int r0n = (uu % nrb) * NRB, nrn = min(NRB, nrhs - r0n);
-#pragma unroll
-    for (int j = 0; j < kPf; ++j) {
-      const int i = tid + j * kCT;
+    const int n = wn.lda * NRB;
+    for (int i = tid; i < n; i += kCT) {
       const int c = i / NRB, k = i - c * NRB;
-      pf[j] = (c < wn.ncols && k < nrn) ? X[(int64_t)(wn.xoff + c) * nrhs + r0n + k] : 0.0;
+      if (c < wn.ncols && k < nrn)
+        cp_async8(xraw + i, X + (int64_t)(wn.xoff + c) * nrhs + r0n + k);
+      else
+        xraw[i] = 0.0;
     }
+    cp_async_commit();
   };
-  if (prefetch && blockIdx.x < total) load_operand(blockIdx.x);
+  if (blockIdx.x < total) prefetch_operand(blockIdx.x);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const WorkItem w = items[u / nrb];
     const int rhs0 = (u % nrb) * NRB;
     const int nr_rhs = min(NRB, nrhs - rhs0);
-    Acc* xs = xbuf + (size_t)buf * max_lda * NRB;
-    if (prefetch) {
-#pragma unroll
-      for (int j = 0; j < kPf; ++j) {
-        const int i = tid + j * kCT;
-        if (i < w.lda * NRB) xs[i] = (Acc)pf[j];
-      }
-      if (u + (int)gridDim.x < total) load_operand(u + gridDim.x);
-    } else {
-      for (int i = tid; i < w.lda * NRB; i += kCT) {
-        const int c = i / NRB, k = i - c * NRB;
-        double v = 0.0;
-        if (c < w.ncols && k < nr_rhs) v = X[(int64_t)(w.xoff + c) * nrhs + rhs0 + k];
-        xs[i] = (Acc)v;
-      }
+    const int nx = w.lda * NRB;
+    cp_async_wait_all();
+    consumer_sync();                          // operand of this unit landed; xs is free
+    for (int i = tid; i < nx; i += kCT) {
+      const int c = i / NRB, k = i - c * NRB;
+      xs[XL::index(c, k)] = (Acc)xraw[i];
     }
-    consumer_sync();
-    const int lpr = lanes_per_row(w.lda, V);
-    const int gpw = 32 / lpr;                 // rows per warp per round
+    consumer_sync();                          // xs complete; xraw is free
+    if (u + (int)gridDim.x < total) prefetch_operand(u + gridDim.x);
+    const int lpr = lanes_per_row(w.lda, V, NRB);
+    const int gpw = 32 / lpr;                 // lane groups per warp
     const int group = lane / lpr, gl = lane - group * lpr;
+    const int wgr = gpw * R;                  // rows per warp group
     const int row_bytes = w.lda * (int)sizeof(T);
-    const int rps = rows_per_stage(row_bytes, stage_bytes, lpr);
+    const int rps = rows_per_stage(row_bytes, stage_bytes, wgr);
     for (int r0 = 0; r0 < w.nrows; r0 += rps) {
       if (!aborted && (*(volatile int*)&abort_flag || !mbar_wait(&full[slot], phase))) {
         if (lane == 0) atomicExch(err, BDDC_ERR_TIMEOUT);
@@ -250,68 +311,110 @@ __global__ void __launch_bounds__(kTmaThreads) k_bgemv_tma(const WorkItem* __res
       }
       if (aborted) continue;
       const int nr = min(rps, w.nrows - r0);
+      const int ngroups = (nr + wgr - 1) / wgr;
       const T* tile = reinterpret_cast<const T*>(stages + (size_t)slot * stage_bytes);
-      for (int base = warp * gpw; base < nr; base += kConsumerWarps * gpw) {
-        const int rr = base + group;
-        Acc acc[NRB];
+      int j = warp - turn;
+      if (j < 0) j += kConsumerWarps;
+      for (; j < ngroups; j += kConsumerWarps) {
+        const int rb = j * wgr + group * R;     // first row of this lane group in the stage
+        Acc acc[R * NRB];
 #pragma unroll
-        for (int k = 0; k < NRB; ++k) acc[k] = Acc(0);
-        if (rr < nr) {
-          const T* a = tile + (size_t)rr * w.lda;
-#pragma unroll 2
-          for (int c0 = gl * V; c0 < w.lda; c0 += lpr * V) {
-            Acc av[V];
-            Op<T>::load(a + c0, av);
+        for (int e = 0; e < R * NRB; ++e) acc[e] = Acc(0);
+        for (int c0 = gl * V; c0 < w.lda; c0 += lpr * V) {
+          Acc av[R][V];
 #pragma unroll
-            for (int v = 0; v < V; ++v)
+          for (int q = 0; q < R; ++q) {
+            if (rb + q < nr) {
+              Op<T>::load(tile + (size_t)(rb + q) * w.lda + c0, av[q]);
+            } else {
 #pragma unroll
-              for (int k = 0; k < NRB; ++k) acc[k] = fma(av[v], xs[(c0 + v) * NRB + k], acc[k]);
+              for (int v = 0; v < V; ++v) av[q][v] = Acc(0);
+            }
+          }
+          const Acc* xb = xs + (c0 / V) * XL::XB;
+#pragma unroll
+          for (int uu = 0; uu < XL::U; ++uu) {
+            Acc xq[XL::Q];
+            load16(xb + uu * XL::Q, xq);
+#pragma unroll
+            for (int jj = 0; jj < XL::Q; ++jj) {
+              const int e = uu * XL::Q + jj, v = e / NRB, k = e - v * NRB;
+#pragma unroll
+              for (int q = 0; q < R; ++q) acc[q * NRB + k] = fma(av[q][v], xq[jj], acc[q * NRB + k]);
+            }
           }
         }
+        const int64_t ybase = (int64_t)w.yoff + w.row0 + r0;
+        if constexpr (Blocking<NRB>::wide) {
+          constexpr int per = R * NRB / kWideLanes;
+          reduce_scatter<R * NRB, kWideLanes>(acc, gl);
 #pragma unroll
-        for (int k = 0; k < NRB; ++k)
-          for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-        // every lane of the group holds all NRB sums; lane gl writes the
-        // columns k = gl, gl + lpr, ... (a group may have fewer lanes than NRB)
-        if (rr < nr && gl < nr_rhs) {
-          const int64_t j = (int64_t)w.yoff + w.row0 + r0 + rr;
-          const int64_t dst = yscatter ? (int64_t)yscatter[j] : j;
+          for (int i = 0; i < per; ++i) {
+            const int e = gl * per + i, q = e / NRB, k = e - q * NRB;
+            if (rb + q < nr && k < nr_rhs) {
+              const int64_t jy = ybase + rb + q;
+              const int64_t dst = yscatter ? (int64_t)yscatter[jy] : jy;
+              Y[dst * nrhs + rhs0 + k] = (double)acc[i];
+            }
+          }
+        } else {
 #pragma unroll
           for (int k = 0; k < NRB; ++k)
-            if (k < nr_rhs && (k & (lpr - 1)) == gl) Y[dst * nrhs + rhs0 + k] = (double)acc[k];
+            for (int o = lpr >> 1; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+          // every lane of the group holds all NRB sums; lane gl writes the
+          // columns k = gl, gl + lpr, ... (a group may have fewer lanes than NRB)
+          if (rb < nr && gl < nr_rhs) {
+            const int64_t jy = ybase + rb;
+            const int64_t dst = yscatter ? (int64_t)yscatter[jy] : jy;
+#pragma unroll
+            for (int k = 0; k < NRB; ++k)
+              if (k < nr_rhs && (k & (lpr - 1)) == gl) Y[dst * nrhs + rhs0 + k] = (double)acc[k];
+          }
         }
       }
+      turn = (turn + ngroups) % kConsumerWarps;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
       if (++slot == kStages) { slot = 0; phase ^= 1u; }
     }
-    buf ^= 1;
   }
+  cp_async_wait_all();
 }
 
 int g_num_sms = 0;
 
-// Stage size: about 12 KB of rows of the widest operator (at least one row),
-// so that four blocks fit on an SM: measured on GB300 with 1728 bf16
-// operators of 343 x 344, four 12 KB stages per block and four blocks per SM
-// streamed faster than fewer, larger stages.
+// Shared memory of one block: kStages stages, two operand buffers, barriers.
+template <typename T, int NRB>
+size_t x_bytes(int max_lda) {
+  return XLayout<typename Op<T>::Acc, Op<T>::V, NRB>::bytes(max_lda) + (size_t)max_lda * NRB * sizeof(double);
+}
+template <typename T, int NRB>
+size_t block_smem(int stage_bytes, int max_lda) {
+  return (size_t)kStages * stage_bytes + x_bytes<T, NRB>(max_lda) + 2 * kStages * sizeof(uint64_t);
+}
+
+// Stage size: about 12 KB of rows of the widest operator (at least one row,
+// a whole number of warp groups when that is possible), so that several
+// blocks fit on an SM: measured on GB300 with 1728 bf16 operators of
+// 343 x 344, four 12 KB stages per block and four blocks per SM streamed
+// faster than fewer, larger stages.
 template <typename T, int NRB>
 int stage_size(int max_lda) {
-  using Acc = typename Op<T>::Acc;
   const long long row = (long long)max_lda * (long long)sizeof(T);
-  const long long xs = 2LL * max_lda * NRB * (long long)sizeof(Acc) + 2 * kStages * 8;
+  const long long xs = (long long)x_bytes<T, NRB>(max_lda) + 2 * kStages * 8;
   const long long cap = (200LL * 1024 - xs) / kStages;
-  long long st = std::max<long long>(row, std::min<long long>(std::max<long long>(12 * 1024 / row, 1) * row, cap));
+  const int wgr = (32 / lanes_per_row(max_lda, Op<T>::V, NRB)) * Blocking<NRB>::R;
+  long long rows = std::max<long long>(12 * 1024 / row, 1);
+  if (rows >= wgr) rows = std::max<long long>((rows + wgr / 2) / wgr, 1) * wgr;
+  long long st = std::max<long long>(row, std::min<long long>(rows * row, cap));
   return (int)((st + 127) / 128 * 128);
 }
 
 template <typename T, int NRB>
 cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* arena, const double* X, double* Y,
                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
-  using Acc = typename Op<T>::Acc;
   const int stage_bytes = stage_size<T, NRB>(max_lda);
-  const size_t smem = (size_t)kStages * stage_bytes + 2 * (size_t)max_lda * NRB * sizeof(Acc) +
-                      2 * kStages * sizeof(uint64_t);
+  const size_t smem = block_smem<T, NRB>(stage_bytes, max_lda);
   auto kern = k_bgemv_tma<T, NRB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -333,14 +436,15 @@ cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* ar
 template <typename T>
 cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void* arena, const double* X, double* Y,
                      const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
-  using Acc = typename Op<T>::Acc;
   const T* A = static_cast<const T*>(arena);
   const size_t row = ((size_t)max_lda * sizeof(T) + 127) / 128 * 128;
-  auto fits = [&](int nrb) { return kStages * row + 2 * (size_t)max_lda * nrb * sizeof(Acc) + 64 <= 200 * 1024; };
-  if (nrhs >= 8 && fits(8)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (nrhs >= 4 && fits(4)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (nrhs >= 2 && fits(2)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (fits(1)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  const size_t xb[4] = {x_bytes<T, 1>(max_lda), x_bytes<T, 2>(max_lda), x_bytes<T, 4>(max_lda),
+                        x_bytes<T, 8>(max_lda)};
+  auto fits = [&](int i) { return kStages * row + xb[i] + 64 <= 200 * 1024; };
+  if (nrhs >= 8 && fits(3)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (nrhs >= 4 && fits(2)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (nrhs >= 2 && fits(1)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (fits(0)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
   return cudaErrorInvalidValue;
 }
 
@@ -348,9 +452,11 @@ cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void
 
 bool bgemv_tma_supported(int precision, int max_lda) {
   const size_t eb = precision == BDDC_PREC_FP64 ? 8 : precision == BDDC_PREC_FP32 ? 4 : 2;
-  const size_t acc = precision == BDDC_PREC_FP64 ? 8 : 4;
+  const size_t xb = precision == BDDC_PREC_FP64   ? x_bytes<double, 1>(max_lda)
+                    : precision == BDDC_PREC_FP32 ? x_bytes<float, 1>(max_lda)
+                                                  : x_bytes<__nv_bfloat16, 1>(max_lda);
   const size_t row = ((size_t)max_lda * eb + 127) / 128 * 128;
-  return kStages * row + 2 * (size_t)max_lda * acc + 64 <= 200 * 1024;
+  return kStages * row + xb + 64 <= 200 * 1024;
 }
 
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
