@@ -65,10 +65,13 @@ extern "C" {
 
 /* ---- options ---------------------------------------------------------- */
 /* Precision of the batched local and interior operators (the explicit
- * local constrained-Neumann and interior-Dirichlet operators). Everything
- * else (outer PCG vectors, dot products, SpMV, setup factorisations, Phi_i,
- * the coarse solve) is float64 in every mode. FP64 runs standard PCG; the
- * other modes run flexible PCG. */
+ * local constrained-Neumann and interior-Dirichlet operators). The outer
+ * PCG vectors, dot products, SpMV, setup factorisations and the coarse
+ * factorisation and solve are float64 in every mode. The coarse basis
+ * Phi_i (coarse residual Phi_i^T y_i and prolongation Phi_i u_c) is float64
+ * in the FP64 mode, and float32 with float32 accumulation in the FP32 and
+ * BF16 modes unless bddc_options_t.phi_fp64 is set. FP64 runs standard
+ * PCG; the other modes run flexible PCG. */
 #define BDDC_PREC_FP64  0
 #define BDDC_PREC_FP32  1   /* float32 operators, float32 accumulation */
 #define BDDC_PREC_BF16  2   /* bfloat16 operators, float32 accumulation */
@@ -106,6 +109,7 @@ typedef struct {
     int32_t coarse;        /* BDDC_COARSE_* */
     int32_t no_graph;      /* 1: launch every PCG iteration's kernels directly instead of
                               replaying a captured CUDA graph (for profilers) */
+    int32_t phi_fp64;      /* 1: keep Phi_i in float64 in the FP32 and BF16 modes too */
 } bddc_options_t;
 
 typedef struct {
@@ -132,6 +136,7 @@ typedef struct {
     int32_t error_subdomain;            /* subdomain of the last SINGULAR error, else -1 */
     int32_t device_error;               /* BDDC_ERR_TIMEOUT if a bounded device wait of an
                                            earlier call ran out, else 0 (bddc_query synchronises) */
+    int32_t phi_precision;              /* BDDC_PREC_FP64 or BDDC_PREC_FP32: storage of Phi_i */
 } bddc_info_t;
 
 /* Build the preconditioner (all factorisations in float64 on the host,

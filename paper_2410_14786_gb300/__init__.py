@@ -51,11 +51,14 @@ class BDDC:
     n_sub; precision in {"fp64", "fp32", "bf16"}; constraints bitmask of
     CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup;
     coarse in {"auto", "dense", "sparse"} (exact float64 coarse solve either way);
-    graph=False launches each PCG iteration directly (for profilers).
+    graph=False launches each PCG iteration directly (for profilers);
+    phi_fp64=True keeps the coarse basis Phi_i in float64 in the fp32 and
+    bf16 forms (by default it is float32 there, float64 in the fp64 form).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
-                 constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True):
+                 constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
+                 phi_fp64=False):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -67,7 +70,8 @@ class BDDC:
                             part.ctypes.data_as(C.POINTER(C.c_int32)), int(n_sub))
         opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
-                            COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1)
+                            COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
+                            1 if phi_fp64 else 0)
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim

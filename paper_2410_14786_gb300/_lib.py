@@ -41,7 +41,7 @@ class Problem(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
-                ("no_graph", C.c_int32)]
+                ("no_graph", C.c_int32), ("phi_fp64", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -52,7 +52,7 @@ class Info(C.Structure):
         "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches",
         "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
-        ("device_error", C.c_int32)]
+        ("device_error", C.c_int32), ("phi_precision", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

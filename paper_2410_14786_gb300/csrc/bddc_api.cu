@@ -91,9 +91,10 @@ std::vector<T> pack_arena(const std::vector<std::vector<double>>& ops, const std
 }
 
 // Pack per-subdomain rectangular float64 blocks (rows x cols, row-major on
-// the host) with rows padded to 16 bytes and blocks aligned to 256 bytes.
+// the host) with rows padded to 16 bytes of the storage type (eb bytes per
+// element) and blocks aligned to 32 elements.
 std::vector<double> pack_rect(const std::vector<std::vector<double>>& src, const std::vector<int>& rows,
-                              const std::vector<int>& cols, bool transpose, std::vector<int64_t>& off,
+                              const std::vector<int>& cols, bool transpose, int eb, std::vector<int64_t>& off,
                               std::vector<int32_t>& ld) {
   // transpose: src[s] is cols x rows and the block stores its transpose
   const size_t S = rows.size();
@@ -103,7 +104,7 @@ std::vector<double> pack_rect(const std::vector<std::vector<double>>& src, const
   for (size_t s = 0; s < S; ++s) {
     cur = (cur + 31) / 32 * 32;
     off[s] = cur;
-    ld[s] = padded_ld(cols[s], 8);
+    ld[s] = padded_ld(cols[s], eb);
     cur += (int64_t)rows[s] * ld[s];
   }
   std::vector<double> out((size_t)std::max<int64_t>(cur, 1), 0.0);
@@ -113,6 +114,15 @@ std::vector<double> pack_rect(const std::vector<std::vector<double>>& src, const
         out[off[s] + (int64_t)r * ld[s] + c] =
             transpose ? src[s][(size_t)c * rows[s] + r] : src[s][(size_t)r * cols[s] + c];
   return out;
+}
+
+// The streamed GEMV moves operator rows with 16-byte bulk copies and reads
+// them with 16-byte vector loads: every item must start on, and have a row
+// pitch of, a multiple of 16 bytes.
+bool items_aligned(const std::vector<WorkItem>& items, int eb) {
+  for (const WorkItem& w : items)
+    if ((w.moff * eb) % 16 != 0 || ((int64_t)w.lda * eb) % 16 != 0 || w.lda < w.ncols) return false;
+  return true;
 }
 
 // Row tiles of rectangular operators.
@@ -197,8 +207,9 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   for (int s = 0; s < S; ++s) { nGv[s] = (int)hs.sub_G[s].size(); ncv[s] = (int)hs.sub_globs[s].size(); }
   std::vector<int64_t> ptoff, poff;
   std::vector<int32_t> ptld, pld;
-  std::vector<double> phit = pack_rect(hs.Phi, ncv, nGv, true, ptoff, ptld);
-  std::vector<double> phi = pack_rect(hs.Phi, nGv, ncv, false, poff, pld);
+  const int phi_eb = elem_bytes(h->phi_prec);
+  std::vector<double> phit = pack_rect(hs.Phi, ncv, nGv, true, phi_eb, ptoff, ptld);
+  std::vector<double> phi = pack_rect(hs.Phi, nGv, ncv, false, phi_eb, poff, pld);
   auto itPT = make_rect_items(ptoff, ptld, ncv, nGv, goff, coff, 128);
   auto itP = make_rect_items(poff, pld, nGv, ncv, coff, goff, 128);
   h->n_wi_PT = (int)itPT.size();
@@ -266,6 +277,8 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     auto tG = make_items(offG, ldG, dG, goff, ttile);
     h->n_wt_I = (int)tI.size();
     h->n_wt_G = (int)tG.size();
+    if (!items_aligned(tI, elem_bytes(prec)) || !items_aligned(tG, elem_bytes(prec)))
+      return fail(BDDC_ERR_INVALID_ARG, "internal: local operator rows not 16-byte aligned");
     CUDA_TRY(upload(h, &h->d_wt_I, tI));
     CUDA_TRY(upload(h, &h->d_wt_G, tG));
   }
@@ -303,6 +316,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       for (int r0 = 0; r0 < nc; r0 += ctile)
         itC.push_back(WorkItem{poff[p], pld[p], pw[p], r0, std::min(ctile, nc - r0), p * kPanel, p * nc});
     h->n_wi_C = (int)itC.size();
+    if (!items_aligned(itC, 8)) return fail(BDDC_ERR_INVALID_ARG, "internal: coarse panels not 16-byte aligned");
     CUDA_TRY(upload(h, &h->d_wi_C, itC));
   } else if (hs.n_c) {
     // sparse Cholesky factorisation of A_c: supernode matrices and level lists
@@ -322,8 +336,17 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(upload(h, &h->d_aig_ptr, aig_ptr));
   CUDA_TRY(upload(h, &h->d_aig_col, aig_col));
   CUDA_TRY(upload(h, &h->d_aig_val, aig_val));
-  CUDA_TRY(upload(h, &h->d_phit, phit));
-  CUDA_TRY(upload(h, &h->d_phi, phi));
+  if (h->phi_prec == BDDC_PREC_FP32) {
+    std::vector<float> f32(phit.begin(), phit.end());
+    CUDA_TRY(upload(h, reinterpret_cast<float**>(&h->d_phit), f32));
+    f32.assign(phi.begin(), phi.end());
+    CUDA_TRY(upload(h, reinterpret_cast<float**>(&h->d_phi), f32));
+  } else {
+    CUDA_TRY(upload(h, reinterpret_cast<double**>(&h->d_phit), phit));
+    CUDA_TRY(upload(h, reinterpret_cast<double**>(&h->d_phi), phi));
+  }
+  if (!items_aligned(itPT, phi_eb) || !items_aligned(itP, phi_eb))
+    return fail(BDDC_ERR_INVALID_ARG, "internal: Phi rows not 16-byte aligned");
   CUDA_TRY(upload(h, &h->d_wi_PT, itPT));
   CUDA_TRY(upload(h, &h->d_wi_P, itP));
   CUDA_TRY(upload(h, &h->d_sub_goff, goff));
@@ -413,7 +436,8 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   in.coarse_update_total = h->c_update_total;
   in.coarse_levels = h->coarse_dense ? 0 : h->c_levels;
   ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
-  in.apply_bytes_1rhs = ops + 2 * 8 * in.sum_nG_nc + in.coarse_bytes +
+  in.phi_precision = h->phi_prec;
+  in.apply_bytes_1rhs = ops + 2 * (int64_t)elem_bytes(h->phi_prec) * in.sum_nG_nc + in.coarse_bytes +
                         (int64_t)(agi_val.size() + aig_val.size()) * 12 + 8 * (in.n_free + hs.n_nodes);
   return BDDC_OK;
 }
@@ -490,6 +514,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->dim = P->dim; h->ne = P->ne; h->n1 = P->ne + 1; h->n_sub = P->n_sub;
   h->precision = O->precision; h->nrhs_max = O->nrhs_max; h->device = O->device;
   h->use_graph = O->no_graph == 0;
+  h->phi_prec = (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -539,6 +564,9 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
     }
     for (int64_t n = 0; n < hs.n_nodes; ++n) info->n_interface_nodes += hs.kappa[n] >= 2;
     info->error_subdomain = -1;
+    info->precision = O->precision;
+    info->phi_precision =
+        (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
   }
   if (Ac && numerics) {
     if (hs.n_c * hs.n_c > Ac_capacity) return fail(BDDC_ERR_INVALID_ARG, "Ac capacity too small");

@@ -409,7 +409,7 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(4);
   if (h->n_c) {
     // coarse residual r_c = sum R_ci^T Phi_G^T y'_G
-    if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, h->w_yG, h->w_g,
+    if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, h->w_yG, h->w_g,
                               nullptr, nrhs, h->d_err, st)) != cudaSuccess)
       return e;
     k_coarse_gather<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx,
@@ -438,7 +438,7 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
     if (h->n_c) {
       k_coarse_scatter<<<blocks_for(h->nC_tot * nrhs), kThreads, 0, st>>>(h->nC_tot, nrhs, h->d_ccdof, h->w_uc,
                                                                           h->w_ucl);
-      if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_P, h->n_wi_P, h->max_ld_P, h->d_phi, h->w_ucl, h->w_eG,
+      if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_P, h->n_wi_P, h->max_ld_P, h->d_phi, h->w_ucl, h->w_eG,
                                 nullptr, nrhs, h->d_err, st)) != cudaSuccess)
         return e;
       eG = h->w_eG;

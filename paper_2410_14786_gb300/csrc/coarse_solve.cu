@@ -139,6 +139,51 @@ __device__ __forceinline__ double warp_dot_gather(const double* __restrict__ row
   return warp_sum((s0 + s1) + (s2 + s3));
 }
 
+// Several right-hand sides at once: columns k0 .. k0 + nr - 1 (nr <= kNR) of
+// x (row-major, nrhs per row), accumulated into lane-partial sums s[k] with
+// the matrix row read once for all of them.
+constexpr int kNR = 8;
+__device__ __forceinline__ void warp_dot_multi(const double* __restrict__ row, const double* x, int j0, int j1,
+                                               int nrhs, int k0, int nr, int lane, double (&s)[kNR]) {
+  for (int j = j0 + lane; j < j1; j += 32) {
+    const double rv = __ldg(&row[j]);
+    const double* xp = x + (int64_t)j * nrhs + k0;
+#pragma unroll
+    for (int k = 0; k < kNR; ++k)
+      if (k < nr) s[k] = fma(rv, __ldcg(xp + k), s[k]);
+  }
+}
+__device__ __forceinline__ void warp_dot_gather_multi(const double* __restrict__ row, const double* x,
+                                                      const int32_t* __restrict__ idx, int n, int nrhs, int k0,
+                                                      int nr, int lane, double (&s)[kNR]) {
+  for (int j = lane; j < n; j += 32) {
+    const double rv = __ldg(&row[j]);
+    const double* xp = x + (int64_t)__ldg(&idx[j]) * nrhs + k0;
+#pragma unroll
+    for (int k = 0; k < kNR; ++k)
+      if (k < nr) s[k] = fma(rv, __ldcg(xp + k), s[k]);
+  }
+}
+// Warp sum of the 8 lane-partial sums, left on lanes with (lane & 3) == 0:
+// that lane holds the total of column k = lane >> 2 (three halving
+// exchanges, then two full ones: 9 shuffles instead of 40).
+__device__ __forceinline__ double warp_sum8(double (&s)[kNR], int lane) {
+#pragma unroll
+  for (int o = 16, n = kNR; o >= 4; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const double send = upper ? s[i] : s[i + n / 2];
+      const double keep = upper ? s[i + n / 2] : s[i];
+      s[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double v = s[0];
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
 __device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
   const int nrhs = a.nrhs;
   if (w.kind == 0) {
@@ -146,22 +191,43 @@ __device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
     const CNodeDev nd = a.nodes[w.a];
     const double* row = a.F + nd.foff + (int64_t)w.row * nd.fld;
     const double* x = a.rp + (int64_t)nd.pos0 * nrhs;
-    for (int k = 0; k < nrhs; ++k) {
-      const double s = warp_dot(row, x, 0, w.row + 1, nrhs, k, lane);
-      if (lane == 0) a.y[(int64_t)(nd.pos0 + w.row) * nrhs + k] = s;
+    double* dst = a.y + (int64_t)(nd.pos0 + w.row) * nrhs;
+    if (nrhs == 1) {
+      const double s = warp_dot(row, x, 0, w.row + 1, 1, 0, lane);
+      if (lane == 0) dst[0] = s;
+      return;
+    }
+    for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+      const int nr = min(kNR, nrhs - k0);
+      double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
+      warp_dot_multi(row, x, 0, w.row + 1, nrhs, k0, nr, lane, s);
+      const double v = warp_sum8(s, lane);
+      if ((lane & 3) == 0 && (lane >> 2) < nr) dst[k0 + (lane >> 2)] = v;
     }
   } else {
     // r'[a] -= sum over the listed contributions, in list order, of
     // M_row . r'_P(node)
-    for (int k = 0; k < nrhs; ++k) {
+    double* dst = &a.rp[(int64_t)w.a * nrhs];
+    if (nrhs == 1) {
       double s = 0.0;
       for (int q = w.b; q < w.e; ++q) {
         const CContrib c = a.list[q];
-        s += warp_dot(a.F + c.row_off, a.rp + (int64_t)c.x_off * nrhs, 0, c.len, nrhs, k, lane);
+        s += warp_dot(a.F + c.row_off, a.rp + c.x_off, 0, c.len, 1, 0, lane);
       }
-      if (lane == 0) {
-        double* dst = &a.rp[(int64_t)w.a * nrhs + k];
-        *dst = __ldcg(dst) - s;
+      if (lane == 0) dst[0] = __ldcg(dst) - s;
+      return;
+    }
+    for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+      const int nr = min(kNR, nrhs - k0);
+      double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int q = w.b; q < w.e; ++q) {
+        const CContrib c = a.list[q];
+        warp_dot_multi(a.F + c.row_off, a.rp + (int64_t)c.x_off * nrhs, 0, c.len, nrhs, k0, nr, lane, s);
+      }
+      const double v = warp_sum8(s, lane);
+      if ((lane & 3) == 0 && (lane >> 2) < nr) {
+        double* d = dst + k0 + (lane >> 2);
+        *d = __ldcg(d) - v;
       }
     }
   }
@@ -173,10 +239,20 @@ __device__ void backward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
   const CNodeDev nd = a.nodes[w.a];
   const double* row = a.B + nd.boff + (int64_t)w.row * nd.bld;
   const double* yp = a.y + (int64_t)nd.pos0 * nrhs;
-  for (int k = 0; k < nrhs; ++k) {
-    const double s = warp_dot(row, yp, w.row, nd.p, nrhs, k, lane) +
-                     warp_dot_gather(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, nrhs, k, lane);
-    if (lane == 0) a.u[(int64_t)a.order[nd.pos0 + w.row] * nrhs + k] = s;
+  double* dst = a.u + (int64_t)a.order[nd.pos0 + w.row] * nrhs;
+  if (nrhs == 1) {
+    const double s = warp_dot(row, yp, w.row, nd.p, 1, 0, lane) +
+                     warp_dot_gather(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, 1, 0, lane);
+    if (lane == 0) dst[0] = s;
+    return;
+  }
+  for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+    const int nr = min(kNR, nrhs - k0);
+    double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
+    warp_dot_multi(row, yp, w.row, nd.p, nrhs, k0, nr, lane, s);
+    warp_dot_gather_multi(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, nrhs, k0, nr, lane, s);
+    const double v = warp_sum8(s, lane);
+    if ((lane & 3) == 0 && (lane >> 2) < nr) dst[k0 + (lane >> 2)] = v;
   }
 }
 

@@ -135,8 +135,9 @@ struct bddc_handle_s {
   int32_t* d_aig_ptr = nullptr; int32_t* d_aig_col = nullptr; double* d_aig_val = nullptr;
   // Phi_Gamma^T [nc x nG] (coarse residual) and Phi_Gamma [nG x nc]
   // (prolongation) per subdomain, float64, with their work lists
-  double* d_phit = nullptr;
-  double* d_phi = nullptr;
+  void* d_phit = nullptr;             // Phi_G^T arena (phi_prec)
+  void* d_phi = nullptr;              // Phi_G arena (phi_prec)
+  int phi_prec = BDDC_PREC_FP64;      // BDDC_PREC_FP64 or BDDC_PREC_FP32
   bddc::WorkItem* d_wi_PT = nullptr; int n_wi_PT = 0; int max_ld_PT = 0;
   bddc::WorkItem* d_wi_P = nullptr; int n_wi_P = 0; int max_ld_P = 0;
   int32_t* d_sub_goff = nullptr;      // [n_sub + 1] interface copy offsets

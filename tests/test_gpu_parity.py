@@ -24,9 +24,10 @@ def _oracle(p, mask=0):
                   constraints=mask or (CORNER | EDGE | FACE))
 
 
-def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto"):
+def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto", phi_fp64=False):
     from paper_2410_14786_gb300 import BDDC
-    return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max, coarse=coarse)
+    return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max, coarse=coarse,
+                             phi_fp64=phi_fp64)
 
 
 def _small_voronoi():
@@ -237,6 +238,25 @@ def test_apply_low_precision_error_bound(prec, tol):
     want = o.apply_nodes(r)
     err = np.linalg.norm(z - want) / np.linalg.norm(want)
     assert err < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("bf16", 3e-2)])
+def test_phi_precision_option(prec, tol):
+    # Phi_i is float32 by default in the low-precision forms; kept in float64
+    # the apply obeys the same bound, and the two differ by float32 rounding of
+    # the coarse component (operand and products rounded to 6e-8, float32
+    # accumulation over n_G <= 386 terms), far below the form's own error
+    p, mask, o = _case("3d_24_3cubed")
+    r = synth.uniform(37, o.n_nodes)
+    r[o.dir] = 0
+    want = o.apply_nodes(r)
+    g32 = _bddc(p, precision=prec, mask=mask)
+    g64 = _bddc(p, precision=prec, mask=mask, phi_fp64=True)
+    assert g32.info()["phi_precision"] == 1 and g64.info()["phi_precision"] == 0
+    z32 = g32.apply(_cuda(r)).cpu().numpy()
+    z64 = g64.apply(_cuda(r)).cpu().numpy()
+    assert np.linalg.norm(z64 - want) / np.linalg.norm(want) < tol
+    assert np.linalg.norm(z32 - z64) / np.linalg.norm(z64) < 1e-5
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])

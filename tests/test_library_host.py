@@ -153,3 +153,17 @@ def test_setup_without_device_fails_cleanly(L):
     h = C.c_void_p()
     rc = L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(h))
     assert rc == -7 and not h.value
+
+
+@pytest.mark.parametrize("precision,phi_fp64,expect", [(0, 0, 0), (1, 0, 1), (2, 0, 1), (2, 1, 0), (1, 1, 0)])
+def test_phi_precision_follows_the_form(L, precision, phi_fp64, expect):
+    """Phi_i is float64 in the FP64 form and float32 in the FP32 / BF16 forms
+    unless phi_fp64 asks for float64 (the coarse solve is float64 in all)."""
+    from paper_2410_14786_gb300 import _lib
+    prob, opts, keep = _structs(synth.config(1), precision=precision)
+    opts.phi_fp64 = phi_fp64
+    info = _lib.Info()
+    rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0)
+    assert rc == 0, L.bddc_last_error()
+    assert info.precision == precision
+    assert info.phi_precision == expect
