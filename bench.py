@@ -163,15 +163,17 @@ def run_gb300(args):
         dist.barrier()
     build.build()
 
-    p = synth.config(args.config)
+    p = synth.config(args.config, args.nrhs or None)
     nrhs = p.nrhs
     f = torch.from_numpy(np.ascontiguousarray(p.f if nrhs > 1 else p.f[:, 0])).cuda()
     forms = {}
     handles = {}
-    precs = ["fp64", "fp32", "bf16"] if not args.only else [args.only]
+    precs = ["fp64", "fp32", "bf16"] if not args.only else args.only.split(",")
     headline = args.precision if args.precision in precs else precs[-1]
     for prec in precs:
-        g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs, graph=not args.no_graph)
+        g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs, graph=not args.no_graph,
+                              tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores]
+                              if prec in ("bf16", "tf32") else "auto")
         handles[prec] = g
         forms[prec] = {"setup_s": g.info()["setup_seconds"]}
     g64 = handles.get("fp64", handles[headline])
@@ -247,10 +249,11 @@ def run_gb300(args):
     prof = head["apply_launch_ms"]
     op_ms = prof["interior_op"] + prof["interface_op"] + prof["interior_op_final"]
     op_bytes = (2 * inf["interior_op_bytes"] + inf["interface_op_bytes"]
-                + 8 * 2 * (2 * inf["n_interior"] + inf["n_interface_copies"]))
+                + 8 * 2 * nrhs * (2 * inf["n_interior"] + inf["n_interface_copies"]))
     achieved = op_bytes / (op_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_bgemv (3 launches per apply)", "peak_kind": peak_kind,
+                "traffic": None, "peak_kind": peak_kind,
+                "kernel": ("k_tc_gemm + k_tc_pack" if inf["tensor_cores"] else "k_bgemv_tma") + " (3 operator passes per apply)",
                 "bytes_per_apply": op_bytes}
 
     # end to end through the public API with host buffers (pinned)
@@ -312,17 +315,20 @@ def run_apply_only(args):
     import synth
     from paper_2410_14786_gb300 import BDDC, build
     build.build()
-    p = synth.config(2)
-    g = BDDC.from_problem(p, precision=args.precision, nrhs_max=1, graph=not args.no_graph)
-    f = torch.from_numpy(np.ascontiguousarray(p.f[:, 0])).cuda()
+    p = synth.config(args.config, args.nrhs or None)
+    g = BDDC.from_problem(p, precision=args.precision, nrhs_max=p.nrhs, graph=not args.no_graph,
+                          tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores]
+                          if args.precision in ("bf16", "tf32") else "auto")
+    f = torch.from_numpy(np.ascontiguousarray(p.f if p.nrhs > 1 else p.f[:, 0])).cuda()
     b = g.rhs(f)
     z = torch.empty_like(b)
     for _ in range(args.apply_only):
         g.apply(b, z)
     x, res = g.pcg_solve(b, rtol=RTOL, maxit=500)
     torch.cuda.synchronize()
-    print(json.dumps({"apply_only": args.apply_only, "precision": args.precision, "iters": int(res.iters[0]),
-                      "relres": float(res.relres[0])}))
+    print(json.dumps({"apply_only": args.apply_only, "precision": args.precision, "nrhs": p.nrhs,
+                      "tensor_cores": g.info()["tensor_cores"], "iters": int(max(res.iters)),
+                      "relres": float(max(res.relres))}))
     g.close()
     return 0
 
@@ -333,8 +339,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16"])
-    ap.add_argument("--only", default=None, choices=[None, "fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16", "tf32"])
+    ap.add_argument("--only", default=None,
+                    help="comma-separated forms to time (fp64, fp32, bf16, tf32); default fp64,fp32,bf16")
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="development aid: override the workload's number of right-hand sides")
+    ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
+                    help="where the bf16 / tf32 local operators run (auto: tf32 always, bf16 from 8 rhs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each PCG iteration's kernels directly (for profilers); not for timing")

@@ -69,12 +69,25 @@ extern "C" {
  * PCG vectors, dot products, SpMV, setup factorisations and the coarse
  * factorisation and solve are float64 in every mode. The coarse basis
  * Phi_i (coarse residual Phi_i^T y_i and prolongation Phi_i u_c) is float64
- * in the FP64 mode, and float32 with float32 accumulation in the FP32 and
- * BF16 modes unless bddc_options_t.phi_fp64 is set. FP64 runs standard
+ * in the FP64 mode, and float32 with float32 accumulation in the FP32,
+ * BF16 and TF32 modes unless bddc_options_t.phi_fp64 is set. FP64 runs standard
  * PCG; the other modes run flexible PCG. */
 #define BDDC_PREC_FP64  0
 #define BDDC_PREC_FP32  1   /* float32 operators, float32 accumulation */
 #define BDDC_PREC_BF16  2   /* bfloat16 operators, float32 accumulation */
+#define BDDC_PREC_TF32  3   /* float32 operators read as TF32 by the tensor cores
+                               (tcgen05 kind::tf32), float32 accumulation */
+
+/* Where the local and interior operators run. AUTO: tensor cores (tcgen05,
+ * operators stored in the MMA tile layout) for TF32, and for BF16 when
+ * nrhs_max >= 8; the streamed CUDA-core GEMV otherwise. ON: tensor cores
+ * for BF16 and TF32 whatever nrhs_max. OFF: CUDA cores (invalid with TF32).
+ * On the tensor cores the float64 operand is split into a high and a low
+ * part in the operator's format (two MMAs per K step), so only the operator
+ * carries the form's rounding. */
+#define BDDC_TC_AUTO 0
+#define BDDC_TC_ON   1
+#define BDDC_TC_OFF  2
 
 /* Coarse solve (always exact, float64). DENSE: the explicit inverse of A_c,
  * applied as one matrix-vector product (n_c^2 float64 multiply-adds).
@@ -109,7 +122,8 @@ typedef struct {
     int32_t coarse;        /* BDDC_COARSE_* */
     int32_t no_graph;      /* 1: launch every PCG iteration's kernels directly instead of
                               replaying a captured CUDA graph (for profilers) */
-    int32_t phi_fp64;      /* 1: keep Phi_i in float64 in the FP32 and BF16 modes too */
+    int32_t phi_fp64;      /* 1: keep Phi_i in float64 in the FP32, BF16 and TF32 modes too */
+    int32_t tensor_cores;  /* BDDC_TC_* */
 } bddc_options_t;
 
 typedef struct {
@@ -137,6 +151,7 @@ typedef struct {
     int32_t device_error;               /* BDDC_ERR_TIMEOUT if a bounded device wait of an
                                            earlier call ran out, else 0 (bddc_query synchronises) */
     int32_t phi_precision;              /* BDDC_PREC_FP64 or BDDC_PREC_FP32: storage of Phi_i */
+    int32_t tensor_cores;               /* 1 if the local operators run on the tensor cores */
 } bddc_info_t;
 
 /* Build the preconditioner (all factorisations in float64 on the host,

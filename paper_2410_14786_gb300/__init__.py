@@ -14,10 +14,11 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64,  # noqa: F401
+from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64, PREC_TF32,  # noqa: F401
                    BDDCError)
 
-PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16}
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16, "tf32": PREC_TF32}
+TENSOR_CORES = {"auto": _lib.TC_AUTO, True: _lib.TC_ON, False: _lib.TC_OFF}
 COARSE = {"auto": _lib.COARSE_AUTO, "dense": _lib.COARSE_DENSE, "sparse": _lib.COARSE_SPARSE}
 
 
@@ -52,13 +53,15 @@ class BDDC:
     CORNERS | EDGES | FACES (0 = all); nrhs_max; host threads for setup;
     coarse in {"auto", "dense", "sparse"} (exact float64 coarse solve either way);
     graph=False launches each PCG iteration directly (for profilers);
-    phi_fp64=True keeps the coarse basis Phi_i in float64 in the fp32 and
-    bf16 forms (by default it is float32 there, float64 in the fp64 form).
+    phi_fp64=True keeps the coarse basis Phi_i in float64 in the fp32, bf16
+    and tf32 forms (by default it is float32 there, float64 in the fp64 form);
+    tensor_cores in {"auto", True, False}: where the local operators of the
+    bf16 / tf32 forms run (auto: tf32 always, bf16 from nrhs_max 8 on).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
-                 phi_fp64=False):
+                 phi_fp64=False, tensor_cores="auto"):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -71,7 +74,7 @@ class BDDC:
         opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
                             COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
-                            1 if phi_fp64 else 0)
+                            1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores])
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim

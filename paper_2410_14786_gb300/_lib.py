@@ -21,7 +21,8 @@ ERR_TIMEOUT = -5
 ERR_BREAKDOWN = -6
 ERR_NO_DEVICE = -7
 
-PREC_FP64, PREC_FP32, PREC_BF16 = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3
+TC_AUTO, TC_ON, TC_OFF = 0, 1, 2
 CORNERS, EDGES, FACES = 1, 2, 4
 COARSE_AUTO, COARSE_DENSE, COARSE_SPARSE = 0, 1, 2
 
@@ -41,7 +42,8 @@ class Problem(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
-                ("no_graph", C.c_int32), ("phi_fp64", C.c_int32)]
+                ("no_graph", C.c_int32), ("phi_fp64", C.c_int32),
+                ("tensor_cores", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -52,7 +54,8 @@ class Info(C.Structure):
         "interior_op_bytes", "interface_op_bytes", "n_interface_copies", "kernel_launches",
         "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
-        ("device_error", C.c_int32), ("phi_precision", C.c_int32)]
+        ("device_error", C.c_int32), ("phi_precision", C.c_int32),
+        ("tensor_cores", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

@@ -55,8 +55,16 @@ cudaError_t upload(bddc_handle_s* h, T** p, const std::vector<T>& v) {
   return e;
 }
 
+// The local operators run on the tensor cores: TF32 always, BF16 when asked
+// or when blocks of at least kTcMinRhs right-hand sides are expected.
+bool tc_enabled(const bddc_options_t* O) {
+  return O->precision == BDDC_PREC_TF32 ||
+         (O->precision == BDDC_PREC_BF16 &&
+          (O->tensor_cores == BDDC_TC_ON || (O->tensor_cores == BDDC_TC_AUTO && O->nrhs_max >= kTcMinRhs)));
+}
+
 int elem_bytes(int precision) {
-  return precision == BDDC_PREC_FP64 ? 8 : precision == BDDC_PREC_FP32 ? 4 : 2;
+  return precision == BDDC_PREC_FP64 ? 8 : (precision == BDDC_PREC_FP32 || precision == BDDC_PREC_TF32) ? 4 : 2;
 }
 
 // leading dimension padded so that every row starts on a 16-byte boundary
@@ -259,28 +267,76 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     arena_bytes += a.size() * sizeof(__nv_bfloat16);
     return upload(h, reinterpret_cast<__nv_bfloat16**>(dst), a);
   };
-  CUDA_TRY(up_arena(hs.AIIinv, dI, offI, ldI, &h->d_aii));
-  CUDA_TRY(up_arena(hs.Kgg, dG, offG, ldG, &h->d_kgg));
-  const int tile = 64;
-  auto itI = make_items(offI, ldI, dI, ioff, tile);
-  auto itG = make_items(offG, ldG, dG, goff, tile);
-  h->n_wi_I = (int)itI.size();
-  h->n_wi_G = (int)itG.size();
-  h->max_cols_I = ldI.empty() ? 0 : *std::max_element(ldI.begin(), ldI.end());
-  h->max_cols_G = ldG.empty() ? 0 : *std::max_element(ldG.begin(), ldG.end());
-  CUDA_TRY(upload(h, &h->d_wi_I, itI));
-  CUDA_TRY(upload(h, &h->d_wi_G, itG));
-  h->use_tma = bgemv_tma_supported(prec, h->max_cols_I) && bgemv_tma_supported(prec, h->max_cols_G);
-  {
-    const int ttile = 128;
-    auto tI = make_items(offI, ldI, dI, ioff, ttile);
-    auto tG = make_items(offG, ldG, dG, goff, ttile);
-    h->n_wt_I = (int)tI.size();
-    h->n_wt_G = (int)tG.size();
-    if (!items_aligned(tI, elem_bytes(prec)) || !items_aligned(tG, elem_bytes(prec)))
-      return fail(BDDC_ERR_INVALID_ARG, "internal: local operator rows not 16-byte aligned");
-    CUDA_TRY(upload(h, &h->d_wt_I, tI));
-    CUDA_TRY(upload(h, &h->d_wt_G, tG));
+  int64_t opbytes_I = 0, opbytes_G = 0;
+  if (h->use_tc) {
+    // tensor-core path: operators in the MMA tile layout, no row-major copy
+    auto up_tc = [&](auto tag, const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
+                     const std::vector<int32_t>& xo, void** arena, TcUnit** units, int* n_units, int32_t** sl,
+                     int64_t* n_sl, int32_t** opi, int64_t* cols, int64_t* bytes) -> int {
+      using T = decltype(tag);
+      TcPacked<T> pk;
+      tc_pack_host<T>(ops, dims, xo, pk);
+      *bytes = (int64_t)(pk.arena.size() * sizeof(T));
+      arena_bytes += pk.arena.size() * sizeof(T);
+      *n_units = (int)pk.units.size();
+      *n_sl = (int64_t)pk.slice_op.size();
+      *cols = pk.cols_total;
+      CUDA_TRY(upload(h, reinterpret_cast<T**>(arena), pk.arena));
+      CUDA_TRY(upload(h, units, pk.units));
+      CUDA_TRY(upload(h, sl, pk.slice_op));
+      CUDA_TRY(upload(h, opi, pk.opinfo));
+      return BDDC_OK;
+    };
+    int rc2;
+    if (prec == BDDC_PREC_BF16) {
+      if ((rc2 = up_tc(__nv_bfloat16{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I,
+                       &h->n_tcs_I, &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I)) != BDDC_OK)
+        return rc2;
+      if ((rc2 = up_tc(__nv_bfloat16{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G,
+                       &h->n_tcs_G, &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G)) != BDDC_OK)
+        return rc2;
+    } else {
+      if ((rc2 = up_tc(float{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I, &h->n_tcs_I,
+                       &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I)) != BDDC_OK)
+        return rc2;
+      if ((rc2 = up_tc(float{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G, &h->n_tcs_G,
+                       &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G)) != BDDC_OK)
+        return rc2;
+    }
+    const size_t bbytes = tc_operand_bytes(prec, std::max(h->tcB_cols_I, h->tcB_cols_G), h->nrhs_max);
+    void* pB = nullptr;
+    CUDA_TRY(cudaMalloc(&pB, bbytes));
+    h->allocations.push_back(pB);
+    h->d_tcB = pB;
+    h->use_tma = false;
+  } else {
+    CUDA_TRY(up_arena(hs.AIIinv, dI, offI, ldI, &h->d_aii));
+    CUDA_TRY(up_arena(hs.Kgg, dG, offG, ldG, &h->d_kgg));
+    const int tile = 64;
+    auto itI = make_items(offI, ldI, dI, ioff, tile);
+    auto itG = make_items(offG, ldG, dG, goff, tile);
+    h->n_wi_I = (int)itI.size();
+    h->n_wi_G = (int)itG.size();
+    h->max_cols_I = ldI.empty() ? 0 : *std::max_element(ldI.begin(), ldI.end());
+    h->max_cols_G = ldG.empty() ? 0 : *std::max_element(ldG.begin(), ldG.end());
+    CUDA_TRY(upload(h, &h->d_wi_I, itI));
+    CUDA_TRY(upload(h, &h->d_wi_G, itG));
+    h->use_tma = bgemv_tma_supported(prec, h->max_cols_I) && bgemv_tma_supported(prec, h->max_cols_G);
+    {
+      const int ttile = 128;
+      auto tI = make_items(offI, ldI, dI, ioff, ttile);
+      auto tG = make_items(offG, ldG, dG, goff, ttile);
+      h->n_wt_I = (int)tI.size();
+      h->n_wt_G = (int)tG.size();
+      if (!items_aligned(tI, elem_bytes(prec)) || !items_aligned(tG, elem_bytes(prec)))
+        return fail(BDDC_ERR_INVALID_ARG, "internal: local operator rows not 16-byte aligned");
+      CUDA_TRY(upload(h, &h->d_wt_I, tI));
+      CUDA_TRY(upload(h, &h->d_wt_G, tG));
+    }
+    for (int s = 0; s < S; ++s) {
+      opbytes_I += (int64_t)dI[s] * ldI[s] * elem_bytes(prec);
+      opbytes_G += (int64_t)dG[s] * ldG[s] * elem_bytes(prec);
+    }
   }
   h->coarse_dense = hs.coarse_dense;
   if (hs.n_c && hs.coarse_dense) {
@@ -422,15 +478,13 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   }
   in.operator_bytes = (int64_t)arena_bytes;
   in.coarse_bytes = in_coarse_bytes;
-  const int eb = elem_bytes(prec);
   // compulsory HBM bytes of one apply (nrhs = 1): operators as stored (A_II^-1
   // read twice), Phi rows twice, coarse inverse once, the sparse couplings,
   // the input r and the output z.
   int64_t ops = 0;
-  for (int s = 0; s < S; ++s) {
-    in.interior_op_bytes += (int64_t)dI[s] * ldI[s] * eb;
-    in.interface_op_bytes += (int64_t)dG[s] * ldG[s] * eb;
-  }
+  in.interior_op_bytes = opbytes_I;
+  in.interface_op_bytes = opbytes_G;
+  in.tensor_cores = h->use_tc ? 1 : 0;
   in.n_interface_copies = h->nG_tot;
   in.coarse_factor_entries = h->c_nnz;
   in.coarse_update_total = h->c_update_total;
@@ -515,6 +569,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->precision = O->precision; h->nrhs_max = O->nrhs_max; h->device = O->device;
   h->use_graph = O->no_graph == 0;
   h->phi_prec = (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
+  h->use_tc = tc_enabled(O);
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -567,6 +622,7 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
     info->precision = O->precision;
     info->phi_precision =
         (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
+    info->tensor_cores = tc_enabled(O) ? 1 : 0;
   }
   if (Ac && numerics) {
     if (hs.n_c * hs.n_c > Ac_capacity) return fail(BDDC_ERR_INVALID_ARG, "Ac capacity too small");

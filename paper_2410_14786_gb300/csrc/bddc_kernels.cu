@@ -350,8 +350,11 @@ cudaError_t bgemv(int precision, const WorkItem* items, int n_items, int max_lda
 
 // One batched application of the interior (A_II^-1) or interface (K_GG)
 // operators of all subdomains.
+// Y = Op X over the interior or interface operators; counts its launches.
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
                      cudaStream_t st) {
+  if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
+  h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)
     return interior ? launch_bgemv_tma(h->precision, h->d_wt_I, h->n_wt_I, h->max_cols_I, h->d_aii, X, Y, yscatter,
                                        nrhs, h->d_err, st)
@@ -372,7 +375,7 @@ cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double
   if (h->n_gu)
     k_zero_nodes<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, x);
   cudaError_t e = local_op(h, true, h->w_rI, x, h->d_inode, nrhs, st);
-  h->launches += 1 + (h->n_gu > 0) + (h->n_wi_I > 0);
+  h->launches += 1 + (h->n_gu > 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -392,7 +395,6 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(1);
   // t_I = A_II^-1 r_I
   if ((e = local_op(h, true, h->w_rI, h->w_tI, nullptr, nrhs, st)) != cudaSuccess) return e;
-  h->launches += h->n_wi_I > 0;
   mark(2);
   if (h->nG_tot) {
     // y'_G = W r_G - A_GI t_I; z_G = K_GG y'_G
@@ -404,7 +406,6 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(3);
   if (h->nG_tot) {
     if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, st)) != cudaSuccess) return e;
-    h->launches++;
   }
   mark(4);
   if (h->n_c) {
@@ -459,7 +460,6 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   h->launches++;
   mark(8);
   if ((e = local_op(h, true, h->w_bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
-  h->launches += h->n_wi_I > 0;
   mark(9);
   return cudaGetLastError();
 }

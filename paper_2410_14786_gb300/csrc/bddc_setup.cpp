@@ -66,7 +66,10 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
   if (P->ne < 1 || P->ne > (P->dim == 2 ? 20000 : 1000)) { err = "ne out of range"; return BDDC_ERR_INVALID_ARG; }
   if (P->n_sub < 1) { err = "n_sub must be >= 1"; return BDDC_ERR_INVALID_ARG; }
   if (!P->elem_sigma || !P->elem_subdomain) { err = "null problem arrays"; return BDDC_ERR_INVALID_ARG; }
-  if (O->precision < BDDC_PREC_FP64 || O->precision > BDDC_PREC_BF16) { err = "unknown precision"; return BDDC_ERR_INVALID_ARG; }
+  if (O->precision < BDDC_PREC_FP64 || O->precision > BDDC_PREC_TF32) { err = "unknown precision"; return BDDC_ERR_INVALID_ARG; }
+  if (O->tensor_cores < BDDC_TC_AUTO || O->tensor_cores > BDDC_TC_OFF) { err = "unknown tensor_cores mode"; return BDDC_ERR_INVALID_ARG; }
+  if (O->tensor_cores == BDDC_TC_OFF && O->precision == BDDC_PREC_TF32) { err = "TF32 needs the tensor cores"; return BDDC_ERR_INVALID_ARG; }
+  if (O->tensor_cores == BDDC_TC_ON && (O->precision == BDDC_PREC_FP64 || O->precision == BDDC_PREC_FP32)) { err = "tensor cores run the BF16 and TF32 forms only"; return BDDC_ERR_INVALID_ARG; }
   if (O->nrhs_max < 1 || O->nrhs_max > 64) { err = "nrhs_max must be in [1, 64]"; return BDDC_ERR_INVALID_ARG; }
   if (O->constraints & ~7u) { err = "unknown constraint bits"; return BDDC_ERR_INVALID_ARG; }
   if (O->coarse < BDDC_COARSE_AUTO || O->coarse > BDDC_COARSE_SPARSE) { err = "unknown coarse mode"; return BDDC_ERR_INVALID_ARG; }

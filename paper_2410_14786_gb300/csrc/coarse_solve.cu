@@ -143,25 +143,46 @@ __device__ __forceinline__ double warp_dot_gather(const double* __restrict__ row
 // x (row-major, nrhs per row), accumulated into lane-partial sums s[k] with
 // the matrix row read once for all of them.
 constexpr int kNR = 8;
+// Four elements per lane per round (as in warp_dot): out-of-range elements
+// read a valid position and are weighted by zero, so all loads of a round
+// are independent and in flight together.
 __device__ __forceinline__ void warp_dot_multi(const double* __restrict__ row, const double* x, int j0, int j1,
                                                int nrhs, int k0, int nr, int lane, double (&s)[kNR]) {
-  for (int j = j0 + lane; j < j1; j += 32) {
-    const double rv = __ldg(&row[j]);
-    const double* xp = x + (int64_t)j * nrhs + k0;
+  for (int j = j0 + lane; j < j1; j += 128) {
+    double rv[4];
+    const double* xp[4];
 #pragma unroll
-    for (int k = 0; k < kNR; ++k)
-      if (k < nr) s[k] = fma(rv, __ldcg(xp + k), s[k]);
+    for (int t = 0; t < 4; ++t) {
+      const bool in = j + 32 * t < j1;
+      rv[t] = in ? __ldg(&row[j + 32 * t]) : 0.0;
+      xp[t] = x + (int64_t)(in ? j + 32 * t : j) * nrhs + k0;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int k = 0; k < kNR; ++k)
+        if (k < nr) s[k] = fma(rv[t], __ldcg(xp[t] + k), s[k]);
   }
 }
 __device__ __forceinline__ void warp_dot_gather_multi(const double* __restrict__ row, const double* x,
                                                       const int32_t* __restrict__ idx, int n, int nrhs, int k0,
                                                       int nr, int lane, double (&s)[kNR]) {
-  for (int j = lane; j < n; j += 32) {
-    const double rv = __ldg(&row[j]);
-    const double* xp = x + (int64_t)__ldg(&idx[j]) * nrhs + k0;
+  for (int j = lane; j < n; j += 128) {
+    double rv[4];
+    int32_t ix[4];
 #pragma unroll
-    for (int k = 0; k < kNR; ++k)
-      if (k < nr) s[k] = fma(rv, __ldcg(xp + k), s[k]);
+    for (int t = 0; t < 4; ++t) {
+      const bool in = j + 32 * t < n;
+      rv[t] = in ? __ldg(&row[j + 32 * t]) : 0.0;
+      ix[t] = __ldg(&idx[in ? j + 32 * t : j]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double* xp = x + (int64_t)ix[t] * nrhs + k0;
+#pragma unroll
+      for (int k = 0; k < kNR; ++k)
+        if (k < nr) s[k] = fma(rv[t], __ldcg(xp + k), s[k]);
+    }
   }
 }
 // Warp sum of the 8 lane-partial sums, left on lanes with (lane & 3) == 0:

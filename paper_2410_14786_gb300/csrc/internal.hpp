@@ -34,6 +34,26 @@ struct CContrib {
   int64_t pad;
 };
 
+// Tensor-core batched GEMM (bddc_tc_gemm.cu). A dense n x n operator is
+// stored as chunks of up to 128 rows x kTcChunkK(precision) columns in the
+// canonical no-swizzle K-major layout of tcgen05.mma: core matrices of 8 rows
+// x 16 bytes, ordered [8-row group][16-byte column slice][8 rows][16 bytes],
+// so the valid rows of a chunk are one contiguous prefix. One unit is up to
+// kTcGroup row tiles of one operator; its chunks are stored in stream order
+// (column chunk outer, row tile inner).
+constexpr int kTcRows = 128;      // rows per tile (MMA M)
+constexpr int kTcGroup = 8;       // row tiles per unit (TMEM: 8 x N <= 512 columns)
+constexpr int kTcMinRhs = 8;      // nrhs_max from which the BF16 form uses tensor cores
+struct TcUnit {
+  int64_t aoff;   // element offset of the unit's first chunk in the tiled arena
+  int32_t n;      // operator dimension
+  int32_t g;      // row tiles in the unit
+  int32_t row0;   // first row of the unit
+  int32_t xoff;   // first entry of the operand in the compact X buffer
+  int32_t yoff;   // first entry of the result in the compact Y buffer
+  int32_t kbase;  // first column of the operator in the packed operand buffer
+};
+
 // One row tile of one dense operator in a batched GEMV launch:
 // Y[yoff + row0 + r] = sum_c Op[row0 + r, c] * X[xoff + c], r < nrows.
 struct WorkItem {
@@ -175,6 +195,15 @@ struct bddc_handle_s {
   bddc::WorkItem* d_wt_I = nullptr; int n_wt_I = 0;
   bddc::WorkItem* d_wt_G = nullptr; int n_wt_G = 0;
   bool use_tma = false;
+  // tensor-core path: tiled arenas (d_aii / d_kgg then hold the tiled layout)
+  bool use_tc = false;
+  bddc::TcUnit* d_tcu_I = nullptr; int n_tcu_I = 0;
+  bddc::TcUnit* d_tcu_G = nullptr; int n_tcu_G = 0;
+  int32_t* d_tcs_I = nullptr; int64_t n_tcs_I = 0;   // operand slice -> operator (interior)
+  int32_t* d_tcs_G = nullptr; int64_t n_tcs_G = 0;
+  int32_t* d_tcop_I = nullptr; int32_t* d_tcop_G = nullptr;   // per operator: {xoff, n, kbase, slice0}
+  void* d_tcB = nullptr;               // packed operand (hi/lo), sized for the widest nrhs
+  int64_t tcB_cols_I = 0, tcB_cols_G = 0;   // sum of padded operator widths
   int max_cols_I = 0, max_cols_G = 0;
   int max_nc = 0;                     // most constraints of one subdomain
   // apply workspace (nrhs_max columns)

@@ -1,9 +1,11 @@
 // Launch wrappers for the libbddc device kernels (sm_103a).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "internal.hpp"
 
@@ -21,6 +23,35 @@ bool bgemv_tma_supported(int precision, int max_lda);
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
                              cudaStream_t st);
+
+// Tensor-core batched GEMM for blocks of right-hand sides (bddc_tc_gemm.cu).
+// Host packing of dense n x n operators (row-major float64) into the tiled
+// layout; per operator opinfo holds {xoff, n, first packed column, first
+// 16-byte column slice}, slice_op maps every 16-byte column slice of the
+// packed operand to its operator.
+template <typename T> struct TcCvt;
+template <> struct TcCvt<float> {
+  static float from(double v) { return (float)v; }
+};
+template <> struct TcCvt<__nv_bfloat16> {
+  static __nv_bfloat16 from(double v) { return __float2bfloat16_rn((float)v); }
+};
+template <typename T> struct TcPacked {
+  std::vector<T> arena;
+  std::vector<TcUnit> units;
+  std::vector<int32_t> slice_op;
+  std::vector<int32_t> opinfo;
+  int64_t cols_total = 0;
+};
+template <typename T>
+void tc_pack_host(const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
+                  const std::vector<int32_t>& xoff, TcPacked<T>& out);
+// Bytes of the packed operand buffer for operators of cols_total padded columns.
+size_t tc_operand_bytes(int precision, int64_t cols_total, int nrhs_max);
+// Y = Op X over the interior (A_II^-1) or interface (K_GG) operators;
+// precision BDDC_PREC_BF16 (kind::f16) or BDDC_PREC_TF32 (kind::tf32).
+cudaError_t launch_tc_gemm(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter,
+                           int nrhs, cudaStream_t st);
 
 // Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
 // u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
