@@ -405,7 +405,10 @@ int stage_size(int max_lda) {
   const long long cap = (200LL * 1024 - xs) / kStages;
   const int wgr = (32 / lanes_per_row(max_lda, Op<T>::V, NRB)) * Blocking<NRB>::R;
   long long rows = std::max<long long>(12 * 1024 / row, 1);
-  if (rows >= wgr) rows = std::max<long long>((rows + wgr / 2) / wgr, 1) * wgr;
+  if (rows >= wgr)
+    rows = std::max<long long>((rows + wgr / 2) / wgr, 1) * wgr;
+  else if ((long long)wgr * row <= cap)
+    rows = wgr;   // wide rows: one whole warp group per stage rather than a partial one
   long long st = std::max<long long>(row, std::min<long long>(rows * row, cap));
   return (int)((st + 127) / 128 * 128);
 }

@@ -22,7 +22,8 @@ struct CNodeDev {
 // One warp's unit of a coarse-sweep level: kind 0 = row `row` of L_PP^-1 of
 // node `a` (forward), kind 1 = all contributions to the dof at elimination
 // position `a` from this level (contributions [b, e)), kind 2 = row `row` of
-// the backward matrix of node `a`.
+// the backward matrix of node `a`. In the row-blocked lists (several
+// right-hand sides) kinds 0 and 2 cover rows [row, row + b).
 struct CUnit {
   int32_t kind, a, row, b, e;
 };
@@ -187,7 +188,9 @@ struct bddc_handle_s {
   int32_t* d_corder = nullptr;        // elimination position -> coarse dof
   int32_t* d_clvl = nullptr;          // unit offsets: [L+1 forward][L+1 backward], then n_c
   unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
-  int c_levels = 0, c_grid = 0, c_block = 0;
+  bddc::CUnit* d_cunits4 = nullptr;   // the same with kinds 0 and 2 blocked by 4 rows
+  int32_t* d_clvl4 = nullptr;
+  int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0;
   int64_t c_nnz = 0, c_update_total = 0;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;

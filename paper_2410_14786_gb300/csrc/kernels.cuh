@@ -93,6 +93,6 @@ enum IntSlot { I_ACTIVE = 0, I_ITERS, I_STATUS, I_COUNT };
 // global int flags after the per-column ones: [0] active columns, [1] breakdown,
 // [2] device error (BDDC_ERR_TIMEOUT from a bounded wait), sticky until setup
 constexpr int kGlobalFlags = 3;
-constexpr int kRedBlocks = 304;   // 2 x 152 SMs for the dot-product partials
+constexpr int kRedBlocks = 1216;  // 8 x 152 SMs: blocks (and fixed-order partials) of the reducing kernels
 
 }  // namespace bddc
