@@ -272,7 +272,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     // tensor-core path: operators in the MMA tile layout, no row-major copy
     auto up_tc = [&](auto tag, const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
                      const std::vector<int32_t>& xo, void** arena, TcUnit** units, int* n_units, int32_t** sl,
-                     int64_t* n_sl, int32_t** opi, int64_t* cols, int64_t* bytes) -> int {
+                     int64_t* n_sl, int32_t** opi, int64_t* cols, int64_t* bytes, int* maxg) -> int {
       using T = decltype(tag);
       TcPacked<T> pk;
       tc_pack_host<T>(ops, dims, xo, pk);
@@ -281,6 +281,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       *n_units = (int)pk.units.size();
       *n_sl = (int64_t)pk.slice_op.size();
       *cols = pk.cols_total;
+      *maxg = pk.max_g;
       CUDA_TRY(upload(h, reinterpret_cast<T**>(arena), pk.arena));
       CUDA_TRY(upload(h, units, pk.units));
       CUDA_TRY(upload(h, sl, pk.slice_op));
@@ -290,17 +291,17 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     int rc2;
     if (prec == BDDC_PREC_BF16) {
       if ((rc2 = up_tc(__nv_bfloat16{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I,
-                       &h->n_tcs_I, &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I)) != BDDC_OK)
+                       &h->n_tcs_I, &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I, &h->tc_maxg_I)) != BDDC_OK)
         return rc2;
       if ((rc2 = up_tc(__nv_bfloat16{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G,
-                       &h->n_tcs_G, &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G)) != BDDC_OK)
+                       &h->n_tcs_G, &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G, &h->tc_maxg_G)) != BDDC_OK)
         return rc2;
     } else {
       if ((rc2 = up_tc(float{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I, &h->n_tcs_I,
-                       &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I)) != BDDC_OK)
+                       &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I, &h->tc_maxg_I)) != BDDC_OK)
         return rc2;
       if ((rc2 = up_tc(float{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G, &h->n_tcs_G,
-                       &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G)) != BDDC_OK)
+                       &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G, &h->tc_maxg_G)) != BDDC_OK)
         return rc2;
     }
     const size_t bbytes = tc_operand_bytes(prec, std::max(h->tcB_cols_I, h->tcB_cols_G), h->nrhs_max);

@@ -50,7 +50,7 @@ constexpr int kChunkBytes = kTcRows * 128;      // 16 KB operator chunk
 constexpr int kBStageBytes = 2 * 64 * 128;      // hi + lo, up to 64 right-hand sides
 constexpr int kSmemA = kAStages * kChunkBytes;
 constexpr int kSmemB = kBStages * kBStageBytes;
-constexpr int kNumBars = 2 * kAStages + 2 * kBStages + 3;
+constexpr int kNumBars = 2 * kAStages + 2 * kBStages + 5;
 constexpr int kSmemTc = kSmemA + kSmemB + kNumBars * 8 + 16;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
@@ -218,7 +218,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     k_tc_gemm(const TcUnit* __restrict__ units, int n_units, const T* __restrict__ arena,
               const unsigned char* __restrict__ Bp, double* __restrict__ Y, const int32_t* __restrict__ yscatter,
-              int nrhs, int N, int32_t* __restrict__ err) {
+              int nrhs, int N, int nbuf, int32_t* __restrict__ err) {
   constexpr int esz = (int)sizeof(T), EPS = 16 / esz, KCH = 128 / esz, KSTEP = 2 * EPS;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;
@@ -227,9 +227,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   uint64_t* a_empty = a_full + kAStages;
   uint64_t* b_full = a_empty + kAStages;
   uint64_t* b_empty = b_full + kBStages;
-  uint64_t* acc_full = b_empty + kBStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* fin = acc_empty + 1;
+  uint64_t* acc_full = b_empty + kBStages;   // [2]: accumulator buffer b complete
+  uint64_t* acc_empty = acc_full + 2;        // [2]: accumulator buffer b read out
+  uint64_t* fin = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -237,8 +237,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kAStages; ++s) { mbar_init(&a_full[s], 1); mbar_init(&a_empty[s], 1); }
     for (int s = 0; s < kBStages; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
     mbar_init(fin, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -311,7 +310,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         const TcUnit w = units[u];
         const int kpad = tc_kpad(w.n, esz);
         const int nkc = (kpad + KCH - 1) / KCH;
-        if (nunit > 0 && (!mbar_wait(acc_empty, (uint32_t)(nunit - 1) & 1u) || aborted())) { fail(); break; }
+        // accumulators: nbuf buffers of 256 columns (or one of 512), used in turn
+        const int ab = nunit % nbuf, use = nunit / nbuf;
+        if (use > 0 && (!mbar_wait(&acc_empty[ab], (uint32_t)(use - 1) & 1u) || aborted())) { fail(); break; }
         tc_fence_after();
         for (int kc = 0; kc < nkc && ok; ++kc) {
           const int kw = min(KCH, kpad - kc * KCH), nsl = kw / EPS;
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             if (!mbar_wait(&a_full[as], aph) || aborted()) { fail(); ok = false; break; }
             tc_fence_after();
             const uint32_t ast = smem_u32(sA + as * kChunkBytes);
-            const uint32_t d = tmem + (uint32_t)(mt * N);
+            const uint32_t d = tmem + (uint32_t)(ab * 256 + mt * N);
             for (int ks = 0; ks < kw / KSTEP; ++ks) {
               const uint64_t ad = sdesc(ast + ks * 256u, 128u, sbo);
               mma<T>(d, ad, sdesc(bst + ks * 256u, 128u, sbo), id, (kc | ks) != 0);
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
           mma_commit(&b_empty[bs]);
           if (++bs == kBStages) { bs = 0; bph ^= 1u; }
         }
-        if (ok) mma_commit(acc_full);
+        if (ok) mma_commit(&acc_full[ab]);
       }
       // every MMA issued has completed before tensor memory is freed
       mma_commit(fin);
@@ -348,7 +349,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     int nunit = 0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++nunit) {
       const TcUnit w = units[u];
-      bool ok = mbar_wait(acc_full, (uint32_t)nunit & 1u) && !aborted();
+      const int ab = nunit % nbuf, use = nunit / nbuf;
+      bool ok = mbar_wait(&acc_full[ab], (uint32_t)use & 1u) && !aborted();
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
         if (lane == 0) fail();
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * N + c0), v);
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 256 + mt * N + c0), v);
           if (dst >= 0) {
 #pragma unroll
             for (int k = 0; k < 16; ++k)
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
     }
   }
   __syncwarp();
@@ -435,6 +437,8 @@ void tc_pack_host(const std::vector<std::vector<double>>& ops, const std::vector
     slice0 += kpad / EPS;
   }
   out.cols_total = kbase;
+  out.max_g = 0;
+  for (const TcUnit& u : out.units) out.max_g = std::max(out.max_g, u.g);
   if (out.arena.empty()) out.arena.push_back(TcCvt<T>::from(0.0));
   // largest units first: the persistent grid takes them round-robin
   std::stable_sort(out.units.begin(), out.units.end(), [&](const TcUnit& a, const TcUnit& b) {
@@ -478,8 +482,12 @@ cudaError_t run_tc(bddc_handle_s* h, bool interior, const double* X, double* Y, 
     cudaDeviceGetAttribute(&g_sms_tc, cudaDevAttrMultiProcessorCount, dev);
   }
   const int grid = std::max(1, std::min(n_units, g_sms_tc));
+  // two accumulator buffers (the epilogue of one unit overlaps the MMAs of
+  // the next) when every unit's tiles fit in half of tensor memory
+  const int maxg = interior ? h->tc_maxg_I : h->tc_maxg_G;
+  const int nbuf = maxg * N <= 256 ? 2 : 1;
   kern<<<grid, kThreadsTc, kSmemTc, st>>>(units, n_units, static_cast<const T*>(interior ? h->d_aii : h->d_kgg),
-                                          static_cast<const unsigned char*>(h->d_tcB), Y, yscatter, nrhs, N,
+                                          static_cast<const unsigned char*>(h->d_tcB), Y, yscatter, nrhs, N, nbuf,
                                           h->d_err);
   h->launches += 2;
   return cudaGetLastError();

@@ -207,6 +207,7 @@ struct bddc_handle_s {
   int32_t* d_tcop_I = nullptr; int32_t* d_tcop_G = nullptr;   // per operator: {xoff, n, kbase, slice0}
   void* d_tcB = nullptr;               // packed operand (hi/lo), sized for the widest nrhs
   int64_t tcB_cols_I = 0, tcB_cols_G = 0;   // sum of padded operator widths
+  int tc_maxg_I = 0, tc_maxg_G = 0;          // most row tiles in one unit
   int max_cols_I = 0, max_cols_G = 0;
   int max_nc = 0;                     // most constraints of one subdomain
   // apply workspace (nrhs_max columns)

@@ -42,6 +42,7 @@ template <typename T> struct TcPacked {
   std::vector<int32_t> slice_op;
   std::vector<int32_t> opinfo;
   int64_t cols_total = 0;
+  int max_g = 0;   // most row tiles in one unit
 };
 template <typename T>
 void tc_pack_host(const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
