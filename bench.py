@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "BDDC-PCG time to rtol 1e-8 & M^-1 applies/s, mixed vs FP64, 1 GB300"
 WORKLOAD = "3d_q1_96cubed_12cubed_subdomains_lognormal_sigma_1rhs"
 RTOL = 1e-8
+# DRAM bytes (read + write) of the three operator passes of one apply, from
+# one ncu capture (--set full) of the streamed GEMV on this workload in the
+# bf16 form; no figure for other workloads or kernels (traffic is then null).
+MEASURED_TRAFFIC = {(WORKLOAD, "bf16", "k_bgemv_tma"): 1.2897e9}
 SAMPLE_NE, SAMPLE_NSUB, SAMPLE_SCALE = 32, 4, 27
 
 
@@ -251,8 +255,10 @@ def run_gb300(args):
     op_bytes = (2 * inf["interior_op_bytes"] + inf["interface_op_bytes"]
                 + 8 * 2 * nrhs * (2 * inf["n_interior"] + inf["n_interface_copies"]))
     achieved = op_bytes / (op_ms * 1e-3) / 1e9
+    kname = "k_tc_gemm" if inf["tensor_cores"] else "k_bgemv_tma"
+    wl = WORKLOAD if args.config == 2 and nrhs == 1 else p.name
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind,
+                "traffic": MEASURED_TRAFFIC.get((wl, headline, kname)), "peak_kind": peak_kind,
                 "kernel": ("k_tc_gemm + k_tc_pack" if inf["tensor_cores"] else "k_bgemv_tma") + " (3 operator passes per apply)",
                 "bytes_per_apply": op_bytes}
 
@@ -286,7 +292,7 @@ def run_gb300(args):
         "metric": METRIC, "value": ws * 1e3 / ms, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+" + headline if headline != "fp64" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.config == 2 else p.name, "elements": f"{p.ne}^{p.dim}",
+        "config": {"workload": WORKLOAD if args.config == 2 and nrhs == 1 else p.name, "elements": f"{p.ne}^{p.dim}",
                    "subdomains": p.n_sub, "nrhs": nrhs, "n_c": inf["n_c"], "rtol": RTOL, "mixed_form": headline, "l2": "inputs larger than L2 (operators >= 1 GB)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline,
