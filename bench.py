@@ -339,6 +339,84 @@ def run_apply_only(args):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint workload on the 96^3 grid and 12^3 partition (884736 element
+    conductivities): J(sigma) = 1/2 ||u(sigma) - u_obs||^2, u_obs from the
+    forward solve at sigma exp(0.1 N(0,1)). Times the forward solve (setup
+    separately) and the backward pass (adjoint BDDC-PCG solve + element
+    kernel) through torch.autograd; with --fd N, checks N seeded gradient
+    entries against central differences (step 1e-6, each side a fresh setup
+    and an FP64 solve to rtol 1e-13)."""
+    import torch
+
+    import synth
+    from paper_2410_14786_gb300 import BDDC, adjoint, build
+    build.build()
+    p = synth.config(4)
+    dim, ne = p.dim, p.ne
+    opts = {"precision": args.only or "fp64"}
+    g0 = BDDC.from_problem(p)
+    f = torch.from_numpy(np.ascontiguousarray(p.f[:, 0])).cuda()
+    b = g0.rhs(f)
+    pert = p.elem_sigma * np.exp(0.1 * synth.normal(3004, p.elem_sigma.size))
+    gp = BDDC(dim, ne, pert, p.elem_subdomain, p.n_sub)
+    u_obs, _ = gp.pcg_solve(b, rtol=1e-13, maxit=2000)
+    gp.close()
+    n1 = ne + 1
+    idx = np.arange(n1 ** dim)
+    crd = [idx % n1, (idx // n1) % n1, idx // (n1 * n1)]
+    free = torch.from_numpy(~np.any([(c == 0) | (c == ne) for c in crd], axis=0)).cuda()
+
+    def objective(u):
+        return 0.5 * ((u - u_obs)[free] ** 2).sum()
+
+    rows = []
+    for step in range(args.warmup + args.steps):
+        sigma = torch.tensor(p.elem_sigma, dtype=torch.float64, requires_grad=True)
+        t0 = time.perf_counter()
+        u = adjoint.solve(sigma, b, dim, ne, p.elem_subdomain, p.n_sub, rtol=RTOL, **opts)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J = objective(u)
+        J.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if step >= args.warmup:
+            rows.append((t1 - t0, t2 - t1))
+    fwd = statistics.median(r[0] for r in rows)
+    bwd = statistics.median(r[1] for r in rows)
+    grad = sigma.grad.numpy().copy()
+    line = {"metric": "adjoint dJ/dsigma (forward incl. setup, backward)", "value": 1.0 / (fwd + bwd),
+            "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (fwd + bwd), "higher_is_better": True, "data": "synthetic",
+            "dtype": "f64" if opts["precision"] == "fp64" else "f64+" + opts["precision"],
+            "config": {"workload": p.name, "elements": f"{ne}^{dim}", "subdomains": p.n_sub, "rtol": RTOL},
+            "forward_s": fwd, "backward_s": bwd, "J": float(J)}
+    if args.fd:
+        gf = BDDC.from_problem(p)
+        picks = [int(v % np.uint64(p.elem_sigma.size)) for v in synth.splitmix64(5004, args.fd)]
+        hstep = 1e-6
+
+        def J_at(sig):
+            gg = BDDC(dim, ne, sig, p.elem_subdomain, p.n_sub)
+            uu, rr = gg.pcg_solve(b, rtol=1e-13, maxit=2000)
+            gg.close()
+            return float(objective(uu))
+        errs = []
+        for e in picks:
+            sp_, sm_ = p.elem_sigma.copy(), p.elem_sigma.copy()
+            sp_[e] += hstep
+            sm_[e] -= hstep
+            fd = (J_at(sp_) - J_at(sm_)) / (2 * hstep)
+            errs.append(abs(fd - grad[e]) / max(abs(grad[e]), 1e-300))
+        gf.close()
+        line["fd_check"] = {"elements": args.fd, "step": hstep, "max_rel_err": max(errs),
+                            "median_rel_err": statistics.median(errs)}
+    print(json.dumps(line))
+    g0.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,7 +433,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each PCG iteration's kernels directly (for profilers); not for timing")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5],
+    ap.add_argument("--fd", type=int, default=0,
+                    help="with --config 4: check this many gradient entries against central differences")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="workload (2 = the metric's configuration; others for development)")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling aid: set up the headline form, run this many applies and one solve, exit")
@@ -366,6 +446,8 @@ def main():
         return run_reference(args)
     if args.apply_only:
         return run_apply_only(args)
+    if args.config == 4:
+        return run_adjoint(args)
     return run_gb300(args)
 
 

@@ -198,6 +198,19 @@ int bddc_matvec(bddc_handle_t h, const double *x, double *y, int32_t nrhs, void 
  * (Dirichlet ones included). Device vectors; asynchronous on `stream`. */
 int bddc_rhs(bddc_handle_t h, const double *f, double *b, int32_t nrhs, void *stream);
 
+/* Element term of the adjoint gradient of J(sigma) = 1/2 sum_k ||u_k -
+ * u_obs,k||^2 subject to A(sigma) u_k = b_k (the workloads' adjoint
+ * configuration; the paper has no gradient): with lambda_k = A^-1 (u_k -
+ * u_obs,k) from a second PCG solve on the same handle (A is symmetric),
+ *     g[e] = dJ/dsigma_e = - sum_k lambda_k,e^T K_ref u_k,e,
+ * K_ref the Q1 stiffness matrix of one element for sigma = 1 and u_k,e,
+ * lambda_k,e the 2^dim nodal values of element e. u, lambda: device vectors
+ * of n_nodes x nrhs (RHS fastest; Dirichlet entries are treated as 0);
+ * g: device array of ne^dim float64, overwritten (element e = ex + ne (ey +
+ * ne ez)). Asynchronous on `stream`. */
+int bddc_elem_grad(bddc_handle_t h, const double *u, const double *lambda, double *g, int32_t nrhs,
+                   void *stream);
+
 /* Solve A x = b by PCG with M^-1 from the start x0 = P_I b (the interior
  * correction of b), independently per column, until ||r_k||_2 <= rtol *
  * ||b||_2 on the updated residual. b, x: device vectors. iters[nrhs] and

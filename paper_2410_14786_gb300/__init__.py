@@ -124,6 +124,18 @@ class BDDC:
         _lib.check(self._L.bddc_rhs(self.handle, _dev_ptr(f), _dev_ptr(b), self._nrhs(f), _stream_ptr(stream)))
         return b
 
+    def elem_grad(self, u, lam, out=None, stream=None):
+        """g[e] = -sum_k lam_k,e^T K_ref u_k,e: the element term of an adjoint
+        gradient dJ/dsigma (u, lam device tensors [n_nodes] or [n_nodes, nrhs])."""
+        import torch
+        n_el = self.ne ** self.dim
+        g = out if out is not None else torch.empty(n_el, dtype=torch.float64, device=u.device)
+        if u.shape != lam.shape:
+            raise ValueError("u and lam must have the same shape")
+        _lib.check(self._L.bddc_elem_grad(self.handle, _dev_ptr(u), _dev_ptr(lam), _dev_ptr(g), self._nrhs(u),
+                                          _stream_ptr(stream)))
+        return g
+
     def coarse_vectors(self, nrhs=1, stream=None):
         import torch
         n_c = self.info()["n_c"]

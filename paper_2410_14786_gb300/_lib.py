@@ -30,7 +30,7 @@ EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
     "bddc_pcg_solve_host", "bddc_coarse_vectors", "bddc_query", "bddc_profile_apply",
     "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_setup_inspect",
-    "bddc_apply_static_scratch",
+    "bddc_apply_static_scratch", "bddc_elem_grad",
 ]
 
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "bddc_apply": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_apply_static_scratch": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_matvec": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_elem_grad": (C.c_int, [vp, vp, vp, vp, i32, vp]),
         "bddc_rhs": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_pcg_solve": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
         "bddc_pcg_solve_host": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),

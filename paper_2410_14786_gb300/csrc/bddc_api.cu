@@ -667,6 +667,14 @@ int bddc_rhs(bddc_handle_t h, const double* f, double* b, int32_t nrhs, void* st
   return BDDC_OK;
 }
 
+int bddc_elem_grad(bddc_handle_t h, const double* u, const double* lambda, double* g, int32_t nrhs, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  if (!u || !lambda || !g) return fail(BDDC_ERR_INVALID_ARG, "u, lambda and g must be device pointers");
+  CUDA_TRY(launch_elem_grad(h, u, lambda, g, nrhs, static_cast<cudaStream_t>(stream)));
+  return BDDC_OK;
+}
+
 int bddc_coarse_vectors(bddc_handle_t h, double* rc_out, double* uc_out, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;

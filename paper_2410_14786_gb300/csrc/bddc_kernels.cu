@@ -293,6 +293,47 @@ __global__ void k_q1_apply(int ne, int nrhs, const double* __restrict__ sigma, d
   }
 }
 
+// Adjoint gradient, element term: g[e] = - sum_k lambda_k,e^T K_ref u_k,e,
+// one thread per element. K_ref[a][b] of the Q1 element depends only on the
+// number of coordinate bits in which local nodes a and b differ (coef[0..3]);
+// Dirichlet nodes carry 0.
+template <int DIM>
+__global__ void k_elem_grad(int ne, int nrhs, double c0, double c1, double c2, double c3,
+                            const double* __restrict__ u, const double* __restrict__ lam, double* __restrict__ g) {
+  constexpr int NL = 1 << DIM;
+  const int64_t n1 = ne + 1;
+  const int64_t n_el = DIM == 2 ? (int64_t)ne * ne : (int64_t)ne * ne * ne;
+  const double coef[4] = {c0, c1, c2, c3};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+    const int ex = (int)(e % ne), ey = (int)((e / ne) % ne), ez = DIM == 3 ? (int)(e / ((int64_t)ne * ne)) : 0;
+    int64_t node[NL];
+    bool live[NL];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) {
+      const int bx = ex + (a & 1), by = ey + ((a >> 1) & 1), bz = DIM == 3 ? ez + ((a >> 2) & 1) : 0;
+      node[a] = bx + n1 * (by + n1 * (int64_t)bz);
+      live[a] = !(bx == 0 || bx == ne || by == 0 || by == ne || (DIM == 3 && (bz == 0 || bz == ne)));
+    }
+    double s = 0.0;
+    for (int k = 0; k < nrhs; ++k) {
+      double uv[NL], lv[NL];
+#pragma unroll
+      for (int a = 0; a < NL; ++a) {
+        uv[a] = live[a] ? u[node[a] * nrhs + k] : 0.0;
+        lv[a] = live[a] ? lam[node[a] * nrhs + k] : 0.0;
+      }
+#pragma unroll
+      for (int a = 0; a < NL; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < NL; ++b) t = fma(coef[__popc(a ^ b)], uv[b], t);
+        s = fma(lv[a], t, s);
+      }
+    }
+    g[e] = -s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // PCG vector kernels
 // ---------------------------------------------------------------------------
@@ -484,6 +525,18 @@ cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, c
   else
     k_q1_apply<3><<<blocks_for(h->n_nodes), kThreads, 0, st>>>(h->ne, nrhs, nullptr, c[0], c[1], c[2], c[3], 0,
                                                                0, f, b);
+  h->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elem_grad(bddc_handle_s* h, const double* u, const double* lam, double* g, int nrhs,
+                             cudaStream_t st) {
+  double c[4];
+  q1_coefs(h->dim, h->h, false, c);   // K_ref: the stiffness coefficients for sigma = 1
+  if (h->dim == 2)
+    k_elem_grad<2><<<blocks_for(h->n_elems), kThreads, 0, st>>>(h->ne, nrhs, c[0], c[1], c[2], c[3], u, lam, g);
+  else
+    k_elem_grad<3><<<blocks_for(h->n_elems), kThreads, 0, st>>>(h->ne, nrhs, c[0], c[1], c[2], c[3], u, lam, g);
   h->launches++;
   return cudaGetLastError();
 }

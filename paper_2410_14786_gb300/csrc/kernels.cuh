@@ -66,6 +66,10 @@ cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double
 // b = (M f) on the free nodes (matrix-free Q1 mass matrix).
 cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, cudaStream_t st);
 
+// g[e] = - sum_k lambda_k,e^T K_ref u_k,e (adjoint gradient, element term).
+cudaError_t launch_elem_grad(bddc_handle_s* h, const double* u, const double* lam, double* g, int nrhs,
+                             cudaStream_t st);
+
 // PCG scalar updates applied by the last block of a reducing kernel.
 enum FinalizeOp { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3, FIN_BETA = 4 };
 
