@@ -180,6 +180,11 @@ def run_gb300(args):
                               if prec in ("bf16", "tf32") else "auto")
         handles[prec] = g
         forms[prec] = {"setup_s": g.info()["setup_seconds"]}
+        if not args.no_autotune:
+            # launch parameters measured on this handle (part of setup, untimed)
+            t0 = time.perf_counter()
+            forms[prec]["tuning"] = g.autotune(nrhs)
+            forms[prec]["autotune_s"] = time.perf_counter() - t0
     g64 = handles.get("fp64", handles[headline])
     b = g64.rhs(f)
     stream = torch.cuda.current_stream()
@@ -431,6 +436,8 @@ def main():
     ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
                     help="where the bf16 / tf32 local operators run (auto: tf32 always, bf16 from 8 rhs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch parameters instead of measuring them at setup")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch each PCG iteration's kernels directly (for profilers); not for timing")
     ap.add_argument("--fd", type=int, default=0,

@@ -198,6 +198,30 @@ int bddc_matvec(bddc_handle_t h, const double *x, double *y, int32_t nrhs, void 
  * (Dirichlet ones included). Device vectors; asynchronous on `stream`. */
 int bddc_rhs(bddc_handle_t h, const double *f, double *b, int32_t nrhs, void *stream);
 
+/* Launch parameters of one handle. The defaults work everywhere;
+ * bddc_autotune measures the candidates on the handle's own operators and
+ * keeps the fastest. A caller may store the result (e.g. in a file keyed by
+ * the problem) and restore it with bddc_set_tuning. */
+typedef struct {
+    int32_t gemv_stage_kb_interior;   /* streamed-GEMV stage size target, KB, 1..64 (default 12) */
+    int32_t gemv_stage_kb_interface;
+    int32_t coarse_rowblock_min_nrhs; /* row-blocked coarse sweeps from this many columns on, 2..65
+                                         (65 = never; default 8) */
+    int32_t reserved;
+} bddc_tuning_t;
+
+/* Time the candidate launch parameters for blocks of nrhs columns (stage
+ * sizes 6, 12, 24 and 48 KB of the streamed GEMV of each operator family
+ * when the handle uses it; one-row against four-row coarse sweep units when
+ * nrhs >= 2), apply the fastest and return them in *out (may be NULL).
+ * Uses the handle's work vectors (their contents are overwritten) and CUDA
+ * events; synchronises `stream`. Results do not change (the candidates
+ * differ only in scheduling, up to the order of the coarse sums). */
+int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t *out, void *stream);
+int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t *out);
+/* Returns INVALID_ARG (and changes nothing) if a field is out of range. */
+int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t *in);
+
 /* Element term of the adjoint gradient of J(sigma) = 1/2 sum_k ||u_k -
  * u_obs,k||^2 subject to A(sigma) u_k = b_k (the workloads' adjoint
  * configuration; the paper has no gradient): with lambda_k = A^-1 (u_k -

@@ -56,12 +56,17 @@ class BDDC:
     phi_fp64=True keeps the coarse basis Phi_i in float64 in the fp32, bf16
     and tf32 forms (by default it is float32 there, float64 in the fp64 form);
     tensor_cores in {"auto", True, False}: where the local operators of the
-    bf16 / tf32 forms run (auto: tf32 always, bf16 from nrhs_max 8 on).
+    bf16 / tf32 forms run (auto: tf32 always, bf16 from nrhs_max 8 on);
+    autotune=True times the launch-parameter candidates on this handle's
+    operators for nrhs_max columns and keeps the fastest (`autotune()`);
+    tune_cache=path keeps those results in a JSON file keyed by the problem's
+    shape, partition and form, so a later handle for the same problem reuses
+    them without measuring again.
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
-                 phi_fp64=False, tensor_cores="auto"):
+                 phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -79,6 +84,51 @@ class BDDC:
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim
         self.precision = precision
+        self.tuned_from_cache = False
+        if tune_cache is not None or autotune:
+            self._tune(part, tune_cache, autotune)
+
+    # -- launch-parameter tuning --------------------------------------------
+    def get_tuning(self) -> dict:
+        t = _lib.Tuning()
+        _lib.check(self._L.bddc_get_tuning(self.handle, C.byref(t)))
+        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_ if n != "reserved"}
+
+    def set_tuning(self, tuning: dict):
+        t = _lib.Tuning(**{k: int(v) for k, v in tuning.items()})
+        _lib.check(self._L.bddc_set_tuning(self.handle, C.byref(t)))
+
+    def autotune(self, nrhs=None, stream=None) -> dict:
+        """Measure the launch-parameter candidates for blocks of nrhs columns
+        (default nrhs_max) on this handle and apply the fastest."""
+        t = _lib.Tuning()
+        _lib.check(self._L.bddc_autotune(self.handle, int(nrhs or self.nrhs_max), C.byref(t),
+                                         _stream_ptr(stream)))
+        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_ if n != "reserved"}
+
+    def _tune(self, part, cache, run):
+        import hashlib
+        import json
+        import os
+        key = "|".join([f"dim{self.dim}", f"ne{self.ne}", f"nrhs{self.nrhs_max}", f"prec{self.precision}",
+                        f"tc{self.info()['tensor_cores']}",
+                        hashlib.sha1(np.ascontiguousarray(part, dtype=np.int32).tobytes()).hexdigest()[:16]])
+        table = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        if key in table:
+            self.set_tuning(table[key])
+            self.tuned_from_cache = True
+            return
+        if not run and cache is None:
+            return
+        table[key] = self.autotune()
+        if cache is not None:
+            tmp = f"{cache}.{os.getpid()}.tmp"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
 
     @classmethod
     def from_problem(cls, p, **kw):

@@ -30,8 +30,13 @@ EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
     "bddc_pcg_solve_host", "bddc_coarse_vectors", "bddc_query", "bddc_profile_apply",
     "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_setup_inspect",
-    "bddc_apply_static_scratch", "bddc_elem_grad",
+    "bddc_apply_static_scratch", "bddc_elem_grad", "bddc_autotune", "bddc_get_tuning", "bddc_set_tuning",
 ]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("gemv_stage_kb_interior", C.c_int32), ("gemv_stage_kb_interface", C.c_int32),
+                ("coarse_rowblock_min_nrhs", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Problem(C.Structure):
@@ -76,6 +81,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "bddc_apply_static_scratch": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_matvec": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_elem_grad": (C.c_int, [vp, vp, vp, vp, i32, vp]),
+        "bddc_autotune": (C.c_int, [vp, i32, vp, vp]),
+        "bddc_get_tuning": (C.c_int, [vp, vp]),
+        "bddc_set_tuning": (C.c_int, [vp, vp]),
         "bddc_rhs": (C.c_int, [vp, vp, vp, i32, vp]),
         "bddc_pcg_solve": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
         "bddc_pcg_solve_host": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),

@@ -843,4 +843,96 @@ int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, i
   return status;
 }
 
+int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
+  if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
+  *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 0};
+  return BDDC_OK;
+}
+
+int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
+  if (!h || !in) return fail(BDDC_ERR_INVALID_ARG, "null handle or input");
+  if (in->gemv_stage_kb_interior < 1 || in->gemv_stage_kb_interior > 64 || in->gemv_stage_kb_interface < 1 ||
+      in->gemv_stage_kb_interface > 64)
+    return fail(BDDC_ERR_INVALID_ARG, "GEMV stage size must be 1..64 KB");
+  if (in->coarse_rowblock_min_nrhs < 2 || in->coarse_rowblock_min_nrhs > 65)
+    return fail(BDDC_ERR_INVALID_ARG, "coarse row-blocking threshold must be 2..65");
+  h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
+  h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
+  h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
+  if (h->iter_graph) {   // a captured iteration holds the old launch parameters
+    cudaGraphExecDestroy(h->iter_graph);
+    h->iter_graph = nullptr;
+  }
+  return BDDC_OK;
+}
+
+int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* stream) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  // time `reps` launches of f after one warm-up launch; the median of 3 rounds
+  auto timed = [&](auto&& f) -> float {
+    if (f() != cudaSuccess) return -1.0f;
+    float best[3];
+    for (int round = 0; round < 3; ++round) {
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r)
+        if (f() != cudaSuccess) return -1.0f;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+      cudaEventElapsedTime(&best[round], e0, e1);
+    }
+    std::sort(best, best + 3);
+    return best[1];
+  };
+  bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 0};
+  cudaError_t ce = cudaSuccess;
+  if ((ce = cudaMemsetAsync(h->w_rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
+      (ce = cudaMemsetAsync(h->w_yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return fail(BDDC_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  if (h->use_tma && !h->use_tc) {
+    const int cand[4] = {6, 12, 24, 48};
+    for (int fam = 0; fam < 2; ++fam) {
+      const bool interior = fam == 0;
+      if ((interior ? h->nI_tot : h->nG_tot) == 0) continue;
+      float best = -1.0f;
+      for (int c : cand) {
+        h->tune_stage_kb[fam] = c;
+        const float ms = timed([&] {
+          return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs, st);
+        });
+        if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+          best = ms;
+          (interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface) = c;
+        }
+      }
+      h->tune_stage_kb[fam] = interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface;
+    }
+  }
+  if (h->n_c && !h->coarse_dense && nrhs >= 2) {
+    CUDA_TRY(cudaMemsetAsync(h->w_rc, 0, sizeof(double) * h->n_c * nrhs, st));
+    const int keep = h->tune_coarse_rb_min;
+    h->tune_coarse_rb_min = nrhs;   // blocked
+    const float blocked = timed([&] { return launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st); });
+    h->tune_coarse_rb_min = 65;     // one row per unit
+    const float single = timed([&] { return launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st); });
+    h->tune_coarse_rb_min = keep;
+    if (blocked >= 0.0f && single >= 0.0f)
+      t.coarse_rowblock_min_nrhs = blocked < single ? std::min(keep, (int)nrhs) : std::max(keep, (int)nrhs + 1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaGetLastError());
+  if ((rc = bddc_set_tuning(h, &t)) != BDDC_OK) return rc;
+  if (out) *out = t;
+  return BDDC_OK;
+}
+
 }  // extern "C"

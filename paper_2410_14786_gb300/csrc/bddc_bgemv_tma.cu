@@ -393,18 +393,19 @@ size_t block_smem(int stage_bytes, int max_lda) {
   return (size_t)kStages * stage_bytes + x_bytes<T, NRB>(max_lda) + 2 * kStages * sizeof(uint64_t);
 }
 
-// Stage size: about 12 KB of rows of the widest operator (at least one row,
+// Stage size: about target_kb KB (12 by default; the autotuner may pick
+// another) of rows of the widest operator (at least one row,
 // a whole number of warp groups when that is possible), so that several
 // blocks fit on an SM: measured on GB300 with 1728 bf16 operators of
 // 343 x 344, four 12 KB stages per block and four blocks per SM streamed
 // faster than fewer, larger stages.
 template <typename T, int NRB>
-int stage_size(int max_lda) {
+int stage_size(int max_lda, int target_kb) {
   const long long row = (long long)max_lda * (long long)sizeof(T);
   const long long xs = (long long)x_bytes<T, NRB>(max_lda) + 2 * kStages * 8;
   const long long cap = (200LL * 1024 - xs) / kStages;
   const int wgr = (32 / lanes_per_row(max_lda, Op<T>::V, NRB)) * Blocking<NRB>::R;
-  long long rows = std::max<long long>(12 * 1024 / row, 1);
+  long long rows = std::max<long long>((long long)target_kb * 1024 / row, 1);
   if (rows >= wgr)
     rows = std::max<long long>((rows + wgr / 2) / wgr, 1) * wgr;
   else if ((long long)wgr * row <= cap)
@@ -415,8 +416,8 @@ int stage_size(int max_lda) {
 
 template <typename T, int NRB>
 cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* arena, const double* X, double* Y,
-                    const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
-  const int stage_bytes = stage_size<T, NRB>(max_lda);
+                    const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb) {
+  const int stage_bytes = stage_size<T, NRB>(max_lda, stage_kb);
   const size_t smem = block_smem<T, NRB>(stage_bytes, max_lda);
   auto kern = k_bgemv_tma<T, NRB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -438,16 +439,20 @@ cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* ar
 
 template <typename T>
 cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void* arena, const double* X, double* Y,
-                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st) {
+                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb) {
   const T* A = static_cast<const T*>(arena);
   const size_t row = ((size_t)max_lda * sizeof(T) + 127) / 128 * 128;
   const size_t xb[4] = {x_bytes<T, 1>(max_lda), x_bytes<T, 2>(max_lda), x_bytes<T, 4>(max_lda),
                         x_bytes<T, 8>(max_lda)};
   auto fits = [&](int i) { return kStages * row + xb[i] + 64 <= 200 * 1024; };
-  if (nrhs >= 8 && fits(3)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (nrhs >= 4 && fits(2)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (nrhs >= 2 && fits(1)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
-  if (fits(0)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st);
+  if (nrhs >= 8 && fits(3)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
+                                                           stage_kb);
+  if (nrhs >= 4 && fits(2)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
+                                                           stage_kb);
+  if (nrhs >= 2 && fits(1)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
+                                                           stage_kb);
+  if (fits(0)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
+                                                           stage_kb);
   return cudaErrorInvalidValue;
 }
 
@@ -464,12 +469,16 @@ bool bgemv_tma_supported(int precision, int max_lda) {
 
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
-                             cudaStream_t st) {
+                             cudaStream_t st, int stage_kb) {
   if (n_items == 0) return cudaSuccess;
+  if (stage_kb < 1 || stage_kb > 64) return cudaErrorInvalidValue;
   switch (precision) {
-    case BDDC_PREC_FP64: return dispatch<double>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
-    case BDDC_PREC_FP32: return dispatch<float>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
-    default: return dispatch<__nv_bfloat16>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st);
+    case BDDC_PREC_FP64:
+      return dispatch<double>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
+    case BDDC_PREC_FP32:
+      return dispatch<float>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
+    default:
+      return dispatch<__nv_bfloat16>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
   }
 }
 

@@ -398,14 +398,18 @@ cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y
   h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)
     return interior ? launch_bgemv_tma(h->precision, h->d_wt_I, h->n_wt_I, h->max_cols_I, h->d_aii, X, Y, yscatter,
-                                       nrhs, h->d_err, st)
+                                       nrhs, h->d_err, st, h->tune_stage_kb[0])
                     : launch_bgemv_tma(h->precision, h->d_wt_G, h->n_wt_G, h->max_cols_G, h->d_kgg, X, Y, yscatter,
-                                       nrhs, h->d_err, st);
+                                       nrhs, h->d_err, st, h->tune_stage_kb[1]);
   return interior ? bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, X, Y, yscatter, nrhs, st)
                   : bgemv(h->precision, h->d_wi_G, h->n_wi_G, h->max_cols_G, h->d_kgg, X, Y, yscatter, nrhs, st);
 }
 
 }  // namespace
+
+cudaError_t launch_local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, int nrhs, cudaStream_t st) {
+  return local_op(h, interior, X, Y, nullptr, nrhs, st);
+}
 
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,
                                        cudaStream_t st) {

@@ -531,8 +531,9 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st) {
   if (h->n_c == 0) return cudaSuccess;
   // row blocking pays from about 8 right-hand sides on (fewer, longer units
-  // per level; measured on 10439 and 89999 coarse dofs)
-  const bool blocked = nrhs >= 8;
+  // per level; measured on 10439 and 89999 coarse dofs); the autotuner may
+  // move the threshold
+  const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
   CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
                blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
                h->c_levels, nrhs};

@@ -139,6 +139,9 @@ struct bddc_handle_s {
   // problem
   int dim = 0, ne = 0, n1 = 0, n_sub = 0, precision = 0, nrhs_max = 1, device = 0;
   bool use_graph = true;
+  // launch parameters chosen by the autotuner (or set by the caller)
+  int tune_stage_kb[2] = {12, 12};   // streamed GEMV stage size: interior, interface operators
+  int tune_coarse_rb_min = 8;        // row-blocked coarse sweeps from this many right-hand sides on
   int64_t n_nodes = 0, n_elems = 0;
   double h = 0;
   // sizes

@@ -20,9 +20,11 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
 // copies through shared memory (bddc_bgemv_tma.cu). err receives
 // BDDC_ERR_TIMEOUT if a bounded wait runs out.
 bool bgemv_tma_supported(int precision, int max_lda);
+// stage_kb: target bytes of one shared-memory stage, in KB (1..64; 12 by default,
+// the autotuner may choose another per operator family).
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
-                             cudaStream_t st);
+                             cudaStream_t st, int stage_kb = 12);
 
 // Tensor-core batched GEMM for blocks of right-hand sides (bddc_tc_gemm.cu).
 // Host packing of dense n x n operators (row-major float64) into the tiled
@@ -58,6 +60,10 @@ cudaError_t launch_tc_gemm(bddc_handle_s* h, bool interior, const double* X, dou
 // u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st);
+
+// Y = Op X over the interior (A_II^-1) or interface (K_GG) operators in the
+// compact layouts, on whichever engine the handle uses (for the autotuner).
+cudaError_t launch_local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, int nrhs, cudaStream_t st);
 
 // x = P_I b: interior correction of b (zero on interface and Dirichlet nodes).
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,

@@ -1,0 +1,87 @@
+"""GPU: the launch-parameter autotuner and the tuning cache. The candidates
+differ only in scheduling: with one right-hand side the apply is bitwise
+unchanged; with several, only the order of the coarse sums may change."""
+import json
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_14786_gb300 import build
+    build.build()
+
+
+def _p():
+    return synth.make_problem(3, 24, 3, "lognormal", k=21)
+
+
+def _r(n, nrhs, seed):
+    r = synth.uniform(seed, n * nrhs).reshape(n, nrhs)
+    return torch.from_numpy(r if nrhs > 1 else r[:, 0].copy()).cuda()
+
+
+def test_autotune_one_rhs_is_bitwise_neutral():
+    from paper_2410_14786_gb300 import BDDC
+    p = _p()
+    g = BDDC.from_problem(p, precision="bf16")
+    r = _r(g.n_nodes, 1, 101)
+    z0 = g.apply(r).clone()
+    t = g.autotune()
+    assert t["gemv_stage_kb_interior"] in (6, 12, 24, 48)
+    assert t["gemv_stage_kb_interface"] in (6, 12, 24, 48)
+    assert g.get_tuning() == t
+    z1 = g.apply(r)
+    assert torch.equal(z0, z1)
+
+
+def test_autotune_several_rhs():
+    from paper_2410_14786_gb300 import BDDC
+    p = _p()
+    g = BDDC.from_problem(p, precision="fp32", nrhs_max=8, tensor_cores="auto")
+    r = _r(g.n_nodes, 8, 102)
+    z0 = g.apply(r).clone()
+    t = g.autotune(8)
+    assert 2 <= t["coarse_rowblock_min_nrhs"] <= 65
+    z1 = g.apply(r)
+    assert float((z1 - z0).norm() / z0.norm()) < 1e-12
+    # a solve after the change re-captures its iteration graph
+    b = g.rhs(_r(g.n_nodes, 8, 103))
+    x, res = g.pcg_solve(b, rtol=1e-8)
+    assert res.status == 0
+
+
+def test_set_tuning_rejects_out_of_range():
+    from paper_2410_14786_gb300 import BDDC, BDDCError
+    g = BDDC.from_problem(_p())
+    before = g.get_tuning()
+    for bad in ({"gemv_stage_kb_interior": 0}, {"gemv_stage_kb_interface": 65}, {"coarse_rowblock_min_nrhs": 1}):
+        t = dict(before)
+        t.update(bad)
+        with pytest.raises(BDDCError):
+            g.set_tuning(t)
+    assert g.get_tuning() == before
+
+
+def test_tune_cache_roundtrip(tmp_path):
+    from paper_2410_14786_gb300 import BDDC
+    p = _p()
+    path = str(tmp_path / "tune.json")
+    g1 = BDDC.from_problem(p, precision="bf16", tune_cache=path)
+    assert not g1.tuned_from_cache
+    table = json.load(open(path))
+    assert len(table) == 1
+    g2 = BDDC.from_problem(p, precision="bf16", tune_cache=path)
+    assert g2.tuned_from_cache
+    assert g2.get_tuning() == g1.get_tuning() == list(table.values())[0]
+    # another form is another key
+    g3 = BDDC.from_problem(p, precision="fp32", tune_cache=path)
+    assert not g3.tuned_from_cache
+    assert len(json.load(open(path))) == 2
