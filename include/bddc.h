@@ -152,6 +152,10 @@ typedef struct {
                                            earlier call ran out, else 0 (bddc_query synchronises) */
     int32_t phi_precision;              /* BDDC_PREC_FP64 or BDDC_PREC_FP32: storage of Phi_i */
     int32_t tensor_cores;               /* 1 if the local operators run on the tensor cores */
+    int32_t solve_graph;                /* 1 if bddc_pcg_solve runs the whole solve as one CUDA graph
+                                           (a conditional WHILE node over the iteration), 0 if it
+                                           replays one captured iteration at a time or launches
+                                           directly */
 } bddc_info_t;
 
 /* Build the preconditioner (all factorisations in float64 on the host,

@@ -60,7 +60,7 @@ class Info(C.Structure):
         "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
         ("device_error", C.c_int32), ("phi_precision", C.c_int32),
-        ("tensor_cores", C.c_int32)]
+        ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

@@ -534,7 +534,9 @@ void bddc_destroy(bddc_handle_t h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->iter_graph) cudaGraphExecDestroy(h->iter_graph);
+  if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->body_stream) cudaStreamDestroy(h->body_stream);
   for (void* p : h->allocations) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   delete h;
@@ -637,6 +639,7 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
 int bddc_query(bddc_handle_t h, bddc_info_t* info) {
   if (!h || !info) return fail(BDDC_ERR_INVALID_ARG, "null argument");
   h->info.kernel_launches = h->launches;
+  h->info.solve_graph = h->use_graph && !h->solve_graph_unsupported ? 1 : 0;
   CUDA_TRY(cudaSetDevice(h->device));
   CUDA_TRY(cudaMemcpy(&h->info.device_error, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   *info = h->info;
@@ -752,6 +755,108 @@ static int capture_iteration(bddc_handle_t h, double* x, int nrhs, double rtol, 
   return BDDC_OK;
 }
 
+// The whole solve as one CUDA graph: x0 = P_I b, r0, the first iteration
+// (beta = 0), then a conditional WHILE node whose body is one PCG iteration
+// followed by the loop-control kernel that sets its condition on the device.
+// Returns OK, or BDDC_ERR_CUDA if this driver cannot build conditional
+// nodes (the caller then falls back to replaying one iteration at a time).
+static int capture_solve(bddc_handle_t h, const double* b, double* x, int nrhs, double rtol, int maxit,
+                         int flexible) {
+  if (h->solve_graph && h->solve_b == b && h->solve_x == x && h->solve_nrhs == nrhs && h->solve_rtol == rtol &&
+      h->solve_maxit == maxit && h->solve_flexible == flexible)
+    return BDDC_OK;
+  if (h->solve_graph) {
+    cudaGraphExecDestroy(h->solve_graph);
+    h->solve_graph = nullptr;
+  }
+  if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (!h->body_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap_stream, bs = h->body_stream;
+  const int64_t l0 = h->launches;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(BDDC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphConditionalHandle cond = 0;
+  e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0);
+  // prologue and first iteration
+  if (e == cudaSuccess) e = launch_interior_correction(h, b, x, nrhs, cs);
+  if (e == cudaSuccess) e = launch_spmv(h, x, h->p_q, nrhs, -1, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_residual(h, b, nrhs, cs);
+  if (e == cudaSuccess) e = launch_dots_fin(h, nrhs, b, b, h->p_r, h->p_r, FIN_INIT, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_apply(h, h->p_r, h->p_z, nrhs, cs);
+  if (e == cudaSuccess) e = launch_dots_fin(h, nrhs, h->p_r, h->p_z, nullptr, nullptr, FIN_RHO, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_update_p(h, nrhs, cs);
+  if (e == cudaSuccess) e = launch_spmv(h, h->p_p, h->p_q, nrhs, FIN_ALPHA, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_update_xr_conv(h, x, nrhs, rtol, flexible, cs);
+  if (e == cudaSuccess) e = launch_loop_control(h, maxit, 1, cond, cs);
+  const int64_t l1 = h->launches;
+  // the loop
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  cudaGraphNodeParams cp = {};
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t eb = launch_apply(h, h->p_r, h->p_z, nrhs, bs);
+    if (eb == cudaSuccess)
+      eb = launch_dots_fin(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, FIN_BETA, rtol, flexible, bs);
+    if (eb == cudaSuccess) eb = launch_update_p(h, nrhs, bs);
+    if (eb == cudaSuccess) eb = launch_spmv(h, h->p_p, h->p_q, nrhs, FIN_ALPHA, rtol, flexible, bs);
+    if (eb == cudaSuccess) eb = launch_update_xr_conv(h, x, nrhs, rtol, flexible, bs);
+    if (eb == cudaSuccess) eb = launch_loop_control(h, maxit, 0, cond, bs);
+    cudaGraph_t body = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(bs, &body);
+    e = eb != cudaSuccess ? eb : ee;
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  const int64_t l2 = h->launches;
+  cudaGraph_t whole = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &whole);
+  h->launches = l0;
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->solve_graph, whole, 0);
+  if (whole) cudaGraphDestroy(whole);
+  if (e != cudaSuccess) {
+    h->solve_graph = nullptr;
+    cudaGetLastError();
+    return fail(BDDC_ERR_CUDA, std::string("whole-solve graph: ") + cudaGetErrorString(e));
+  }
+  h->solve_pro_launches = l1 - l0;
+  h->solve_body_launches = l2 - l1;
+  h->solve_b = b; h->solve_x = x; h->solve_nrhs = nrhs; h->solve_rtol = rtol; h->solve_maxit = maxit;
+  h->solve_flexible = flexible;
+  return BDDC_OK;
+}
+
+// per-column results of pcg_core
+static int pcg_finish(bddc_handle_t h, int nrhs, int32_t* iters, double* relres, cudaStream_t st, int status) {
+  const int R = h->nrhs_max;
+  std::vector<int32_t> hi(I_COUNT * R + kGlobalFlags);
+  std::vector<double> hd(S_COUNT * R);
+  CUDA_TRY(cudaMemcpyAsync(hi.data(), h->d_iscal, hi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(hd.data(), h->d_scal, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[k] = hi[I_ITERS * R + k];
+    if (relres) relres[k] = hd[S_RELRES * R + k];
+    if (hi[I_STATUS * R + k] == BDDC_ERR_BREAKDOWN) status = BDDC_ERR_BREAKDOWN;
+  }
+  if (status == BDDC_ERR_BREAKDOWN) g_last_error = "PCG breakdown in at least one column";
+  return status;
+}
+
 static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, double rtol, int maxit,
                     int32_t* iters, double* relres, cudaStream_t st) {
   const int flexible = h->precision != BDDC_PREC_FP64;
@@ -764,14 +869,27 @@ static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, doubl
     if (hf[2]) return fail(BDDC_ERR_TIMEOUT, "a bounded device wait ran out");
     return BDDC_OK;
   };
+  auto finish = [&](int status) { return pcg_finish(h, nrhs, iters, relres, st, status); };
+  int rc;
+  int status = BDDC_OK;
+  if (h->use_graph && maxit > 0 && !h->solve_graph_unsupported) {
+    if ((rc = capture_solve(h, b, x, nrhs, rtol, maxit, flexible)) != BDDC_OK) {
+      h->solve_graph_unsupported = true;   // fall back to one captured iteration at a time
+    } else {
+      CUDA_TRY(cudaGraphLaunch(h->solve_graph, st));
+      if ((rc = read_flags())) return rc;
+      h->launches += h->solve_pro_launches + (int64_t)std::max(hf[3] - 1, 0) * h->solve_body_launches;
+      if (hf[0] > 0) status = BDDC_NOT_CONVERGED;
+      return finish(status);
+    }
+  }
   // x0 = P_I b ; r0 = b - A x0
   CUDA_TRY(launch_interior_correction(h, b, x, nrhs, st));
   CUDA_TRY(launch_spmv(h, x, h->p_q, nrhs, -1, rtol, flexible, st));
   CUDA_TRY(launch_residual(h, b, nrhs, st));
   CUDA_TRY(launch_dots_fin(h, nrhs, b, b, h->p_r, h->p_r, FIN_INIT, rtol, flexible, st));
-  int rc = read_flags();
+  rc = read_flags();
   if (rc) return rc;
-  int status = BDDC_OK;
   if (hf[0] > 0 && maxit > 0) {
     // first iteration launched directly, the rest replay a captured graph
     CUDA_TRY(launch_apply(h, h->p_r, h->p_z, nrhs, st));
@@ -803,19 +921,7 @@ static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, doubl
   } else if (hf[0] > 0) {
     status = BDDC_NOT_CONVERGED;
   }
-  // per-column results
-  std::vector<int32_t> hi(I_COUNT * R + kGlobalFlags);
-  std::vector<double> hd(S_COUNT * R);
-  CUDA_TRY(cudaMemcpyAsync(hi.data(), h->d_iscal, hi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(hd.data(), h->d_scal, hd.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  for (int k = 0; k < nrhs; ++k) {
-    if (iters) iters[k] = hi[I_ITERS * R + k];
-    if (relres) relres[k] = hd[S_RELRES * R + k];
-    if (hi[I_STATUS * R + k] == BDDC_ERR_BREAKDOWN) status = BDDC_ERR_BREAKDOWN;
-  }
-  if (status == BDDC_ERR_BREAKDOWN) g_last_error = "PCG breakdown in at least one column";
-  return status;
+  return finish(status);
 }
 
 int bddc_pcg_solve(bddc_handle_t h, const double* b, double* x, int32_t nrhs, double rtol, int32_t maxit,
@@ -859,9 +965,13 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
   h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
-  if (h->iter_graph) {   // a captured iteration holds the old launch parameters
+  if (h->iter_graph) {   // captured graphs hold the old launch parameters
     cudaGraphExecDestroy(h->iter_graph);
     h->iter_graph = nullptr;
+  }
+  if (h->solve_graph) {
+    cudaGraphExecDestroy(h->solve_graph);
+    h->solve_graph = nullptr;
   }
   return BDDC_OK;
 }

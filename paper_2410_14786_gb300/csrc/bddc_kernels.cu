@@ -555,6 +555,21 @@ cudaError_t launch_update_p(bddc_handle_s* h, int nrhs, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_loop_control(int32_t* gflags, int maxit, int first, cudaGraphConditionalHandle cond) {
+  const int it = first ? 1 : gflags[3] + 1;
+  gflags[3] = it;
+  cudaGraphSetConditional(cond, (gflags[0] > 0 && it < maxit && gflags[2] == 0) ? 1u : 0u);
+}
+}  // namespace
+
+cudaError_t launch_loop_control(bddc_handle_s* h, int maxit, int first, cudaGraphConditionalHandle cond,
+                                cudaStream_t st) {
+  k_loop_control<<<1, 1, 0, st>>>(h->d_iscal + I_COUNT * h->nrhs_max, maxit, first, cond);
+  h->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual(bddc_handle_s* h, const double* b, int nrhs, cudaStream_t st) {
   const int64_t n = h->n_nodes * nrhs;
   k_residual<<<blocks_for(n), kThreads, 0, st>>>(n, b, h->p_q, h->p_r, h->p_p, h->p_zold);

@@ -237,6 +237,16 @@ struct bddc_handle_s {
   int graph_nrhs = 0, graph_flexible = -1;
   double graph_rtol = 0.0;
   int64_t graph_launches = 0;              // kernels in one replay
+  // the whole solve as one graph: prologue and first iteration, then a
+  // conditional WHILE node over one iteration; valid for (b, x, nrhs, rtol, maxit, form)
+  cudaGraphExec_t solve_graph = nullptr;
+  const double* solve_b = nullptr;
+  const double* solve_x = nullptr;
+  int solve_nrhs = 0, solve_maxit = 0, solve_flexible = -1;
+  double solve_rtol = 0.0;
+  int64_t solve_pro_launches = 0, solve_body_launches = 0;
+  cudaStream_t body_stream = nullptr;
+  bool solve_graph_unsupported = false;
   cudaStream_t cap_stream = nullptr;       // private stream used only for capture
   int64_t launches = 0;                    // kernels launched so far
   std::vector<void*> allocations;

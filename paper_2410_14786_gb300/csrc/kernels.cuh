@@ -102,8 +102,16 @@ cudaError_t launch_residual(bddc_handle_s* h, const double* b, int nrhs, cudaStr
 enum ScalarSlot { S_RHO = 0, S_ALPHA, S_BETA, S_BB, S_RR, S_RELRES, S_COUNT };
 enum IntSlot { I_ACTIVE = 0, I_ITERS, I_STATUS, I_COUNT };
 // global int flags after the per-column ones: [0] active columns, [1] breakdown,
-// [2] device error (BDDC_ERR_TIMEOUT from a bounded wait), sticky until setup
-constexpr int kGlobalFlags = 3;
+// [2] device error (BDDC_ERR_TIMEOUT from a bounded wait), sticky until setup,
+// [3] iterations done by the whole-solve graph
+constexpr int kGlobalFlags = 4;
+
+// Loop control of the whole-solve graph (after the first iteration with
+// first = 1, then after every iteration of the conditional body): counts the
+// iteration and sets the WHILE condition to (an active column, fewer than
+// maxit iterations, no device wait ran out).
+cudaError_t launch_loop_control(bddc_handle_s* h, int maxit, int first, cudaGraphConditionalHandle cond,
+                                cudaStream_t st);
 constexpr int kRedBlocks = 1216;  // 8 x 152 SMs: blocks (and fixed-order partials) of the reducing kernels
 
 }  // namespace bddc

@@ -328,3 +328,25 @@ def test_full_size_config2_properties():
         assert rm.status == 0
         assert float((xm - x).norm() / x.norm()) < 1e-6
         gm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_whole_solve_graph(prec):
+    """The whole solve runs as one CUDA graph (a conditional WHILE node over
+    the iteration, its condition set on the device) and gives the same
+    iterates as launching every kernel directly."""
+    p, mask, o = _case("3d_24_3cubed")
+    b = _cuda(o.rhs(p.f[:, 0]))
+    from paper_2410_14786_gb300 import BDDC
+    gg = BDDC.from_problem(p, precision=prec, constraints=mask)
+    gd = BDDC.from_problem(p, precision=prec, constraints=mask, graph=False)
+    xg, rg = gg.pcg_solve(b, rtol=1e-8)
+    assert gg.info()["solve_graph"] == 1
+    xd, rd = gd.pcg_solve(b, rtol=1e-8)
+    assert list(rg.iters) == list(rd.iters)
+    assert torch.equal(xg, xd)
+    # maxit is honoured inside the graph, and a second solve replays it
+    x3, r3 = gg.pcg_solve(b, rtol=1e-8, maxit=3)
+    assert int(r3.iters[0]) == 3 and r3.status == 1
+    x4, r4 = gg.pcg_solve(b, rtol=1e-8)
+    assert torch.equal(x4, xg)

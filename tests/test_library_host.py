@@ -192,3 +192,17 @@ def test_tensor_core_option_rejects_invalid(L, precision, tc):
     info = _lib.Info()
     rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0)
     assert rc == _lib.ERR_INVALID_ARG
+
+
+def test_struct_mirrors_match_the_header():
+    """The ctypes mirrors of bddc_options_t, bddc_info_t and bddc_tuning_t
+    list the header's fields in order."""
+    import re
+    from paper_2410_14786_gb300 import _lib
+    hdr = open(os.path.join(ROOT, "include", "bddc.h")).read()
+    for cname, pyname in (("bddc_options_t", "Options"), ("bddc_info_t", "Info"), ("bddc_tuning_t", "Tuning")):
+        body = re.search(r"typedef struct \{((?:(?!typedef).)*?)\}\s*" + cname + ";", hdr, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = [n.strip() for decl in re.findall(r"\b(?:int32_t|uint32_t|int64_t|double)\s+([\w\s,]+?);", body)
+                  for n in decl.split(",")]
+        assert fields == [n for n, _ in getattr(_lib, pyname)._fields_], cname
