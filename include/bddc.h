@@ -210,7 +210,7 @@ typedef struct {
     int32_t gemv_stage_kb_interior;   /* streamed-GEMV stage size target, KB, 1..64 (default 12) */
     int32_t gemv_stage_kb_interface;
     int32_t coarse_rowblock_min_nrhs; /* row-blocked coarse sweeps from this many columns on, 2..65
-                                         (65 = never; default 8) */
+                                         (65 = never; default 16) */
     int32_t reserved;
 } bddc_tuning_t;
 

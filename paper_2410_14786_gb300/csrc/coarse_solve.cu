@@ -205,7 +205,7 @@ __device__ __forceinline__ double warp_sum8(double (&s)[kNR], int lane) {
   return v;
 }
 
-__device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
+__device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane, int kb, int ke) {
   const int nrhs = a.nrhs;
   if (w.kind == 0) {
     // y[pos0 + i] = sum_{j <= i} L_PP^-1[i, j] r'[pos0 + j]
@@ -213,12 +213,12 @@ __device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
     const double* row = a.F + nd.foff + (int64_t)w.row * nd.fld;
     const double* x = a.rp + (int64_t)nd.pos0 * nrhs;
     double* dst = a.y + (int64_t)(nd.pos0 + w.row) * nrhs;
-    if (nrhs == 1) {
-      const double s = warp_dot(row, x, 0, w.row + 1, 1, 0, lane);
-      if (lane == 0) dst[0] = s;
+    if (ke - kb == 1) {
+      const double s = warp_dot(row, x, 0, w.row + 1, nrhs, kb, lane);
+      if (lane == 0) dst[kb] = s;
       return;
     }
-    for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+    for (int k0 = kb; k0 < ke; k0 += kNR) {
       const int nr = min(kNR, nrhs - k0);
       double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
       warp_dot_multi(row, x, 0, w.row + 1, nrhs, k0, nr, lane, s);
@@ -229,16 +229,16 @@ __device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
     // r'[a] -= sum over the listed contributions, in list order, of
     // M_row . r'_P(node)
     double* dst = &a.rp[(int64_t)w.a * nrhs];
-    if (nrhs == 1) {
+    if (ke - kb == 1) {
       double s = 0.0;
       for (int q = w.b; q < w.e; ++q) {
         const CContrib c = a.list[q];
-        s += warp_dot(a.F + c.row_off, a.rp + c.x_off, 0, c.len, 1, 0, lane);
+        s += warp_dot(a.F + c.row_off, a.rp + (int64_t)c.x_off * nrhs, 0, c.len, nrhs, kb, lane);
       }
-      if (lane == 0) dst[0] = __ldcg(dst) - s;
+      if (lane == 0) dst[kb] = __ldcg(dst + kb) - s;
       return;
     }
-    for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+    for (int k0 = kb; k0 < ke; k0 += kNR) {
       const int nr = min(kNR, nrhs - k0);
       double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int q = w.b; q < w.e; ++q) {
@@ -254,20 +254,20 @@ __device__ void forward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
   }
 }
 
-__device__ void backward_unit(const CoarseArgs& a, const CUnit& w, int lane) {
+__device__ void backward_unit(const CoarseArgs& a, const CUnit& w, int lane, int kb, int ke) {
   // u[dof of pos0 + i] = sum_{j >= i} L_PP^-T[i, j] y[pos0 + j] - sum_b M[b, i] u[upd_b]
   const int nrhs = a.nrhs;
   const CNodeDev nd = a.nodes[w.a];
   const double* row = a.B + nd.boff + (int64_t)w.row * nd.bld;
   const double* yp = a.y + (int64_t)nd.pos0 * nrhs;
   double* dst = a.u + (int64_t)a.order[nd.pos0 + w.row] * nrhs;
-  if (nrhs == 1) {
-    const double s = warp_dot(row, yp, w.row, nd.p, 1, 0, lane) +
-                     warp_dot_gather(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, 1, 0, lane);
-    if (lane == 0) dst[0] = s;
+  if (ke - kb == 1) {
+    const double s = warp_dot(row, yp, w.row, nd.p, nrhs, kb, lane) +
+                     warp_dot_gather(row + nd.p, a.u, a.upd + nd.upd_off, nd.u, nrhs, kb, lane);
+    if (lane == 0) dst[kb] = s;
     return;
   }
-  for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+  for (int k0 = kb; k0 < ke; k0 += kNR) {
     const int nr = min(kNR, nrhs - k0);
     double s[kNR] = {0, 0, 0, 0, 0, 0, 0, 0};
     warp_dot_multi(row, yp, w.row, nd.p, nrhs, k0, nr, lane, s);
@@ -307,13 +307,13 @@ __device__ __forceinline__ void warp_rows_multi(const double* __restrict__ row, 
   }
 }
 
-__device__ void forward_rows(const CoarseArgs& a, const CUnit& w, int lane) {
+__device__ void forward_rows(const CoarseArgs& a, const CUnit& w, int lane, int kb, int ke) {
   // y[pos0 + i] = sum_{j <= i} L_PP^-1[i, j] r'[pos0 + j], i in [row, row + b)
   const int nrhs = a.nrhs, nq = w.b;
   const CNodeDev nd = a.nodes[w.a];
   const double* row = a.F + nd.foff + (int64_t)w.row * nd.fld;
   const double* x = a.rp + (int64_t)nd.pos0 * nrhs;
-  for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+  for (int k0 = kb; k0 < ke; k0 += kNR) {
     const int nr = min(kNR, nrhs - k0);
     double s[kRB][kNR];
 #pragma unroll
@@ -330,13 +330,13 @@ __device__ void forward_rows(const CoarseArgs& a, const CUnit& w, int lane) {
   }
 }
 
-__device__ void backward_rows(const CoarseArgs& a, const CUnit& w, int lane) {
+__device__ void backward_rows(const CoarseArgs& a, const CUnit& w, int lane, int kb, int ke) {
   // u[dof of pos0 + i] = sum_{j >= i} L_PP^-T[i, j] y[pos0 + j] - sum_b M[b, i] u[upd_b]
   const int nrhs = a.nrhs, nq = w.b;
   const CNodeDev nd = a.nodes[w.a];
   const double* row = a.B + nd.boff + (int64_t)w.row * nd.bld;
   const double* yp = a.y + (int64_t)nd.pos0 * nrhs;
-  for (int k0 = 0; k0 < nrhs; k0 += kNR) {
+  for (int k0 = kb; k0 < ke; k0 += kNR) {
     const int nr = min(kNR, nrhs - k0);
     double s[kRB][kNR];
 #pragma unroll
@@ -365,6 +365,12 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  // a warp unit is (row unit, block of bw columns): the column blocks of one
+  // unit run on different warps instead of one after the other. One-row
+  // units take one column each (the single-column dot products); the
+  // row-blocked units take kNR columns.
+  const int bw = RB == 1 ? 1 : kNR;
+  const int nrb = (a.nrhs + bw - 1) / bw;
   // r' = r_c in elimination order
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_c * a.nrhs;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -373,21 +379,25 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
   }
   if (!grid_barrier(a)) return;
   for (int lv = 0; lv < L; ++lv) {
-    for (int t = off_f[lv] + gw; t < off_f[lv + 1]; t += nw) {
-      const CUnit w = a.units[t];
+    for (int64_t t = (int64_t)off_f[lv] * nrb + gw; t < (int64_t)off_f[lv + 1] * nrb; t += nw) {
+      const int64_t ui = t / nrb;
+      const int kb = (int)(t - ui * nrb) * bw, ke = min(a.nrhs, kb + bw);
+      const CUnit w = a.units[ui];
       if (RB > 1 && w.kind == 0)
-        forward_rows(a, w, lane);
+        forward_rows(a, w, lane, kb, ke);
       else
-        forward_unit(a, w, lane);
+        forward_unit(a, w, lane, kb, ke);
     }
     if (!grid_barrier(a)) return;
   }
   for (int lv = L - 1; lv >= 0; --lv) {
-    for (int t = off_b[lv] + gw; t < off_b[lv + 1]; t += nw) {
+    for (int64_t t = (int64_t)off_b[lv] * nrb + gw; t < (int64_t)off_b[lv + 1] * nrb; t += nw) {
+      const int64_t ui = t / nrb;
+      const int kb = (int)(t - ui * nrb) * bw, ke = min(a.nrhs, kb + bw);
       if (RB > 1)
-        backward_rows(a, a.units[t], lane);
+        backward_rows(a, a.units[ui], lane, kb, ke);
       else
-        backward_unit(a, a.units[t], lane);
+        backward_unit(a, a.units[ui], lane, kb, ke);
     }
     if (lv > 0 && !grid_barrier(a)) return;
   }
@@ -530,9 +540,9 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
 
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st) {
   if (h->n_c == 0) return cudaSuccess;
-  // row blocking pays from about 8 right-hand sides on (fewer, longer units
-  // per level; measured on 10439 and 89999 coarse dofs); the autotuner may
-  // move the threshold
+  // row blocking pays from about 16 right-hand sides on (fewer, longer units
+  // per level; measured on 10439 coarse dofs); the autotuner may move the
+  // threshold
   const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
   CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
                blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,

@@ -141,7 +141,7 @@ struct bddc_handle_s {
   bool use_graph = true;
   // launch parameters chosen by the autotuner (or set by the caller)
   int tune_stage_kb[2] = {12, 12};   // streamed GEMV stage size: interior, interface operators
-  int tune_coarse_rb_min = 8;        // row-blocked coarse sweeps from this many right-hand sides on
+  int tune_coarse_rb_min = 16;       // row-blocked coarse sweeps from this many right-hand sides on
   int64_t n_nodes = 0, n_elems = 0;
   double h = 0;
   // sizes
