@@ -10,7 +10,7 @@ coarse solve, prolongation, SpMV, dot products), inputs resident in HBM.
 
 `value` is solves per second of the headline mixed form (bf16 local and
 interior operators with float32 accumulation inside flexible PCG; everything
-else float64). The FP64 form and the FP32 form are timed beside it.
+else float64). The FP64, FP32 and TF32 (tensor-core) forms are timed beside it.
 
 `--impl reference` times the CPU oracle (the plain NumPy/SciPy definitions
 of the paper's Sec. 2) on a bounded sample of the same workload: the same
@@ -172,7 +172,7 @@ def run_gb300(args):
     f = torch.from_numpy(np.ascontiguousarray(p.f if nrhs > 1 else p.f[:, 0])).cuda()
     forms = {}
     handles = {}
-    precs = ["fp64", "fp32", "bf16"] if not args.only else args.only.split(",")
+    precs = ["fp64", "fp32", "tf32", "bf16"] if not args.only else args.only.split(",")
     headline = args.precision if args.precision in precs else precs[-1]
     for prec in precs:
         g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs, graph=not args.no_graph,
@@ -430,7 +430,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp64", "fp32", "bf16", "tf32"])
     ap.add_argument("--only", default=None,
-                    help="comma-separated forms to time (fp64, fp32, bf16, tf32); default fp64,fp32,bf16")
+                    help="comma-separated forms to time (fp64, fp32, tf32, bf16); default all four")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="development aid: override the workload's number of right-hand sides")
     ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],

@@ -211,13 +211,15 @@ typedef struct {
     int32_t gemv_stage_kb_interface;
     int32_t coarse_rowblock_min_nrhs; /* row-blocked coarse sweeps from this many columns on, 2..65
                                          (65 = never; default 16) */
-    int32_t reserved;
+    int32_t gemv_rows_interior;       /* streamed-GEMV work unit: row tile of 64, 128 (default) or 256 rows */
+    int32_t gemv_rows_interface;
 } bddc_tuning_t;
 
-/* Time the candidate launch parameters for blocks of nrhs columns (stage
- * sizes 6, 12, 24 and 48 KB of the streamed GEMV of each operator family
- * when the handle uses it; one-row against four-row coarse sweep units when
- * nrhs >= 2), apply the fastest and return them in *out (may be NULL).
+/* Time the candidate launch parameters for blocks of nrhs columns (row
+ * tiles of 64, 128 and 256 rows and stage sizes of 6, 12, 24 and 48 KB of
+ * the streamed GEMV of each operator family when the handle uses it;
+ * one-row against four-row coarse sweep units when nrhs >= 2), apply the
+ * fastest and return them in *out (may be NULL).
  * Uses the handle's work vectors (their contents are overwritten) and CUDA
  * events; synchronises `stream`. Results do not change (the candidates
  * differ only in scheduling, up to the order of the coarse sums). */

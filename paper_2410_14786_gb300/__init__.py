@@ -92,7 +92,7 @@ class BDDC:
     def get_tuning(self) -> dict:
         t = _lib.Tuning()
         _lib.check(self._L.bddc_get_tuning(self.handle, C.byref(t)))
-        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_ if n != "reserved"}
+        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_}
 
     def set_tuning(self, tuning: dict):
         t = _lib.Tuning(**{k: int(v) for k, v in tuning.items()})
@@ -104,7 +104,7 @@ class BDDC:
         t = _lib.Tuning()
         _lib.check(self._L.bddc_autotune(self.handle, int(nrhs or self.nrhs_max), C.byref(t),
                                          _stream_ptr(stream)))
-        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_ if n != "reserved"}
+        return {n: getattr(t, n) for n, _ in _lib.Tuning._fields_}
 
     def _tune(self, part, cache, run):
         import hashlib

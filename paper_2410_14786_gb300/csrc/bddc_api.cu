@@ -323,16 +323,18 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     CUDA_TRY(upload(h, &h->d_wi_I, itI));
     CUDA_TRY(upload(h, &h->d_wi_G, itG));
     h->use_tma = bgemv_tma_supported(prec, h->max_cols_I) && bgemv_tma_supported(prec, h->max_cols_G);
-    {
-      const int ttile = 128;
+    // work lists of the streamed GEMV for row tiles of 64, 128 and 256 rows
+    // (the autotuner picks one per operator family; 128 by default)
+    for (int c = 0; c < 3; ++c) {
+      const int ttile = 64 << c;
       auto tI = make_items(offI, ldI, dI, ioff, ttile);
       auto tG = make_items(offG, ldG, dG, goff, ttile);
-      h->n_wt_I = (int)tI.size();
-      h->n_wt_G = (int)tG.size();
+      h->n_wtx_I[c] = (int)tI.size();
+      h->n_wtx_G[c] = (int)tG.size();
       if (!items_aligned(tI, elem_bytes(prec)) || !items_aligned(tG, elem_bytes(prec)))
         return fail(BDDC_ERR_INVALID_ARG, "internal: local operator rows not 16-byte aligned");
-      CUDA_TRY(upload(h, &h->d_wt_I, tI));
-      CUDA_TRY(upload(h, &h->d_wt_G, tG));
+      CUDA_TRY(upload(h, &h->d_wtx_I[c], tI));
+      CUDA_TRY(upload(h, &h->d_wtx_G[c], tG));
     }
     for (int s = 0; s < S; ++s) {
       opbytes_I += (int64_t)dI[s] * ldI[s] * elem_bytes(prec);
@@ -951,7 +953,8 @@ int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, i
 
 int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
   if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
-  *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 0};
+  *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min,
+                       64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1]};
   return BDDC_OK;
 }
 
@@ -962,6 +965,11 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
     return fail(BDDC_ERR_INVALID_ARG, "GEMV stage size must be 1..64 KB");
   if (in->coarse_rowblock_min_nrhs < 2 || in->coarse_rowblock_min_nrhs > 65)
     return fail(BDDC_ERR_INVALID_ARG, "coarse row-blocking threshold must be 2..65");
+  auto tile_class = [](int rows) { return rows == 64 ? 0 : rows == 128 ? 1 : rows == 256 ? 2 : -1; };
+  if (tile_class(in->gemv_rows_interior) < 0 || tile_class(in->gemv_rows_interface) < 0)
+    return fail(BDDC_ERR_INVALID_ARG, "GEMV row tile must be 64, 128 or 256");
+  h->tune_tile_class[0] = tile_class(in->gemv_rows_interior);
+  h->tune_tile_class[1] = tile_class(in->gemv_rows_interface);
   h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
   h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
@@ -998,7 +1006,8 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     std::sort(best, best + 3);
     return best[1];
   };
-  bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 0};
+  bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
+                  64 << h->tune_tile_class[1]};
   cudaError_t ce = cudaSuccess;
   if ((ce = cudaMemsetAsync(h->w_rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
       (ce = cudaMemsetAsync(h->w_yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
@@ -1007,22 +1016,31 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     return fail(BDDC_ERR_CUDA, cudaGetErrorString(ce));
   }
   if (h->use_tma && !h->use_tc) {
+    // every (row tile, stage size) pair of each operator family
     const int cand[4] = {6, 12, 24, 48};
     for (int fam = 0; fam < 2; ++fam) {
       const bool interior = fam == 0;
       if ((interior ? h->nI_tot : h->nG_tot) == 0) continue;
       float best = -1.0f;
-      for (int c : cand) {
-        h->tune_stage_kb[fam] = c;
-        const float ms = timed([&] {
-          return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs, st);
-        });
-        if (ms >= 0.0f && (best < 0.0f || ms < best)) {
-          best = ms;
-          (interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface) = c;
+      int best_kb = h->tune_stage_kb[fam], best_tc = h->tune_tile_class[fam];
+      for (int tc = 0; tc < 3; ++tc)
+        for (int c : cand) {
+          h->tune_stage_kb[fam] = c;
+          h->tune_tile_class[fam] = tc;
+          const float ms = timed([&] {
+            return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs,
+                                   st);
+          });
+          if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+            best = ms;
+            best_kb = c;
+            best_tc = tc;
+          }
         }
-      }
-      h->tune_stage_kb[fam] = interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface;
+      h->tune_stage_kb[fam] = best_kb;
+      h->tune_tile_class[fam] = best_tc;
+      (interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface) = best_kb;
+      (interior ? t.gemv_rows_interior : t.gemv_rows_interface) = 64 << best_tc;
     }
   }
   if (h->n_c && !h->coarse_dense && nrhs >= 2) {

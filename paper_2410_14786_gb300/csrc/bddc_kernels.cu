@@ -397,9 +397,11 @@ cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
   h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)
-    return interior ? launch_bgemv_tma(h->precision, h->d_wt_I, h->n_wt_I, h->max_cols_I, h->d_aii, X, Y, yscatter,
+    return interior ? launch_bgemv_tma(h->precision, h->d_wtx_I[h->tune_tile_class[0]],
+                                       h->n_wtx_I[h->tune_tile_class[0]], h->max_cols_I, h->d_aii, X, Y, yscatter,
                                        nrhs, h->d_err, st, h->tune_stage_kb[0])
-                    : launch_bgemv_tma(h->precision, h->d_wt_G, h->n_wt_G, h->max_cols_G, h->d_kgg, X, Y, yscatter,
+                    : launch_bgemv_tma(h->precision, h->d_wtx_G[h->tune_tile_class[1]],
+                                       h->n_wtx_G[h->tune_tile_class[1]], h->max_cols_G, h->d_kgg, X, Y, yscatter,
                                        nrhs, h->d_err, st, h->tune_stage_kb[1]);
   return interior ? bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, X, Y, yscatter, nrhs, st)
                   : bgemv(h->precision, h->d_wi_G, h->n_wi_G, h->max_cols_G, h->d_kgg, X, Y, yscatter, nrhs, st);

@@ -141,6 +141,7 @@ struct bddc_handle_s {
   bool use_graph = true;
   // launch parameters chosen by the autotuner (or set by the caller)
   int tune_stage_kb[2] = {12, 12};   // streamed GEMV stage size: interior, interface operators
+  int tune_tile_class[2] = {1, 1};   // streamed GEMV row tile 64 << class: interior, interface
   int tune_coarse_rb_min = 16;       // row-blocked coarse sweeps from this many right-hand sides on
   int64_t n_nodes = 0, n_elems = 0;
   double h = 0;
@@ -198,8 +199,9 @@ struct bddc_handle_s {
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
   // larger row tiles for the streamed (bulk-copy) GEMV
-  bddc::WorkItem* d_wt_I = nullptr; int n_wt_I = 0;
-  bddc::WorkItem* d_wt_G = nullptr; int n_wt_G = 0;
+  // streamed-GEMV work lists for row tiles of 64 << c rows, c = 0, 1, 2
+  bddc::WorkItem* d_wtx_I[3] = {nullptr, nullptr, nullptr}; int n_wtx_I[3] = {0, 0, 0};
+  bddc::WorkItem* d_wtx_G[3] = {nullptr, nullptr, nullptr}; int n_wtx_G[3] = {0, 0, 0};
   bool use_tma = false;
   // tensor-core path: tiled arenas (d_aii / d_kgg then hold the tiled layout)
   bool use_tc = false;

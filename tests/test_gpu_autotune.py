@@ -37,6 +37,7 @@ def test_autotune_one_rhs_is_bitwise_neutral():
     t = g.autotune()
     assert t["gemv_stage_kb_interior"] in (6, 12, 24, 48)
     assert t["gemv_stage_kb_interface"] in (6, 12, 24, 48)
+    assert t["gemv_rows_interior"] in (64, 128, 256) and t["gemv_rows_interface"] in (64, 128, 256)
     assert g.get_tuning() == t
     z1 = g.apply(r)
     assert torch.equal(z0, z1)
@@ -62,7 +63,8 @@ def test_set_tuning_rejects_out_of_range():
     from paper_2410_14786_gb300 import BDDC, BDDCError
     g = BDDC.from_problem(_p())
     before = g.get_tuning()
-    for bad in ({"gemv_stage_kb_interior": 0}, {"gemv_stage_kb_interface": 65}, {"coarse_rowblock_min_nrhs": 1}):
+    for bad in ({"gemv_stage_kb_interior": 0}, {"gemv_stage_kb_interface": 65}, {"coarse_rowblock_min_nrhs": 1},
+                {"gemv_rows_interior": 100}):
         t = dict(before)
         t.update(bad)
         with pytest.raises(BDDCError):
