@@ -389,17 +389,21 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
         return BDDC_ERR_SINGULAR;
       }
     } else if (factor_coarse) {
-      // glob centroids in grid units for the nested dissection
-      std::vector<double> xyz(3 * nC, 0.0);
-      for (int64_t g = 0; g < nC; ++g) {
-        for (int32_t nd : hs.glob_nodes[g]) {
-          xyz[3 * g] += (double)(nd % n1);
-          xyz[3 * g + 1] += (double)((nd / n1) % n1);
-          xyz[3 * g + 2] += dim == 3 ? (double)(nd / (n1 * n1)) : 0.0;
-        }
-        for (int d = 0; d < 3; ++d) xyz[3 * g + d] /= (double)hs.glob_nodes[g].size();
+      // subdomain centroids (element centres, grid units) for the nested dissection
+      std::vector<double> sxyz(3 * (size_t)P->n_sub, 0.0);
+      std::vector<int64_t> cnt(P->n_sub, 0);
+      const int64_t ne = P->ne;
+      const int64_t n_el = dim == 3 ? ne * ne * ne : ne * ne;
+      for (int64_t e = 0; e < n_el; ++e) {
+        const int32_t q = P->elem_subdomain[e];
+        sxyz[3 * q] += (double)(e % ne) + 0.5;
+        sxyz[3 * q + 1] += (double)((e / ne) % ne) + 0.5;
+        sxyz[3 * q + 2] += dim == 3 ? (double)(e / (ne * ne)) + 0.5 : 0.0;
+        cnt[q]++;
       }
-      const int rc = coarse_factor(nC, hs.Ac_ptr, hs.Ac_col, hs.Ac_val, xyz, hs.cfac, err);
+      for (int32_t q = 0; q < P->n_sub; ++q)
+        for (int d = 0; d < 3; ++d) sxyz[3 * q + d] /= (double)std::max<int64_t>(cnt[q], 1);
+      const int rc = coarse_factor(nC, hs.Ac_ptr, hs.Ac_col, hs.Ac_val, hs.glob_subs, sxyz, hs.cfac, err);
       if (rc != BDDC_OK) return rc;
     }
   }

@@ -2,12 +2,19 @@
 //
 // The coarse problem A_c u_c = r_c (Sec. 2, Eq. coarsegrid) is solved exactly
 // in float64 through a supernodal Cholesky factorisation. Ordering: nested
-// dissection of the coarse graph (two coarse dofs are adjacent when a
-// subdomain holds both), by recursive geometric bisection of the globs'
-// centroids. Among cut planes near the median, the one whose vertex
-// separator (dofs on the far side with a neighbour on the near side) is
-// smallest is taken. Every node of the dissection tree is a supernode whose
-// pivots are its separator (or, at the leaves, its whole vertex set).
+// dissection of the coarse graph, in which two coarse dofs are adjacent when
+// a subdomain holds both, so the graph is a union of one clique per
+// subdomain. The dissection therefore splits subdomains, not dofs: the
+// current group of subdomains is cut by a plane across the longest extent of
+// their centroids (among cuts near the median, the one with the smallest
+// separator, lightly penalised for imbalance); a dof all of whose subdomains
+// lie on one side goes to that side, a dof with subdomains on both sides is
+// in the separator. No subdomain holds dofs of both sides, so this is a
+// vertex separator, and it holds only the globs on the surface between the
+// two groups (a plane through dofs, by contrast, also takes every far-side
+// dof of each subdomain the plane crosses). Every node of the dissection
+// tree is a supernode whose pivots are its separator (or, at the leaves, its
+// whole vertex set).
 //
 // Factorisation: multifrontal. The front of node t holds its pivots P and
 // its update set U (the later dofs coupled to t's subtree). With
@@ -35,31 +42,28 @@ namespace {
 constexpr int kLeaf = 384;  // vertex sets up to this size are not split
 
 struct Dissection {
-  const std::vector<int64_t>& rp;
-  const std::vector<int32_t>& ci;
-  const std::vector<double>& xyz;
-  std::vector<int32_t> stamp;       // per dof: id of the set it currently belongs to
-  std::vector<double> cpos;         // per dof: coordinate along the current axis
-  int next_stamp = 1;
+  const std::vector<std::vector<int32_t>>& subs;   // per dof: its subdomains
+  const std::vector<double>& sxyz;                 // per subdomain: centroid
+  std::vector<int8_t> side;                        // per subdomain: 1 or 2 during a split
   CoarseFactor& cf;
-  std::vector<int32_t> order;       // position -> dof
+  std::vector<int32_t> order;                      // position -> dof
 
-  Dissection(const std::vector<int64_t>& r, const std::vector<int32_t>& c, const std::vector<double>& x,
-             int64_t n, CoarseFactor& f)
-      : rp(r), ci(c), xyz(x), stamp(n, 0), cpos(n, 0.0), cf(f) {}
+  Dissection(const std::vector<std::vector<int32_t>>& s, const std::vector<double>& x, int n_sub, CoarseFactor& f)
+      : subs(s), sxyz(x), side(n_sub, 0), cf(f) {}
 
-  // Split V; returns the index of the new tree node (children first).
-  int build(std::vector<int32_t> V, int depth) {
-    std::vector<int32_t> sep, h1, h2;
-    bool leaf = (int)V.size() <= kLeaf || depth > 60;
-    if (!leaf) leaf = !split(V, sep, h1, h2);
+  // V: the dofs all of whose subdomains are in G. Returns the index of the
+  // new tree node (children first).
+  int build(std::vector<int32_t> V, std::vector<int32_t> G, int depth) {
+    std::vector<int32_t> sep, h1, h2, g1, g2;
+    bool leaf = (int)V.size() <= kLeaf || G.size() < 2 || depth > 60;
+    if (!leaf) leaf = !split(V, G, sep, h1, h2, g1, g2);
     CoarseNode node;
     std::vector<int> kids;
     if (leaf) {
       node.piv = V;
     } else {
-      if (!h1.empty()) kids.push_back(build(std::move(h1), depth + 1));
-      if (!h2.empty()) kids.push_back(build(std::move(h2), depth + 1));
+      if (!h1.empty()) kids.push_back(build(std::move(h1), std::move(g1), depth + 1));
+      if (!h2.empty()) kids.push_back(build(std::move(h2), std::move(g2), depth + 1));
       node.piv = sep;
     }
     std::sort(node.piv.begin(), node.piv.end());
@@ -73,84 +77,79 @@ struct Dissection {
     return id;
   }
 
-  bool split(const std::vector<int32_t>& V, std::vector<int32_t>& sep, std::vector<int32_t>& h1,
-             std::vector<int32_t>& h2) {
-    // axis of largest extent
+  // 1 or 2: all subdomains of v on that side; 0: on both (separator)
+  int dof_side(int32_t v) const {
+    int s1 = 0, s2 = 0;
+    for (int32_t q : subs[v]) (side[q] == 1 ? s1 : s2)++;
+    return s2 == 0 ? 1 : s1 == 0 ? 2 : 0;
+  }
+
+  bool split(const std::vector<int32_t>& V, const std::vector<int32_t>& G, std::vector<int32_t>& sep,
+             std::vector<int32_t>& h1, std::vector<int32_t>& h2, std::vector<int32_t>& g1,
+             std::vector<int32_t>& g2) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int32_t v : V)
+    for (int32_t q : G)
       for (int d = 0; d < 3; ++d) {
-        lo[d] = std::min(lo[d], xyz[3 * v + d]);
-        hi[d] = std::max(hi[d], xyz[3 * v + d]);
+        lo[d] = std::min(lo[d], sxyz[3 * q + d]);
+        hi[d] = std::max(hi[d], sxyz[3 * q + d]);
       }
     int ax = 0;
     for (int d = 1; d < 3; ++d)
       if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
-    if (!(hi[ax] > lo[ax])) return false;
-    std::vector<double> c(V.size());
-    for (size_t i = 0; i < V.size(); ++i) c[i] = xyz[3 * V[i] + ax];
-    std::vector<double> sc = c;
-    std::sort(sc.begin(), sc.end());
-    // candidate cut values: distinct coordinates in the middle half
-    std::vector<double> cand;
-    const size_t a = sc.size() / 4, b = sc.size() - sc.size() / 4;
-    for (size_t i = std::max<size_t>(a, 1); i < b; ++i)
-      if (sc[i] > sc[i - 1]) cand.push_back(sc[i]);
-    if (cand.empty())
-      for (size_t i = 1; i < sc.size(); ++i)
-        if (sc[i] > sc[i - 1]) cand.push_back(sc[i]);
-    if (cand.empty()) return false;
+    std::vector<int32_t> Gs = G;
+    std::stable_sort(Gs.begin(), Gs.end(),
+                     [&](int32_t a, int32_t b) { return sxyz[3 * a + ax] < sxyz[3 * b + ax]; });
+    // candidate cuts: after position m (first m subdomains on side 1), m in the middle half
+    const int ng = (int)Gs.size();
+    std::vector<int> cand;
+    for (int m = std::max(1, ng / 4); m <= std::min(ng - 1, ng - ng / 4); ++m) cand.push_back(m);
+    if (cand.empty()) cand.push_back(ng / 2);
     if (cand.size() > 48) {
-      std::vector<double> thin;
+      std::vector<int> thin;
       for (size_t i = 0; i < 48; ++i) thin.push_back(cand[i * cand.size() / 48]);
       cand.swap(thin);
     }
-    const int st = next_stamp++;
-    for (int32_t v : V) stamp[v] = st;
-    for (size_t i = 0; i < V.size(); ++i) cpos[V[i]] = c[i];
-    double best_cost = 1e300, best_s = 0;
-    for (double s : cand) {
-      int64_t n1 = 0, ns = 0;
-      for (size_t i = 0; i < V.size(); ++i) {
-        if (c[i] < s) { ++n1; continue; }
-        const int32_t v = V[i];
-        for (int64_t j = rp[v]; j < rp[v + 1]; ++j) {
-          const int32_t w = ci[j];
-          if (stamp[w] == st && cpos[w] < s) { ++ns; break; }
-        }
+    double best_cost = 1e300;
+    int best_m = -1;
+    for (int m : cand) {
+      for (int i = 0; i < ng; ++i) side[Gs[i]] = i < m ? 1 : 2;
+      int64_t n1 = 0, n2 = 0, ns = 0;
+      for (int32_t v : V) {
+        const int sd = dof_side(v);
+        (sd == 1 ? n1 : sd == 2 ? n2 : ns)++;
       }
-      const int64_t n2 = (int64_t)V.size() - n1 - ns;
-      if (n1 == 0 || n2 <= 0) continue;
+      if (n1 == 0 || n2 == 0) continue;
       const double cost = (double)ns + 0.05 * std::fabs((double)(n1 - n2));
-      if (cost < best_cost) { best_cost = cost; best_s = s; }
+      if (cost < best_cost) { best_cost = cost; best_m = m; }
     }
-    if (best_cost >= 1e299) return false;
-    for (size_t i = 0; i < V.size(); ++i) {
-      const int32_t v = V[i];
-      if (c[i] < best_s) { h1.push_back(v); continue; }
-      bool touches = false;
-      for (int64_t j = rp[v]; j < rp[v + 1] && !touches; ++j) {
-        const int32_t w = ci[j];
-        touches = stamp[w] == st && cpos[w] < best_s;
-      }
-      (touches ? sep : h2).push_back(v);
+    if (best_m < 0) return false;
+    for (int i = 0; i < ng; ++i) {
+      side[Gs[i]] = i < best_m ? 1 : 2;
+      (i < best_m ? g1 : g2).push_back(Gs[i]);
     }
-    return !sep.empty() || (!h1.empty() && !h2.empty());
+    for (int32_t v : V) {
+      const int sd = dof_side(v);
+      (sd == 1 ? h1 : sd == 2 ? h2 : sep).push_back(v);
+    }
+    return true;
   }
 };
 
 }  // namespace
 
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                  const std::vector<double>& val, const std::vector<double>& xyz, CoarseFactor& cf,
-                  std::string& err) {
+                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
+                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {
   cf = CoarseFactor();
   cf.n = n;
   if (n == 0) return BDDC_OK;
   // ---- ordering and tree ----------------------------------------------------------
-  Dissection nd(rp, ci, xyz, n, cf);
-  std::vector<int32_t> all(n);
+  const int n_sub = (int)(sub_xyz.size() / 3);
+  Dissection nd(dof_subs, sub_xyz, n_sub, cf);
+  std::vector<int32_t> all(n), groups(n_sub);
   std::iota(all.begin(), all.end(), 0);
-  nd.build(std::move(all), 0);
+  std::iota(groups.begin(), groups.end(), 0);
+  nd.build(std::move(all), std::move(groups), 0);
   std::vector<int32_t> pos(n);
   for (int64_t i = 0; i < n; ++i) pos[nd.order[i]] = (int32_t)i;
   cf.order = nd.order;

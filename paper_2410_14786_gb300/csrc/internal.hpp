@@ -85,9 +85,11 @@ struct CoarseFactor {
 };
 // Nested-dissection supernodal Cholesky of the SPD matrix (rp, ci, val)
 // (CSR, both triangles); xyz: 3 coordinates per dof for the dissection.
+// dof_subs: the subdomains of every coarse dof (glob); sub_xyz: centroid of
+// every subdomain (3 per subdomain) for the dissection.
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                  const std::vector<double>& val, const std::vector<double>& xyz, CoarseFactor& cf,
-                  std::string& err);
+                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
+                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err);
 
 // Host-side results of the topology and numeric setup (float64).
 struct HostSetup {
