@@ -150,17 +150,35 @@ __global__ void __launch_bounds__(kThreads) k_bgemv(const WorkItem* __restrict__
 // ---------------------------------------------------------------------------
 // y'_G = W r_G - A_GI t_I   (rows: interface copies; cols: compact interior)
 // ---------------------------------------------------------------------------
+// One thread per (row, block of CB columns; CB = 1 measured fastest for 1 to
+// 64 columns: more threads hide more latency), the CSR loop unrolled so that
+// the loads of several nonzeros are in flight together.
+template <int CB>
 __global__ void k_iface_rhs(int64_t nG, int nrhs, const int32_t* __restrict__ ptr,
                             const int32_t* __restrict__ col, const double* __restrict__ val,
                             const double* __restrict__ tI, double* __restrict__ yG) {
-  const int64_t total = nG * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = i / nrhs;
-    const int k = (int)(i - q * nrhs);
-    double s = 0.0;
-    for (int j = ptr[q]; j < ptr[q + 1]; ++j) s = fma(val[j], tI[(int64_t)col[j] * nrhs + k], s);
-    yG[i] -= s;
+  const int ncb = (nrhs + CB - 1) / CB;
+  const int64_t total = nG * ncb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / ncb;
+    const int kb = (int)(t - q * ncb) * CB;
+    double s[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) s[c] = 0.0;
+    const int j1 = ptr[q + 1];
+#pragma unroll 4
+    for (int j = ptr[q]; j < j1; ++j) {
+      const double v = val[j];
+      const double* tp = tI + (int64_t)col[j] * nrhs + kb;
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (kb + c < nrhs) s[c] = fma(v, tp[c], s[c]);
+    }
+    double* yp = yG + q * nrhs + kb;
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (kb + c < nrhs) yp[c] -= s[c];
   }
 }
 
@@ -191,37 +209,66 @@ __global__ void k_coarse_scatter(int64_t nC, int nrhs, const int32_t* __restrict
 }
 
 // z[node] = sum over the copies q of the node of W_q (z_G[q] + (Phi_G u_c)[q])
+template <int CB>
 __global__ void k_prolong_gather(int64_t n_gu, int nrhs, const int32_t* __restrict__ gu_node,
                                  const int32_t* __restrict__ gu_ptr, const int32_t* __restrict__ gu_copy,
                                  const double* __restrict__ gw, const double* __restrict__ zG,
                                  const double* __restrict__ eG, double* __restrict__ z) {
-  const int64_t total = n_gu * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t u = i / nrhs;
-    const int k = (int)(i - u * nrhs);
-    double v = 0.0;
-    for (int j = gu_ptr[u]; j < gu_ptr[u + 1]; ++j) {
-      const int64_t q = (int64_t)gu_copy[j] * nrhs + k;
-      v = fma(gw[gu_copy[j]], zG[q] + eG[q], v);
+  const int ncb = (nrhs + CB - 1) / CB;
+  const int64_t total = n_gu * ncb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = t / ncb;
+    const int kb = (int)(t - u * ncb) * CB;
+    double v[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) v[c] = 0.0;
+    const int j1 = gu_ptr[u + 1];
+#pragma unroll 4
+    for (int j = gu_ptr[u]; j < j1; ++j) {
+      const int32_t cq = gu_copy[j];
+      const double w = gw[cq];
+      const int64_t q = (int64_t)cq * nrhs + kb;
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (kb + c < nrhs) v[c] = fma(w, zG[q + c] + eG[q + c], v[c]);
     }
-    z[(int64_t)gu_node[u] * nrhs + k] = v;
+    double* zp = z + (int64_t)gu_node[u] * nrhs + kb;
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (kb + c < nrhs) zp[c] = v[c];
   }
 }
 
 // b_I = r_I - A_IG v_G   (rows: compact interior; cols: node ids)
+template <int CB>
 __global__ void k_interior_rhs(int64_t nI, int nrhs, const int32_t* __restrict__ ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ val,
                                const double* __restrict__ rI, const double* __restrict__ z,
                                double* __restrict__ bI) {
-  const int64_t total = nI * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i / nrhs;
-    const int k = (int)(i - p * nrhs);
-    double s = rI[i];
-    for (int j = ptr[p]; j < ptr[p + 1]; ++j) s = fma(-val[j], z[(int64_t)col[j] * nrhs + k], s);
-    bI[i] = s;
+  const int ncb = (nrhs + CB - 1) / CB;
+  const int64_t total = nI * ncb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / ncb;
+    const int kb = (int)(t - p * ncb) * CB;
+    const double* rp = rI + p * nrhs + kb;
+    double s[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) s[c] = kb + c < nrhs ? rp[c] : 0.0;
+    const int j1 = ptr[p + 1];
+#pragma unroll 4
+    for (int j = ptr[p]; j < j1; ++j) {
+      const double v = val[j];
+      const double* zp = z + (int64_t)col[j] * nrhs + kb;
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (kb + c < nrhs) s[c] = fma(-v, zp[c], s[c]);
+    }
+    double* bp = bI + p * nrhs + kb;
+#pragma unroll
+    for (int c = 0; c < CB; ++c)
+      if (kb + c < nrhs) bp[c] = s[c];
   }
 }
 
@@ -445,9 +492,8 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(2);
   if (h->nG_tot) {
     // y'_G = W r_G - A_GI t_I; z_G = K_GG y'_G
-    k_iface_rhs<<<blocks_for(h->nG_tot * nrhs), kThreads, 0, st>>>(h->nG_tot, nrhs, h->d_agi_ptr,
-                                                                   h->d_agi_col, h->d_agi_val, h->w_tI,
-                                                                   h->w_yG);
+    k_iface_rhs<1><<<blocks_for(h->nG_tot * nrhs), kThreads, 0, st>>>(h->nG_tot, nrhs, h->d_agi_ptr, h->d_agi_col,
+                                                                    h->d_agi_val, h->w_tI, h->w_yG);
     h->launches++;
   }
   mark(3);
@@ -495,15 +541,14 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
       cudaMemsetAsync(h->w_eG, 0, sizeof(double) * h->nG_tot * nrhs, st);
       eG = h->w_eG;
     }
-    k_prolong_gather<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr,
-                                                                      h->d_gu_copy, h->d_gw, h->w_zG, eG, z);
+    k_prolong_gather<1><<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(
+        h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr, h->d_gu_copy, h->d_gw, h->w_zG, eG, z);
     h->launches++;
   }
   mark(7);
   // z_I = A_II^-1 (r_I - A_IG v_G)
-  k_interior_rhs<<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(h->nI_tot, nrhs, h->d_aig_ptr,
-                                                                    h->d_aig_col, h->d_aig_val, h->w_rI, z,
-                                                                    h->w_bI);
+  k_interior_rhs<1><<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(
+      h->nI_tot, nrhs, h->d_aig_ptr, h->d_aig_col, h->d_aig_val, h->w_rI, z, h->w_bI);
   h->launches++;
   mark(8);
   if ((e = local_op(h, true, h->w_bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
