@@ -213,13 +213,16 @@ typedef struct {
                                          (65 = never; default 16) */
     int32_t gemv_rows_interior;       /* streamed-GEMV work unit: row tile of 64, 128 (default) or 256 rows */
     int32_t gemv_rows_interface;
+    int32_t coarse_overlap;           /* 1: the interface operator runs on a second stream, concurrently
+                                         with the coarse residual and solve (default 0) */
 } bddc_tuning_t;
 
 /* Time the candidate launch parameters for blocks of nrhs columns (row
  * tiles of 64, 128 and 256 rows and stage sizes of 6, 12, 24 and 48 KB of
  * the streamed GEMV of each operator family when the handle uses it;
- * one-row against four-row coarse sweep units when nrhs >= 2), apply the
- * fastest and return them in *out (may be NULL).
+ * one-row against four-row coarse sweep units when nrhs >= 2; whole applies
+ * with and without the coarse overlap), apply the fastest and return them in
+ * *out (may be NULL).
  * Uses the handle's work vectors (their contents are overwritten) and CUDA
  * events; synchronises `stream`. Results do not change (the candidates
  * differ only in scheduling, up to the order of the coarse sums). */

@@ -539,6 +539,11 @@ void bddc_destroy(bddc_handle_t h) {
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->body_stream) cudaStreamDestroy(h->body_stream);
+  for (int a = 0; a < 2; ++a) {
+    if (h->aux_stream[a]) cudaStreamDestroy(h->aux_stream[a]);
+    if (h->ev_fork[a]) cudaEventDestroy(h->ev_fork[a]);
+    if (h->ev_join[a]) cudaEventDestroy(h->ev_join[a]);
+  }
   for (void* p : h->allocations) cudaFree(p);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   delete h;
@@ -582,6 +587,11 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
     return rc;
   }
   cudaError_t e = cudaDeviceSynchronize();
+  for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+    e = cudaStreamCreateWithFlags(&h->aux_stream[a], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork[a], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join[a], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     bddc_destroy(h);
     return fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
@@ -700,17 +710,23 @@ int bddc_profile_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs
   cudaEvent_t ev[10];
   for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
   for (int i = 0; i < 9; ++i) out_ms[i] = 0;
-  for (int rep = 0; rep < reps; ++rep) {
-    CUDA_TRY(launch_apply(h, r, z, nrhs, st, ev));
-    CUDA_TRY(cudaEventSynchronize(ev[9]));
+  // per-launch times need the launches in sequence: the coarse overlap (the
+  // interface operator on a second stream) is off while profiling
+  const int keep_overlap = h->tune_overlap;
+  h->tune_overlap = 0;
+  for (int rep = 0; rep < reps && rc == BDDC_OK; ++rep) {
+    cudaError_t e = launch_apply(h, r, z, nrhs, st, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[9]);
     float ms;
-    for (int i = 0; i < 9; ++i) {
-      CUDA_TRY(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
+      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
       out_ms[i] += ms / reps;
     }
+    if (e != cudaSuccess) rc = fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
   }
+  h->tune_overlap = keep_overlap;
   for (auto& e : ev) cudaEventDestroy(e);
-  return BDDC_OK;
+  return rc;
 }
 
 // Capture one PCG iteration (apply, beta, p update, SpMV with alpha, x/r
@@ -811,7 +827,9 @@ static int capture_solve(bddc_handle_t h, const double* b, double* x, int nrhs, 
     e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
+    h->aux_sel = 1;   // the prologue's capture (on set 0) is still open
     cudaError_t eb = launch_apply(h, h->p_r, h->p_z, nrhs, bs);
+    h->aux_sel = 0;
     if (eb == cudaSuccess)
       eb = launch_dots_fin(h, nrhs, h->p_r, h->p_z, h->p_r, h->p_zold, FIN_BETA, rtol, flexible, bs);
     if (eb == cudaSuccess) eb = launch_update_p(h, nrhs, bs);
@@ -954,7 +972,7 @@ int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, i
 int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
   if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
   *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min,
-                       64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1]};
+                       64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1], h->tune_overlap};
   return BDDC_OK;
 }
 
@@ -968,8 +986,11 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   auto tile_class = [](int rows) { return rows == 64 ? 0 : rows == 128 ? 1 : rows == 256 ? 2 : -1; };
   if (tile_class(in->gemv_rows_interior) < 0 || tile_class(in->gemv_rows_interface) < 0)
     return fail(BDDC_ERR_INVALID_ARG, "GEMV row tile must be 64, 128 or 256");
+  if (in->coarse_overlap != 0 && in->coarse_overlap != 1)
+    return fail(BDDC_ERR_INVALID_ARG, "coarse_overlap must be 0 or 1");
   h->tune_tile_class[0] = tile_class(in->gemv_rows_interior);
   h->tune_tile_class[1] = tile_class(in->gemv_rows_interface);
+  h->tune_overlap = in->coarse_overlap;
   h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
   h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
@@ -1007,7 +1028,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     return best[1];
   };
   bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
-                  64 << h->tune_tile_class[1]};
+                  64 << h->tune_tile_class[1], h->tune_overlap};
   cudaError_t ce = cudaSuccess;
   if ((ce = cudaMemsetAsync(h->w_rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
       (ce = cudaMemsetAsync(h->w_yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
@@ -1053,6 +1074,28 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     h->tune_coarse_rb_min = keep;
     if (blocked >= 0.0f && single >= 0.0f)
       t.coarse_rowblock_min_nrhs = blocked < single ? std::min(keep, (int)nrhs) : std::max(keep, (int)nrhs + 1);
+  }
+  // whole applies with and without the coarse overlap (after the choices above)
+  if (h->aux_stream[0] && h->n_c && !h->coarse_dense && h->nG_tot) {
+    h->tune_stage_kb[0] = t.gemv_stage_kb_interior;
+    h->tune_stage_kb[1] = t.gemv_stage_kb_interface;
+    h->tune_coarse_rb_min = t.coarse_rowblock_min_nrhs;
+    double* rz = nullptr;
+    const size_t nv = (size_t)h->n_nodes * nrhs;
+    if (cudaMalloc(&rz, 2 * nv * sizeof(double)) == cudaSuccess) {
+      cudaMemsetAsync(rz, 0, 2 * nv * sizeof(double), st);
+      const int keep = h->tune_overlap;
+      h->tune_overlap = 0;
+      const float plain = timed([&] { return launch_apply(h, rz, rz + nv, nrhs, st); });
+      h->tune_overlap = 1;
+      const float over = timed([&] { return launch_apply(h, rz, rz + nv, nrhs, st); });
+      h->tune_overlap = keep;
+      if (plain >= 0.0f && over >= 0.0f) t.coarse_overlap = over < plain ? 1 : 0;
+      cudaStreamSynchronize(st);
+      cudaFree(rz);
+    } else {
+      cudaGetLastError();
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -416,7 +416,8 @@ int stage_size(int max_lda, int target_kb) {
 
 template <typename T, int NRB>
 cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* arena, const double* X, double* Y,
-                    const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb) {
+                    const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb,
+                    int max_per_sm) {
   const int stage_bytes = stage_size<T, NRB>(max_lda, stage_kb);
   const size_t smem = block_smem<T, NRB>(stage_bytes, max_lda);
   auto kern = k_bgemv_tma<T, NRB>;
@@ -431,6 +432,7 @@ cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* ar
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, per_sm);
+  if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
   const int units = n_items * ((nrhs + NRB - 1) / NRB);
   const int grid = std::max(1, std::min(units, g_num_sms * per_sm));
   kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, nrhs, stage_bytes, max_lda, err);
@@ -439,20 +441,21 @@ cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* ar
 
 template <typename T>
 cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void* arena, const double* X, double* Y,
-                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb) {
+                     const int32_t* yscatter, int nrhs, int32_t* err, cudaStream_t st, int stage_kb,
+                     int max_per_sm) {
   const T* A = static_cast<const T*>(arena);
   const size_t row = ((size_t)max_lda * sizeof(T) + 127) / 128 * 128;
   const size_t xb[4] = {x_bytes<T, 1>(max_lda), x_bytes<T, 2>(max_lda), x_bytes<T, 4>(max_lda),
                         x_bytes<T, 8>(max_lda)};
   auto fits = [&](int i) { return kStages * row + xb[i] + 64 <= 200 * 1024; };
   if (nrhs >= 8 && fits(3)) return run_tma<T, 8>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
-                                                           stage_kb);
+                                                           stage_kb, max_per_sm);
   if (nrhs >= 4 && fits(2)) return run_tma<T, 4>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
-                                                           stage_kb);
+                                                           stage_kb, max_per_sm);
   if (nrhs >= 2 && fits(1)) return run_tma<T, 2>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
-                                                           stage_kb);
+                                                           stage_kb, max_per_sm);
   if (fits(0)) return run_tma<T, 1>(items, n_items, max_lda, A, X, Y, yscatter, nrhs, err, st,
-                                                           stage_kb);
+                                                           stage_kb, max_per_sm);
   return cudaErrorInvalidValue;
 }
 
@@ -469,16 +472,16 @@ bool bgemv_tma_supported(int precision, int max_lda) {
 
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
-                             cudaStream_t st, int stage_kb) {
+                             cudaStream_t st, int stage_kb, int max_per_sm) {
   if (n_items == 0) return cudaSuccess;
   if (stage_kb < 1 || stage_kb > 64) return cudaErrorInvalidValue;
   switch (precision) {
     case BDDC_PREC_FP64:
-      return dispatch<double>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
+      return dispatch<double>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb, max_per_sm);
     case BDDC_PREC_FP32:
-      return dispatch<float>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
+      return dispatch<float>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb, max_per_sm);
     default:
-      return dispatch<__nv_bfloat16>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb);
+      return dispatch<__nv_bfloat16>(items, n_items, max_lda, arena, X, Y, yscatter, nrhs, err, st, stage_kb, max_per_sm);
   }
 }
 

@@ -440,16 +440,16 @@ cudaError_t bgemv(int precision, const WorkItem* items, int n_items, int max_lda
 // operators of all subdomains.
 // Y = Op X over the interior or interface operators; counts its launches.
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
-                     cudaStream_t st) {
+                     cudaStream_t st, int max_per_sm = 0) {
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
   h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)
     return interior ? launch_bgemv_tma(h->precision, h->d_wtx_I[h->tune_tile_class[0]],
                                        h->n_wtx_I[h->tune_tile_class[0]], h->max_cols_I, h->d_aii, X, Y, yscatter,
-                                       nrhs, h->d_err, st, h->tune_stage_kb[0])
+                                       nrhs, h->d_err, st, h->tune_stage_kb[0], max_per_sm)
                     : launch_bgemv_tma(h->precision, h->d_wtx_G[h->tune_tile_class[1]],
                                        h->n_wtx_G[h->tune_tile_class[1]], h->max_cols_G, h->d_kgg, X, Y, yscatter,
-                                       nrhs, h->d_err, st, h->tune_stage_kb[1]);
+                                       nrhs, h->d_err, st, h->tune_stage_kb[1], max_per_sm);
   return interior ? bgemv(h->precision, h->d_wi_I, h->n_wi_I, h->max_cols_I, h->d_aii, X, Y, yscatter, nrhs, st)
                   : bgemv(h->precision, h->d_wi_G, h->n_wi_G, h->max_cols_G, h->d_kgg, X, Y, yscatter, nrhs, st);
 }
@@ -497,14 +497,26 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
     h->launches++;
   }
   mark(3);
-  if (h->nG_tot) {
+  // The interface operator (z_G = K_GG y'_G) and the coarse residual and
+  // solve depend only on y'_G: with tune_overlap they run concurrently, the
+  // interface operator on a second stream capped at 2 blocks per SM, the
+  // coarse sweeps on one 512-thread block per SM, so that both fit on every
+  // SM at once (the coarse kernel is cooperative: its grid must be resident).
+  const int ax = h->aux_sel;
+  const bool overlap = h->tune_overlap && h->nG_tot && h->n_c && !h->coarse_dense && h->aux_stream[ax];
+  if (overlap) {
+    if ((e = cudaEventRecord(h->ev_fork[ax], st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->aux_stream[ax], h->ev_fork[ax], 0)) != cudaSuccess) return e;
+    if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, h->aux_stream[ax], 2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(h->ev_join[ax], h->aux_stream[ax])) != cudaSuccess) return e;
+  } else if (h->nG_tot) {
     if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, st)) != cudaSuccess) return e;
   }
   mark(4);
   if (h->n_c) {
     // coarse residual r_c = sum R_ci^T Phi_G^T y'_G
     if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, h->w_yG, h->w_g,
-                              nullptr, nrhs, h->d_err, st)) != cudaSuccess)
+                              nullptr, nrhs, h->d_err, st, 12, overlap ? 2 : 0)) != cudaSuccess)
       return e;
     k_coarse_gather<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx,
                                                                     h->w_g, h->w_rc);
@@ -522,9 +534,10 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
       h->launches += 2;
     } else {
       // u_c = A_c^-1 r_c: sparse Cholesky forward and backward sweeps
-      if ((e = launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st)) != cudaSuccess) return e;
+      if ((e = launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st, overlap)) != cudaSuccess) return e;
     }
   }
+  if (overlap && (e = cudaStreamWaitEvent(st, h->ev_join[ax], 0)) != cudaSuccess) return e;
   mark(6);
   if (h->n_gu) {
     // v_G = sum R^T W (z_G + Phi_G u_c)

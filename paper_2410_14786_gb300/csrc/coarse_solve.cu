@@ -530,6 +530,7 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   h->c_grid = sms * std::min(per_sm, 2);
+  h->c_sms = sms;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve<kRB>, kThreads / 2, 0)) !=
       cudaSuccess)
     return e;
@@ -538,7 +539,8 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   return cudaSuccess;
 }
 
-cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st) {
+cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st,
+                                bool narrow) {
   if (h->n_c == 0) return cudaSuccess;
   // row blocking pays from about 16 right-hand sides on (fewer, longer units
   // per level; measured on 10439 coarse dofs); the autotuner may move the
@@ -550,8 +552,8 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   cudaError_t e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocked ? h->c_grid4 : h->c_grid);
-  cfg.blockDim = dim3(blocked ? kThreads / 2 : kThreads);
+  cfg.gridDim = dim3(narrow ? h->c_sms : blocked ? h->c_grid4 : h->c_grid);
+  cfg.blockDim = dim3((narrow || blocked) ? kThreads / 2 : kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

@@ -145,6 +145,13 @@ struct bddc_handle_s {
   int tune_stage_kb[2] = {12, 12};   // streamed GEMV stage size: interior, interface operators
   int tune_tile_class[2] = {1, 1};   // streamed GEMV row tile 64 << class: interior, interface
   int tune_coarse_rb_min = 16;       // row-blocked coarse sweeps from this many right-hand sides on
+  int tune_overlap = 0;              // interface operator concurrent with the coarse residual and solve
+  // second stream of the apply and its fork / join events, one set per
+  // capture sequence: [0] direct launches and the solve graph's prologue,
+  // [1] the body of its conditional node (captured while [0] is still open)
+  cudaStream_t aux_stream[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+  int aux_sel = 0;
   int64_t n_nodes = 0, n_elems = 0;
   double h = 0;
   // sizes
@@ -196,7 +203,7 @@ struct bddc_handle_s {
   unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
   bddc::CUnit* d_cunits4 = nullptr;   // the same with kinds 0 and 2 blocked by 4 rows
   int32_t* d_clvl4 = nullptr;
-  int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0;
+  int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0, c_sms = 0;
   int64_t c_nnz = 0, c_update_total = 0;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;

@@ -21,10 +21,11 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
 // BDDC_ERR_TIMEOUT if a bounded wait runs out.
 bool bgemv_tma_supported(int precision, int max_lda);
 // stage_kb: target bytes of one shared-memory stage, in KB (1..64; 12 by default,
-// the autotuner may choose another per operator family).
+// the autotuner may choose another per operator family); max_per_sm > 0 caps
+// the blocks per SM (to leave room for a concurrent kernel).
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int nrhs, int32_t* err,
-                             cudaStream_t st, int stage_kb = 12);
+                             cudaStream_t st, int stage_kb = 12, int max_per_sm = 0);
 
 // Tensor-core batched GEMM for blocks of right-hand sides (bddc_tc_gemm.cu).
 // Host packing of dense n x n operators (row-major float64) into the tiled
@@ -59,7 +60,10 @@ cudaError_t launch_tc_gemm(bddc_handle_s* h, bool interior, const double* X, dou
 // Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
 // u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);
-cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st);
+// narrow: one block of 512 threads per SM, leaving room on every SM for a
+// concurrent kernel (the interface operator) while the sweeps run.
+cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st,
+                                bool narrow = false);
 
 // Y = Op X over the interior (A_II^-1) or interface (K_GG) operators in the
 // compact layouts, on whichever engine the handle uses (for the autotuner).

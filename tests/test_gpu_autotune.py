@@ -64,7 +64,7 @@ def test_set_tuning_rejects_out_of_range():
     g = BDDC.from_problem(_p())
     before = g.get_tuning()
     for bad in ({"gemv_stage_kb_interior": 0}, {"gemv_stage_kb_interface": 65}, {"coarse_rowblock_min_nrhs": 1},
-                {"gemv_rows_interior": 100}):
+                {"gemv_rows_interior": 100}, {"coarse_overlap": 2}):
         t = dict(before)
         t.update(bad)
         with pytest.raises(BDDCError):
@@ -87,3 +87,27 @@ def test_tune_cache_roundtrip(tmp_path):
     g3 = BDDC.from_problem(p, precision="fp32", tune_cache=path)
     assert not g3.tuned_from_cache
     assert len(json.load(open(path))) == 2
+
+
+@pytest.mark.parametrize("prec,nrhs", [("bf16", 1), ("fp64", 1), ("bf16", 8)])
+def test_coarse_overlap_is_bitwise_neutral(prec, nrhs):
+    """The interface operator on a second stream, concurrent with the coarse
+    residual and solve, computes exactly what the one-stream apply does, in
+    direct launches and inside the captured solve graph."""
+    from paper_2410_14786_gb300 import BDDC
+    p = _p()
+    g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs)
+    r = _r(g.n_nodes, nrhs, 104)
+    t = g.get_tuning()
+    z0 = g.apply(r).clone()
+    b = g.rhs(_r(g.n_nodes, nrhs, 105))
+    x0, r0 = g.pcg_solve(b, rtol=1e-8)
+    t1 = dict(t)
+    t1["coarse_overlap"] = 1
+    g.set_tuning(t1)
+    assert g.get_tuning()["coarse_overlap"] == 1
+    z1 = g.apply(r)
+    assert torch.equal(z0, z1)
+    x1, r1 = g.pcg_solve(b, rtol=1e-8)
+    assert list(r0.iters) == list(r1.iters)
+    assert torch.equal(x0, x1)
