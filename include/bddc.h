@@ -275,7 +275,9 @@ int bddc_query(bddc_handle_t h, bddc_info_t *info);
  * restriction, interior operator (t_I = A_II^-1 r_I), condensed interface
  * right-hand side, interface operator (z_G = K_GG y'_G), coarse residual,
  * coarse solve, prolongation, interior right-hand side, interior operator
- * (final). For profiling only; z receives M^-1 r. */
+ * (final). The launches run in sequence, without the coarse overlap of
+ * bddc_tuning_t whatever the handle's tuning. For profiling only; z
+ * receives M^-1 r. */
 int bddc_profile_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs,
                        int32_t reps, double *out_ms, void *stream);
 
