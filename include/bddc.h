@@ -124,6 +124,9 @@ typedef struct {
                               replaying a captured CUDA graph (for profilers) */
     int32_t phi_fp64;      /* 1: keep Phi_i in float64 in the FP32, BF16 and TF32 modes too */
     int32_t tensor_cores;  /* BDDC_TC_* */
+    int32_t coarse_blocks; /* blocks of the one-column sparse coarse solve (one per SM at
+                              most); 0 = one per SM. Fewer blocks give each warp more
+                              units of every level (for small coarse problems). >= 0 */
 } bddc_options_t;
 
 typedef struct {

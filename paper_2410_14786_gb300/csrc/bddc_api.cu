@@ -165,7 +165,7 @@ std::vector<WorkItem> make_items(const std::vector<int64_t>& off, const std::vec
 
 int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   const int S = hs.n_sub;
-  int64_t in_coarse_bytes = 0;
+  int64_t in_coarse_bytes = 0, coarse_read_1rhs = 0;
   // ---- compact layouts --------------------------------------------------------
   std::vector<int32_t> ioff(S + 1, 0), goff(S + 1, 0), coff(S + 1, 0);
   for (int s = 0; s < S; ++s) {
@@ -188,6 +188,14 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       csub[coff[s] + r] = s;
       ccdof[coff[s] + r] = hs.sub_globs[s][r];
     }
+  }
+  // sparse coarse solve: the coarse dofs are numbered in elimination order on
+  // the device (r_c, u_c and the factor then share one order, and the sweeps
+  // read and write contiguous runs); cperm maps a glob to that number
+  std::vector<int32_t> cperm;
+  if (hs.n_c && !hs.coarse_dense) {
+    coarse_renumber(hs.cfac, cperm);
+    for (auto& c : ccdof) c = cperm[c];
   }
   // A_GI with global compact interior columns; A_IG with node-id columns
   std::vector<int32_t> agi_ptr(h->nG_tot + 1, 0), agi_col, aig_ptr(h->nI_tot + 1, 0), aig_col;
@@ -369,6 +377,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     std::vector<double>().swap(hs.Acinv);
     CUDA_TRY(upload(h, &h->d_acinv, ac));
     in_coarse_bytes = cur * 8;
+    coarse_read_1rhs = in_coarse_bytes;
     h->c_nnz = cur;
     const int ctile = 128;
     for (int p = 0; p < h->n_cpanels; ++p)
@@ -380,7 +389,8 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   } else if (hs.n_c) {
     // sparse Cholesky factorisation of A_c: supernode matrices and level lists
     CUDA_TRY(build_coarse_device(h, hs.cfac));
-    in_coarse_bytes = h->c_nnz * 8;
+    in_coarse_bytes = h->c_nnz * 8 + h->g_entries * 12;
+    coarse_read_1rhs = h->g_entries * 12;
   }
   // ---- index arrays -----------------------------------------------------------------
   std::vector<double> sigma(P->elem_sigma, P->elem_sigma + hs.n_elems);
@@ -412,6 +422,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(upload(h, &h->d_sub_coff, coff));
   CUDA_TRY(upload(h, &h->d_csub, csub));
   CUDA_TRY(upload(h, &h->d_ccdof, ccdof));
+  if (!cperm.empty()) CUDA_TRY(upload(h, &h->d_cperm, cperm));
   CUDA_TRY(upload(h, &h->d_cg_ptr, cg_ptr));
   CUDA_TRY(upload(h, &h->d_cg_idx, cg_idx));
   CUDA_TRY(upload(h, &h->d_gu_node, gu_node));
@@ -482,8 +493,9 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   in.operator_bytes = (int64_t)arena_bytes;
   in.coarse_bytes = in_coarse_bytes;
   // compulsory HBM bytes of one apply (nrhs = 1): operators as stored (A_II^-1
-  // read twice), Phi rows twice, coarse inverse once, the sparse couplings,
-  // the input r and the output z.
+  // read twice), Phi rows twice, the coarse inverse (or the gather form of the
+  // sparse factor: coefficients and operand indices) once, the sparse
+  // couplings, the input r and the output z.
   int64_t ops = 0;
   in.interior_op_bytes = opbytes_I;
   in.interface_op_bytes = opbytes_G;
@@ -494,7 +506,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   in.coarse_levels = h->coarse_dense ? 0 : h->c_levels;
   ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
   in.phi_precision = h->phi_prec;
-  in.apply_bytes_1rhs = ops + 2 * (int64_t)elem_bytes(h->phi_prec) * in.sum_nG_nc + in.coarse_bytes +
+  in.apply_bytes_1rhs = ops + 2 * (int64_t)elem_bytes(h->phi_prec) * in.sum_nG_nc + coarse_read_1rhs +
                         (int64_t)(agi_val.size() + aig_val.size()) * 12 + 8 * (in.n_free + hs.n_nodes);
   return BDDC_OK;
 }
@@ -580,6 +592,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->use_graph = O->no_graph == 0;
   h->phi_prec = (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
   h->use_tc = tc_enabled(O);
+  h->g_blocks = O->coarse_blocks;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -696,6 +709,13 @@ int bddc_coarse_vectors(bddc_handle_t h, double* rc_out, double* uc_out, int32_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)h->n_c * nrhs * sizeof(double);
   if (bytes == 0) return BDDC_OK;
+  // in glob order (the sparse coarse solve numbers the coarse dofs in its
+  // elimination order on the device)
+  if (h->d_cperm) {
+    if (rc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w_rc, rc_out, st));
+    if (uc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w_uc, uc_out, st));
+    return BDDC_OK;
+  }
   if (rc_out) CUDA_TRY(cudaMemcpyAsync(rc_out, h->w_rc, bytes, cudaMemcpyDeviceToDevice, st));
   if (uc_out) CUDA_TRY(cudaMemcpyAsync(uc_out, h->w_uc, bytes, cudaMemcpyDeviceToDevice, st));
   return BDDC_OK;

@@ -198,6 +198,15 @@ __global__ void k_coarse_gather(int64_t n_c, int nrhs, const int32_t* __restrict
 }
 
 // u_c per local constraint (the values Phi_G multiplies in the prolongation)
+__global__ void k_gather_rows(int64_t n, int nrhs, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * nrhs;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nrhs;
+    dst[i] = src[(int64_t)perm[r] * nrhs + (i - r * nrhs)];
+  }
+}
+
 __global__ void k_coarse_scatter(int64_t nC, int nrhs, const int32_t* __restrict__ ccdof, const double* __restrict__ uc,
                                  double* __restrict__ ucl) {
   const int64_t total = nC * nrhs;
@@ -590,6 +599,13 @@ cudaError_t launch_rhs(bddc_handle_s* h, const double* f, double* b, int nrhs, c
     k_q1_apply<3><<<blocks_for(h->n_nodes), kThreads, 0, st>>>(h->ne, nrhs, nullptr, c[0], c[1], c[2], c[3], 0,
                                                                0, f, b);
   h->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(int64_t n, int nrhs, const int32_t* perm, const double* src, double* dst,
+                               cudaStream_t st) {
+  if (n * nrhs == 0) return cudaSuccess;
+  k_gather_rows<<<blocks_for(n * nrhs), kThreads, 0, st>>>(n, nrhs, perm, src, dst);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,18 @@
 // levels are separated by grid-wide barriers whose waits are bounded; on
 // timeout a block records BDDC_ERR_TIMEOUT and all blocks leave at their next
 // barrier. Values written by other blocks are read through L2 (__ldcg).
+//
+// One right-hand side takes the gather form (k_coarse_gather): at one column
+// the sweeps are bound by chains of dependent memory round trips, not by
+// bytes, so every output value becomes one dot product with an explicit
+// operand index per coefficient, stored in the order the warps consume them.
+// The coefficients and indices are constant, so a warp loads the next batch
+// of them while it waits for the operand values of the current one, and
+// across each grid barrier: after a barrier only the operand loads remain.
+// The contributions to a receiving dof are one contiguous dot, r' is never
+// permuted (an operand that no earlier level has updated is read from r_c in
+// dof order), and the units of each level are assigned to warps on the host,
+// longest first to the least-loaded warp.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,37 +58,36 @@ struct CoarseArgs {
   double* rp;                // r' (elimination order)
   double* y;                 // y (elimination order)
   double* u;                 // u_c (dof order)
-  unsigned int* bar;         // [0] arrivals, [1] generation
+  unsigned int* bar;         // [0] barrier arrivals
   int32_t* err;
   int levels, nrhs;
 };
 
 // Grid-wide barrier; false when a wait ran out (here or in another block).
-__device__ bool grid_barrier(const CoarseArgs& a) {
+// bar counts arrivals since the launch (zeroed before it): the k-th barrier
+// of a launch releases at k * gridDim.x arrivals, so no block resets it.
+// Ordering: the block's writes precede thread 0's release increment (block
+// barrier, then red.release at GPU scope); thread 0's acquire load of the
+// final count precedes the block's later reads (then the block barrier).
+__device__ bool grid_sync(unsigned int* bar, int32_t* err, unsigned int& epoch) {
   __shared__ int ok;
+  const unsigned int target = ++epoch * gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned int* gen = a.bar + 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(a.bar, 1u);
-    if (arrived == gridDim.x - 1) {
-      a.bar[0] = 0;
-      __threadfence();
-      atomicAdd(a.bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (*(volatile int32_t*)a.err == BDDC_ERR_TIMEOUT || clock64() - t0 > kBarrierCycles) {
-          atomicExch(a.err, BDDC_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if (*(volatile int32_t*)err == BDDC_ERR_TIMEOUT || clock64() - t0 > kBarrierCycles) {
+        atomicExch(err, BDDC_ERR_TIMEOUT);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
-    if (*(volatile int32_t*)a.err == BDDC_ERR_TIMEOUT) ok = 0;
+    if (*(volatile int32_t*)err == BDDC_ERR_TIMEOUT) ok = 0;
   }
   __syncthreads();
   return ok != 0;
@@ -377,7 +388,8 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
     const int64_t pos = i / a.nrhs;
     a.rp[i] = a.r[(int64_t)a.order[pos] * a.nrhs + (i - pos * a.nrhs)];
   }
-  if (!grid_barrier(a)) return;
+  unsigned int epoch = 0;
+  if (!grid_sync(a.bar, a.err, epoch)) return;
   for (int lv = 0; lv < L; ++lv) {
     for (int64_t t = (int64_t)off_f[lv] * nrb + gw; t < (int64_t)off_f[lv + 1] * nrb; t += nw) {
       const int64_t ui = t / nrb;
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
       else
         forward_unit(a, w, lane, kb, ke);
     }
-    if (!grid_barrier(a)) return;
+    if (!grid_sync(a.bar, a.err, epoch)) return;
   }
   for (int lv = L - 1; lv >= 0; --lv) {
     for (int64_t t = (int64_t)off_b[lv] * nrb + gw; t < (int64_t)off_b[lv + 1] * nrb; t += nw) {
@@ -399,7 +411,146 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
       else
         backward_unit(a, a.units[ui], lane, kb, ke);
     }
-    if (lv > 0 && !grid_barrier(a)) return;
+    if (lv > 0 && !grid_sync(a.bar, a.err, epoch)) return;
+  }
+}
+
+// ---- gather form (one right-hand side) --------------------------------------------------
+constexpr int kGThreads = 512;    // one block per SM
+constexpr int kGU = 8;            // coefficients per lane per batch (256 per warp)
+constexpr int kGBatch = 32 * kGU;
+
+struct GatherArgs {
+  const CGUnit* units;
+  const int32_t* wo;         // [2 L][warps + 1] descriptor offsets
+  const double* C;
+  const int32_t* I;
+  const double* r;           // r_c (dof order)
+  double* rp;                // r' (forward), then u (backward), elimination order
+  double* y;                 // y (elimination order)
+  double* u;                 // u_c (dof order)
+  unsigned int* bar;
+  int32_t* err;
+  int levels, n_c;
+};
+
+// Coefficients and operand indices of one batch: elements base + lane + 32 i
+// of a unit; past its end the index is -1 (the operand is not read).
+__device__ __forceinline__ void gather_batch(const GatherArgs& a, int64_t off, int len, int base, int lane,
+                                             double (&c)[kGU], int (&ix)[kGU]) {
+#pragma unroll
+  for (int i = 0; i < kGU; ++i) {
+    const int j = base + lane + 32 * i;
+    const bool in = j < len;
+    c[i] = in ? __ldg(a.C + off + j) : 0.0;
+    ix[i] = in ? __ldg(a.I + off + j) : -1;
+  }
+}
+
+// Lane l holds the descriptor of the warp's unit m0 + l of a phase.
+__device__ __forceinline__ CGUnit gather_desc(const GatherArgs& a, int beg, int cnt, int m0, int lane) {
+  CGUnit d{0, 0, 0, 0, 0};
+  if (m0 + lane < cnt) d = a.units[beg + m0 + lane];
+  return d;
+}
+
+__device__ __forceinline__ double gather_x(const double* A, const double* B, int n_c, int ix) {
+  return __ldcg(ix < n_c ? A + ix : B + (ix - n_c));
+}
+
+__global__ void __launch_bounds__(kGThreads, 1) k_coarse_gather(GatherArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (kGThreads / 32);
+  const int gw = blockIdx.x * (kGThreads / 32) + (threadIdx.x >> 5);
+  const int P = 2 * a.levels;
+  unsigned int epoch = 0;
+  int beg = a.wo[gw], cnt = a.wo[gw + 1] - beg;
+  CGUnit dl = gather_desc(a, beg, cnt, 0, lane);
+  // nc / nix: the batch to be used next, loaded ahead (pre)
+  double nc[kGU];
+  int nix[kGU];
+  bool pre = false;
+  if (cnt > 0) {
+    gather_batch(a, __shfl_sync(0xffffffffu, dl.off, 0), __shfl_sync(0xffffffffu, dl.len, 0), 0, lane, nc, nix);
+    pre = true;
+  }
+  for (int ph = 0; ph < P; ++ph) {
+    int nbeg = 0, ncnt = 0;
+    CGUnit ndl{0, 0, 0, 0, 0};
+    if (ph + 1 < P) {
+      const int32_t* w = a.wo + (int64_t)(ph + 1) * (nw + 1) + gw;
+      nbeg = w[0];
+      ncnt = w[1] - nbeg;
+      ndl = gather_desc(a, nbeg, ncnt, 0, lane);
+    }
+    const bool fwd = ph < a.levels;
+    const double* XA = fwd ? a.rp : a.y;
+    const double* XB = fwd ? a.r : a.rp;
+    for (int m = 0; m < cnt; ++m) {
+      if (m > 0 && (m & 31) == 0) dl = gather_desc(a, beg, cnt, m, lane);
+      const int sl = m & 31;
+      const int64_t off = __shfl_sync(0xffffffffu, dl.off, sl);
+      const int len = __shfl_sync(0xffffffffu, dl.len, sl);
+      const int dst = __shfl_sync(0xffffffffu, dl.dst, sl);
+      const int aux = __shfl_sync(0xffffffffu, dl.aux, sl);
+      if (!pre) gather_batch(a, off, len, 0, lane, nc, nix);
+      double s = 0.0, x0 = 0.0;
+      for (int base = 0; base < len; base += kGBatch) {
+        double c[kGU], xv[kGU];
+        int ix[kGU];
+#pragma unroll
+        for (int i = 0; i < kGU; ++i) {
+          c[i] = nc[i];
+          ix[i] = nix[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kGU; ++i) xv[i] = ix[i] >= 0 ? gather_x(XA, XB, a.n_c, ix[i]) : 0.0;
+        if (base == 0 && fwd && aux >= 0) x0 = gather_x(XA, XB, a.n_c, aux);
+        // the next batch: of this unit, else the first of the next unit
+        // (this phase or the next one)
+        pre = true;
+        if (base + kGBatch < len) {
+          gather_batch(a, off, len, base + kGBatch, lane, nc, nix);
+        } else if (m + 1 < cnt) {
+          const int s2 = (m + 1) & 31;
+          if (s2 != 0)
+            gather_batch(a, __shfl_sync(0xffffffffu, dl.off, s2), __shfl_sync(0xffffffffu, dl.len, s2), 0, lane,
+                         nc, nix);
+          else
+            pre = false;
+        } else if (ncnt > 0) {
+          gather_batch(a, __shfl_sync(0xffffffffu, ndl.off, 0), __shfl_sync(0xffffffffu, ndl.len, 0), 0, lane, nc,
+                       nix);
+        } else {
+          pre = false;
+        }
+#pragma unroll
+        for (int i = 0; i < kGU; ++i) s = fma(c[i], xv[i], s);
+      }
+      s = warp_sum(s);
+      if (lane == 0) {
+        if (!fwd) {
+          a.rp[dst] = s;
+          a.u[aux] = s;
+        } else if (aux < 0) {
+          a.y[dst] = s;
+        } else {
+          a.rp[dst] = x0 - s;
+        }
+      }
+    }
+    if (cnt == 0) {
+      pre = false;
+      if (ncnt > 0) {
+        gather_batch(a, __shfl_sync(0xffffffffu, ndl.off, 0), __shfl_sync(0xffffffffu, ndl.len, 0), 0, lane, nc,
+                     nix);
+        pre = true;
+      }
+    }
+    if (ph + 1 < P && !grid_sync(a.bar, a.err, epoch)) return;
+    beg = nbeg;
+    cnt = ncnt;
+    dl = ndl;
   }
 }
 
@@ -412,6 +563,157 @@ cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
   *dst = static_cast<T*>(p);
   if (!v.empty()) e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
+}
+
+// Gather form of both sweeps for a grid of `blocks` blocks of kGThreads:
+// phases 0 .. L-1 are the forward levels (height lv), phases L .. 2L-1 the
+// backward levels (height 2L-1-phase). Within a phase the units are assigned
+// to warps longest first, each to the warp with the least work so far, and
+// stored warp by warp; the coefficients and indices of a unit are contiguous.
+}  // namespace
+
+void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, GatherLayout& g) {
+  const int nw = blocks * warps_per_block;
+  const int L = cf.n_levels;
+  const int nn = (int)cf.nodes.size();
+  const int32_t n = (int32_t)cf.n;
+  std::vector<int32_t> pos(n), first(nn);
+  for (int32_t i = 0; i < n; ++i) pos[cf.order[i]] = i;
+  for (int t = 0; t < nn; ++t) first[t] = cf.nodes[t].last - cf.nodes[t].p + 1;
+  // kind 0: row i of node a (forward); kind 1: receiving position a with
+  // contributions [cb, ce) of rlist; kind 2: row i of node a (backward)
+  struct GU {
+    int32_t kind, a, i, len, cb, ce;
+  };
+  std::vector<int8_t> has(n, 0);   // r' at this position updated by an earlier level
+  auto xf = [&](int32_t q) { return has[q] ? q : n + cf.order[q]; };
+  std::vector<std::vector<int32_t>> recv(n);
+  std::vector<int32_t> touched, rlist, ord;
+  std::vector<GU> us;
+  std::vector<CGUnit>& gu = g.units;
+  std::vector<double>& gC = g.C;
+  std::vector<int32_t>& gI = g.I;
+  std::vector<int32_t>& wo = g.wo;
+  gu.clear();
+  gC.clear();
+  gI.clear();
+  wo.assign((size_t)2 * L * (nw + 1), 0);
+  int64_t total = 0;
+  for (const CoarseNode& T : cf.nodes) total += 2 * (int64_t)T.p * (T.p + T.u);
+  gC.reserve((size_t)total);
+  gI.reserve((size_t)total);
+  std::vector<std::vector<int32_t>> per(nw);
+  for (int ph = 0; ph < 2 * L; ++ph) {
+    const bool fwd = ph < L;
+    const int lv = fwd ? ph : 2 * L - 1 - ph;
+    us.clear();
+    rlist.clear();
+    touched.clear();
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      if (T.height != lv || T.p == 0) continue;
+      for (int i = 0; i < T.p; ++i) us.push_back(GU{fwd ? 0 : 2, t, i, fwd ? i + 1 : T.p - i + T.u, 0, 0});
+      if (!fwd) continue;
+      for (int b = 0; b < T.u; ++b) {
+        const int32_t w = pos[T.upd[b]];
+        if (recv[w].empty()) touched.push_back(w);
+        recv[w].push_back(t);
+        recv[w].push_back(b);
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int32_t w : touched) {
+      const int32_t cb = (int32_t)rlist.size();
+      int32_t len = 0;
+      for (size_t q = 0; q < recv[w].size(); q += 2) {
+        rlist.push_back(recv[w][q]);
+        rlist.push_back(recv[w][q + 1]);
+        len += cf.nodes[recv[w][q]].p;
+      }
+      us.push_back(GU{1, w, 0, len, cb, (int32_t)rlist.size()});
+      recv[w].clear();
+    }
+    // longest first to the least-loaded warp (cost: batches of kGBatch, and
+    // a quarter batch per unit for its reduction and store)
+    ord.resize(us.size());
+    for (size_t k = 0; k < us.size(); ++k) ord[k] = (int32_t)k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return us[x].len > us[y].len; });
+    for (auto& v : per) v.clear();
+    std::vector<std::pair<int64_t, int32_t>> heap;
+    heap.reserve(nw);
+    for (int w = 0; w < nw; ++w) heap.emplace_back(0, w);
+    auto gt = [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) { return x > y; };
+    for (int32_t k : ord) {
+      std::pop_heap(heap.begin(), heap.end(), gt);
+      auto& top = heap.back();
+      per[top.second].push_back(k);
+      top.first += 4 * ((us[k].len + kGBatch - 1) / kGBatch) + 1;
+      std::push_heap(heap.begin(), heap.end(), gt);
+    }
+    // the h-th least-loaded warp is warp h / blocks of block h % blocks, so
+    // the work of a small level spreads over all SMs (their FP64 pipes)
+    int32_t* wrow = &wo[(size_t)ph * (nw + 1)];
+    for (int w = 0; w < nw; ++w) {
+      wrow[w] = (int32_t)gu.size();
+      for (int32_t k : per[(w % warps_per_block) * blocks + w / warps_per_block]) {
+        const GU& x = us[k];
+        CGUnit d{(int64_t)gC.size(), x.len, 0, -1, 0};
+        if (x.kind == 0) {
+          const CoarseNode& T = cf.nodes[x.a];
+          const int32_t pos0 = first[x.a];
+          for (int j = 0; j <= x.i; ++j) {
+            gC.push_back(T.Fm[(size_t)x.i * T.p + j]);
+            gI.push_back(xf(pos0 + j));
+          }
+          d.dst = pos0 + x.i;
+        } else if (x.kind == 1) {
+          for (int32_t q = x.cb; q < x.ce; q += 2) {
+            const CoarseNode& T = cf.nodes[rlist[q]];
+            const int32_t pos0 = first[rlist[q]], b = rlist[q + 1];
+            for (int j = 0; j < T.p; ++j) {
+              gC.push_back(T.Fm[(size_t)(T.p + b) * T.p + j]);
+              gI.push_back(xf(pos0 + j));
+            }
+          }
+          d.dst = x.a;
+          d.aux = xf(x.a);
+        } else {
+          const CoarseNode& T = cf.nodes[x.a];
+          const int32_t pos0 = first[x.a];
+          const size_t f = (size_t)T.p + T.u;
+          for (int j = x.i; j < T.p; ++j) {
+            gC.push_back(T.Bm[(size_t)x.i * f + j]);
+            gI.push_back(pos0 + j);
+          }
+          for (int b = 0; b < T.u; ++b) {
+            gC.push_back(T.Bm[(size_t)x.i * f + T.p + b]);
+            gI.push_back(n + pos[T.upd[b]]);
+          }
+          d.dst = pos0 + x.i;
+          d.aux = cf.order[pos0 + x.i];
+        }
+        gu.push_back(d);
+      }
+    }
+    wrow[nw] = (int32_t)gu.size();
+    if (fwd)
+      for (const GU& x : us)
+        if (x.kind == 1) has[x.a] = 1;
+  }
+}
+
+namespace {
+
+cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, int blocks) {
+  GatherLayout g;
+  gather_layout(cf, blocks, kGThreads / 32, g);
+  h->g_entries = (int64_t)g.C.size();
+  h->g_blocks = blocks;
+  cudaError_t e;
+  if ((e = up(h, &h->d_gC, g.C)) != cudaSuccess) return e;
+  if ((e = up(h, &h->d_gI, g.I)) != cudaSuccess) return e;
+  if ((e = up(h, &h->d_gU, g.units)) != cudaSuccess) return e;
+  return up(h, &h->d_gwo, g.wo);
 }
 
 }  // namespace
@@ -536,7 +838,10 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   h->c_grid4 = sms * std::min(per_sm, 2);
-  return cudaSuccess;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_gather, kGThreads, 0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorNotSupported;
+  return build_gather(h, cf, h->g_blocks > 0 ? std::min(h->g_blocks, sms) : sms);
 }
 
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st,
@@ -545,20 +850,34 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   // row blocking pays from about 16 right-hand sides on (fewer, longer units
   // per level; measured on 10439 coarse dofs); the autotuner may move the
   // threshold
+  cudaError_t e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  if (nrhs == 1 && h->d_gU) {
+    GatherArgs g{h->d_gU, h->d_gwo, h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
+                 h->c_levels, (int)h->n_c};
+    if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->g_blocks);
+    cfg.blockDim = dim3(kGThreads);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_coarse_gather, g);
+    h->launches++;
+    return e;
+  }
   const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
   CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
                blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
                h->c_levels, nrhs};
-  cudaError_t e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st);
-  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(narrow ? h->c_sms : blocked ? h->c_grid4 : h->c_grid);
   cfg.blockDim = dim3((narrow || blocked) ? kThreads / 2 : kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   e = blocked ? cudaLaunchKernelEx(&cfg, k_coarse_solve<kRB>, a) : cudaLaunchKernelEx(&cfg, k_coarse_solve<1>, a);

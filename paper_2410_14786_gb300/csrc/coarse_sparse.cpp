@@ -137,6 +137,16 @@ struct Dissection {
 
 }  // namespace
 
+void coarse_renumber(CoarseFactor& cf, std::vector<int32_t>& perm) {
+  perm.assign(cf.n, 0);
+  for (int64_t i = 0; i < cf.n; ++i) perm[cf.order[i]] = (int32_t)i;
+  for (CoarseNode& T : cf.nodes) {
+    for (int32_t& v : T.piv) v = perm[v];
+    for (int32_t& w : T.upd) w = perm[w];
+  }
+  for (int64_t i = 0; i < cf.n; ++i) cf.order[i] = (int32_t)i;
+}
+
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
                   const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {

@@ -27,6 +27,32 @@ struct CNodeDev {
 struct CUnit {
   int32_t kind, a, row, b, e;
 };
+// One output value of a coarse sweep in the gather form (one right-hand
+// side): value = sum_{j < len} C[off + j] * X[I[off + j]], where an index
+// below n_c addresses the first operand vector and an index n_c + i entry i
+// of the second (forward: r' in elimination order, r_c in dof order;
+// backward: y, u in elimination order). Forward: aux < 0 writes y[dst]; aux
+// >= 0 writes r'[dst] = X[aux] - value. Backward: writes u at position dst
+// and at dof aux.
+struct CGUnit {
+  int64_t off;
+  int32_t len, dst, aux, pad;
+};
+// The gather form of both sweeps for blocks x warps_per_block warps
+// (coarse_solve.cu), warp w of block b being warp b * warps_per_block + w:
+// phases 0 .. L-1 are the forward levels (height = phase), phases L .. 2L-1
+// the backward levels (height = 2L-1-phase). The descriptors of warp w in
+// phase ph are units[wo[ph (warps+1) + w] .. wo[ph (warps+1) + w + 1]),
+// warps = blocks x warps_per_block,
+// processed in that order; C and I hold each unit's coefficients and operand
+// indices contiguously.
+struct CoarseFactor;
+struct GatherLayout {
+  std::vector<CGUnit> units;
+  std::vector<double> C;
+  std::vector<int32_t> I, wo;
+};
+void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, GatherLayout& g);
 // One contribution to a receiving dof: an M row of a node and its operand.
 struct CContrib {
   int64_t row_off;  // offset of the M row in the forward matrices
@@ -87,6 +113,10 @@ struct CoarseFactor {
 // (CSR, both triangles); xyz: 3 coordinates per dof for the dissection.
 // dof_subs: the subdomains of every coarse dof (glob); sub_xyz: centroid of
 // every subdomain (3 per subdomain) for the dissection.
+// Renumbers the coarse dofs of a factorisation by their elimination
+// position (pivot and update-set lists; the order becomes the identity);
+// perm[old dof] = new dof.
+void coarse_renumber(CoarseFactor& cf, std::vector<int32_t>& perm);
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
                   const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err);
@@ -199,10 +229,19 @@ struct bddc_handle_s {
   bddc::CContrib* d_clist = nullptr;  // contributions of the receiving units
   int32_t* d_cupd = nullptr;          // update-set dofs of every node
   int32_t* d_corder = nullptr;        // elimination position -> coarse dof
+  int32_t* d_cperm = nullptr;         // glob -> device coarse dof (sparse coarse: elimination order)
   int32_t* d_clvl = nullptr;          // unit offsets: [L+1 forward][L+1 backward], then n_c
   unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
   bddc::CUnit* d_cunits4 = nullptr;   // the same with kinds 0 and 2 blocked by 4 rows
   int32_t* d_clvl4 = nullptr;
+  // gather form of the sweeps (one right-hand side): coefficients and operand
+  // indices in warp order, unit descriptors, per-phase per-warp offsets
+  double* d_gC = nullptr;
+  int32_t* d_gI = nullptr;
+  bddc::CGUnit* d_gU = nullptr;
+  int32_t* d_gwo = nullptr;           // [2 L][warps + 1]
+  int g_blocks = 0;                   // grid the warp assignment was made for (requested: 0 = SMs)
+  int64_t g_entries = 0;
   int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0, c_sms = 0;
   int64_t c_nnz = 0, c_update_total = 0;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;

@@ -57,6 +57,10 @@ size_t tc_operand_bytes(int precision, int64_t cols_total, int nrhs_max);
 cudaError_t launch_tc_gemm(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter,
                            int nrhs, cudaStream_t st);
 
+// dst[i, k] = src[perm[i], k] for i < n, k < nrhs (row gather).
+cudaError_t launch_gather_rows(int64_t n, int nrhs, const int32_t* perm, const double* src, double* dst,
+                               cudaStream_t st);
+
 // Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
 // u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);

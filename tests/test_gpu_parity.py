@@ -24,10 +24,10 @@ def _oracle(p, mask=0):
                   constraints=mask or (CORNER | EDGE | FACE))
 
 
-def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto", phi_fp64=False):
+def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto", phi_fp64=False, coarse_blocks=0):
     from paper_2410_14786_gb300 import BDDC
     return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max, coarse=coarse,
-                             phi_fp64=phi_fp64)
+                             phi_fp64=phi_fp64, coarse_blocks=coarse_blocks)
 
 
 def _small_voronoi():
@@ -108,6 +108,55 @@ def test_apply_sparse_coarse(name):
     rc, uc = g.coarse_vectors(3)
     want = np.stack([o.apply_parts(o.to_free(r[:, k]))["uc"] for k in range(3)], axis=1)
     assert _rel(uc.cpu().numpy(), want) < 1e-11
+
+
+@pytest.mark.parametrize("name,blocks", [("cfg1_2d", 0), ("3d_24_3cubed", 0), ("3d_voronoi", 0),
+                                         ("3d_corners_only", 0), ("3d_voronoi", 1)])
+def test_one_column_sparse_coarse(name, blocks):
+    """One right-hand side: the sweeps of the sparse coarse solve in their
+    gather form (one dot product per output value, warps assigned on the
+    host) give the oracle's exact u_c."""
+    p, mask, o = _case(name)
+    g = _bddc(p, mask=mask, coarse="sparse", coarse_blocks=blocks)
+    r = synth.uniform(38, o.n_nodes)
+    r[o.dir] = 0
+    z = g.apply(_cuda(r)).cpu().numpy()
+    parts = o.apply_parts(o.to_free(r))
+    assert _rel(z, o.to_nodes(parts["z"])) < 1e-11
+    rc, uc = g.coarse_vectors()
+    assert _rel(rc.cpu().numpy()[:, 0], parts["rc"]) < 1e-11
+    assert _rel(uc.cpu().numpy()[:, 0], parts["uc"]) < 1e-11
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 3])
+def test_one_column_sparse_coarse_many_levels(blocks):
+    """48^3 elements in 8^3 cubes: 2863 coarse dofs, 4 levels. With one or
+    three blocks every warp walks more than 32 units of a level. The one-column
+    sweeps against the dense inverse (pinned to the oracle above) and against
+    the multi-column sweeps; the PCG iteration count is unchanged."""
+    p = synth.make_problem(3, 48, 8, "lognormal", k=24)
+    gs = _bddc(p, coarse="sparse", coarse_blocks=blocks)
+    assert gs.info()["coarse_levels"] >= 3
+    gd = _bddc(p, coarse="dense")
+    gm = _bddc(p, coarse="sparse", nrhs_max=2)
+    n = (p.ne + 1) ** 3
+    r = torch.from_numpy(synth.uniform(39, n * 2).reshape(n, 2)).cuda()
+    zs, zd = gs.apply(r[:, 0].contiguous()), gd.apply(r[:, 0].contiguous())
+    _, uc_s = gs.coarse_vectors()
+    _, uc_d = gd.coarse_vectors()
+    zm = gm.apply(r)
+    _, uc_m = gm.coarse_vectors(2)
+    assert float((uc_s[:, 0] - uc_d[:, 0]).abs().max() / uc_d.abs().max()) < 1e-11
+    assert float((uc_s[:, 0] - uc_m[:, 0]).abs().max() / uc_d.abs().max()) < 1e-11
+    assert float((zs - zd).abs().max() / zd.abs().max()) < 1e-11
+    assert float((zs - zm[:, 0]).abs().max() / zd.abs().max()) < 1e-11
+    b = gs.rhs(torch.from_numpy(p.f[:, 0].copy()).cuda())
+    xs, rs = gs.pcg_solve(b, rtol=1e-8)
+    xd, rd = gd.pcg_solve(b, rtol=1e-8)
+    assert rs.status == 0 and int(rs.iters[0]) == int(rd.iters[0])
+    assert float((xs - xd).norm() / xd.norm()) < 1e-9
+    for g in (gs, gd, gm):
+        g.close()
 
 
 def test_pcg_sparse_coarse_matches_oracle():
