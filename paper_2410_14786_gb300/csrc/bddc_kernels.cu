@@ -509,8 +509,9 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   // The interface operator (z_G = K_GG y'_G) and the coarse residual and
   // solve depend only on y'_G: with tune_overlap they run concurrently, the
   // interface operator on a second stream capped at 2 blocks per SM, the
-  // coarse sweeps on one 512-thread block per SM, so that both fit on every
-  // SM at once (the coarse kernel is cooperative: its grid must be resident).
+  // coarse sweeps on one block of 256 (one column) or 512 threads per SM, so
+  // that both fit on every SM at once (the coarse kernel is cooperative: its
+  // grid must be resident).
   const int ax = h->aux_sel;
   const bool overlap = h->tune_overlap && h->nG_tot && h->n_c && !h->coarse_dense && h->aux_stream[ax];
   if (overlap) {

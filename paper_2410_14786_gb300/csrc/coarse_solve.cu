@@ -17,7 +17,7 @@
 // timeout a block records BDDC_ERR_TIMEOUT and all blocks leave at their next
 // barrier. Values written by other blocks are read through L2 (__ldcg).
 //
-// One right-hand side takes the gather form (k_coarse_gather): at one column
+// One right-hand side takes the gather form (k_coarse_sweeps): at one column
 // the sweeps are bound by chains of dependent memory round trips, not by
 // bytes, so every output value becomes one dot product with an explicit
 // operand index per coefficient, stored in the order the warps consume them.
@@ -416,7 +416,10 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
 }
 
 // ---- gather form (one right-hand side) --------------------------------------------------
-constexpr int kGThreads = 512;    // one block per SM
+// One block per SM, at most 128 registers a thread: 512 threads when the
+// sweeps run alone, 256 (half an SM's registers) when they overlap the
+// interface operator, whose two streamed-GEMV blocks per SM then fit beside.
+constexpr int kGThreadsWide = 512, kGThreadsNarrow = 256;
 constexpr int kGU = 8;            // coefficients per lane per batch (256 per warp)
 constexpr int kGBatch = 32 * kGU;
 
@@ -458,10 +461,11 @@ __device__ __forceinline__ double gather_x(const double* A, const double* B, int
   return __ldcg(ix < n_c ? A + ix : B + (ix - n_c));
 }
 
-__global__ void __launch_bounds__(kGThreads, 1) k_coarse_gather(GatherArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(GatherArgs a) {
   const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (kGThreads / 32);
-  const int gw = blockIdx.x * (kGThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (NT / 32);
+  const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
   const int P = 2 * a.levels;
   unsigned int epoch = 0;
   int beg = a.wo[gw], cnt = a.wo[gw + 1] - beg;
@@ -565,15 +569,17 @@ cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
   return e;
 }
 
-// Gather form of both sweeps for a grid of `blocks` blocks of kGThreads:
-// phases 0 .. L-1 are the forward levels (height lv), phases L .. 2L-1 the
-// backward levels (height 2L-1-phase). Within a phase the units are assigned
-// to warps longest first, each to the warp with the least work so far, and
-// stored warp by warp; the coefficients and indices of a unit are contiguous.
 }  // namespace
 
-void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, GatherLayout& g) {
-  const int nw = blocks * warps_per_block;
+// Gather form of both sweeps: phases 0 .. L-1 are the forward levels (height
+// lv), phases L .. 2L-1 the backward levels (height 2L-1-phase). The
+// coefficients and indices of the units of a phase are stored longest unit
+// first; for each launch shape the units are assigned to warps longest first,
+// each to the warp with the least work so far, and their descriptors stored
+// warp by warp.
+
+void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const int* warps_per_block,
+                   GatherLayout& g) {
   const int L = cf.n_levels;
   const int nn = (int)cf.nodes.size();
   const int32_t n = (int32_t)cf.n;
@@ -590,19 +596,20 @@ void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, Gath
   std::vector<std::vector<int32_t>> recv(n);
   std::vector<int32_t> touched, rlist, ord;
   std::vector<GU> us;
-  std::vector<CGUnit>& gu = g.units;
+  std::vector<CGUnit> desc;
   std::vector<double>& gC = g.C;
   std::vector<int32_t>& gI = g.I;
-  std::vector<int32_t>& wo = g.wo;
-  gu.clear();
   gC.clear();
   gI.clear();
-  wo.assign((size_t)2 * L * (nw + 1), 0);
+  g.units.assign(nshapes, {});
+  g.wo.assign(nshapes, {});
+  for (int sh = 0; sh < nshapes; ++sh)
+    g.wo[sh].assign((size_t)2 * L * (blocks[sh] * warps_per_block[sh] + 1), 0);
   int64_t total = 0;
   for (const CoarseNode& T : cf.nodes) total += 2 * (int64_t)T.p * (T.p + T.u);
   gC.reserve((size_t)total);
   gI.reserve((size_t)total);
-  std::vector<std::vector<int32_t>> per(nw);
+  std::vector<std::vector<int32_t>> per;
   for (int ph = 0; ph < 2 * L; ++ph) {
     const bool fwd = ph < L;
     const int lv = fwd ? ph : 2 * L - 1 - ph;
@@ -633,69 +640,76 @@ void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, Gath
       us.push_back(GU{1, w, 0, len, cb, (int32_t)rlist.size()});
       recv[w].clear();
     }
-    // longest first to the least-loaded warp (cost: batches of kGBatch, and
-    // a quarter batch per unit for its reduction and store)
+    // coefficients and indices of every unit, longest unit first
     ord.resize(us.size());
     for (size_t k = 0; k < us.size(); ++k) ord[k] = (int32_t)k;
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return us[x].len > us[y].len; });
-    for (auto& v : per) v.clear();
-    std::vector<std::pair<int64_t, int32_t>> heap;
-    heap.reserve(nw);
-    for (int w = 0; w < nw; ++w) heap.emplace_back(0, w);
-    auto gt = [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) { return x > y; };
+    desc.resize(us.size());
     for (int32_t k : ord) {
-      std::pop_heap(heap.begin(), heap.end(), gt);
-      auto& top = heap.back();
-      per[top.second].push_back(k);
-      top.first += 4 * ((us[k].len + kGBatch - 1) / kGBatch) + 1;
-      std::push_heap(heap.begin(), heap.end(), gt);
-    }
-    // the h-th least-loaded warp is warp h / blocks of block h % blocks, so
-    // the work of a small level spreads over all SMs (their FP64 pipes)
-    int32_t* wrow = &wo[(size_t)ph * (nw + 1)];
-    for (int w = 0; w < nw; ++w) {
-      wrow[w] = (int32_t)gu.size();
-      for (int32_t k : per[(w % warps_per_block) * blocks + w / warps_per_block]) {
-        const GU& x = us[k];
-        CGUnit d{(int64_t)gC.size(), x.len, 0, -1, 0};
-        if (x.kind == 0) {
-          const CoarseNode& T = cf.nodes[x.a];
-          const int32_t pos0 = first[x.a];
-          for (int j = 0; j <= x.i; ++j) {
-            gC.push_back(T.Fm[(size_t)x.i * T.p + j]);
+      const GU& x = us[k];
+      CGUnit d{(int64_t)gC.size(), x.len, 0, -1, 0};
+      if (x.kind == 0) {
+        const CoarseNode& T = cf.nodes[x.a];
+        const int32_t pos0 = first[x.a];
+        for (int j = 0; j <= x.i; ++j) {
+          gC.push_back(T.Fm[(size_t)x.i * T.p + j]);
+          gI.push_back(xf(pos0 + j));
+        }
+        d.dst = pos0 + x.i;
+      } else if (x.kind == 1) {
+        for (int32_t q = x.cb; q < x.ce; q += 2) {
+          const CoarseNode& T = cf.nodes[rlist[q]];
+          const int32_t pos0 = first[rlist[q]], b = rlist[q + 1];
+          for (int j = 0; j < T.p; ++j) {
+            gC.push_back(T.Fm[(size_t)(T.p + b) * T.p + j]);
             gI.push_back(xf(pos0 + j));
           }
-          d.dst = pos0 + x.i;
-        } else if (x.kind == 1) {
-          for (int32_t q = x.cb; q < x.ce; q += 2) {
-            const CoarseNode& T = cf.nodes[rlist[q]];
-            const int32_t pos0 = first[rlist[q]], b = rlist[q + 1];
-            for (int j = 0; j < T.p; ++j) {
-              gC.push_back(T.Fm[(size_t)(T.p + b) * T.p + j]);
-              gI.push_back(xf(pos0 + j));
-            }
-          }
-          d.dst = x.a;
-          d.aux = xf(x.a);
-        } else {
-          const CoarseNode& T = cf.nodes[x.a];
-          const int32_t pos0 = first[x.a];
-          const size_t f = (size_t)T.p + T.u;
-          for (int j = x.i; j < T.p; ++j) {
-            gC.push_back(T.Bm[(size_t)x.i * f + j]);
-            gI.push_back(pos0 + j);
-          }
-          for (int b = 0; b < T.u; ++b) {
-            gC.push_back(T.Bm[(size_t)x.i * f + T.p + b]);
-            gI.push_back(n + pos[T.upd[b]]);
-          }
-          d.dst = pos0 + x.i;
-          d.aux = cf.order[pos0 + x.i];
         }
-        gu.push_back(d);
+        d.dst = x.a;
+        d.aux = xf(x.a);
+      } else {
+        const CoarseNode& T = cf.nodes[x.a];
+        const int32_t pos0 = first[x.a];
+        const size_t f = (size_t)T.p + T.u;
+        for (int j = x.i; j < T.p; ++j) {
+          gC.push_back(T.Bm[(size_t)x.i * f + j]);
+          gI.push_back(pos0 + j);
+        }
+        for (int b = 0; b < T.u; ++b) {
+          gC.push_back(T.Bm[(size_t)x.i * f + T.p + b]);
+          gI.push_back(n + pos[T.upd[b]]);
+        }
+        d.dst = pos0 + x.i;
+        d.aux = cf.order[pos0 + x.i];
       }
+      desc[k] = d;
     }
-    wrow[nw] = (int32_t)gu.size();
+    // per launch shape: longest first to the least-loaded warp (cost: batches
+    // of kGBatch, and a quarter batch per unit for its reduction and store);
+    // the h-th least-loaded warp is warp h / blocks of block h % blocks, so
+    // the work of a small level spreads over all SMs (their FP64 pipes)
+    for (int sh = 0; sh < nshapes; ++sh) {
+      const int nb = blocks[sh], wpb = warps_per_block[sh], nw = nb * wpb;
+      per.assign(nw, {});
+      std::vector<std::pair<int64_t, int32_t>> heap;
+      heap.reserve(nw);
+      for (int w = 0; w < nw; ++w) heap.emplace_back(0, w);
+      auto gt = [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) { return x > y; };
+      for (int32_t k : ord) {
+        std::pop_heap(heap.begin(), heap.end(), gt);
+        auto& top = heap.back();
+        per[top.second].push_back(k);
+        top.first += 4 * ((us[k].len + kGBatch - 1) / kGBatch) + 1;
+        std::push_heap(heap.begin(), heap.end(), gt);
+      }
+      std::vector<CGUnit>& gu = g.units[sh];
+      int32_t* wrow = &g.wo[sh][(size_t)ph * (nw + 1)];
+      for (int w = 0; w < nw; ++w) {
+        wrow[w] = (int32_t)gu.size();
+        for (int32_t k : per[(w % wpb) * nb + w / wpb]) gu.push_back(desc[k]);
+      }
+      wrow[nw] = (int32_t)gu.size();
+    }
     if (fwd)
       for (const GU& x : us)
         if (x.kind == 1) has[x.a] = 1;
@@ -706,14 +720,18 @@ namespace {
 
 cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, int blocks) {
   GatherLayout g;
-  gather_layout(cf, blocks, kGThreads / 32, g);
+  const int nb[2] = {blocks, blocks}, wpb[2] = {kGThreadsWide / 32, kGThreadsNarrow / 32};
+  gather_layout(cf, 2, nb, wpb, g);
   h->g_entries = (int64_t)g.C.size();
   h->g_blocks = blocks;
   cudaError_t e;
   if ((e = up(h, &h->d_gC, g.C)) != cudaSuccess) return e;
   if ((e = up(h, &h->d_gI, g.I)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_gU, g.units)) != cudaSuccess) return e;
-  return up(h, &h->d_gwo, g.wo);
+  for (int sh = 0; sh < 2; ++sh) {
+    if ((e = up(h, &h->d_gU[sh], g.units[sh])) != cudaSuccess) return e;
+    if ((e = up(h, &h->d_gwo[sh], g.wo[sh])) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -838,7 +856,12 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   h->c_grid4 = sms * std::min(per_sm, 2);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_gather, kGThreads, 0)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsWide>, kGThreadsWide,
+                                                         0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorNotSupported;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsNarrow>,
+                                                         kGThreadsNarrow, 0)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
   return build_gather(h, cf, h->g_blocks > 0 ? std::min(h->g_blocks, sms) : sms);
@@ -854,17 +877,19 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
-  if (nrhs == 1 && h->d_gU) {
-    GatherArgs g{h->d_gU, h->d_gwo, h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
+  if (nrhs == 1 && h->d_gC) {
+    const int sh = narrow ? 1 : 0;
+    GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
                  h->c_levels, (int)h->n_c};
     if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->g_blocks);
-    cfg.blockDim = dim3(kGThreads);
+    cfg.blockDim = dim3(narrow ? kGThreadsNarrow : kGThreadsWide);
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_coarse_gather, g);
+    e = narrow ? cudaLaunchKernelEx(&cfg, k_coarse_sweeps<kGThreadsNarrow>, g)
+               : cudaLaunchKernelEx(&cfg, k_coarse_sweeps<kGThreadsWide>, g);
     h->launches++;
     return e;
   }

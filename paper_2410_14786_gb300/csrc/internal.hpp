@@ -38,21 +38,22 @@ struct CGUnit {
   int64_t off;
   int32_t len, dst, aux, pad;
 };
-// The gather form of both sweeps for blocks x warps_per_block warps
-// (coarse_solve.cu), warp w of block b being warp b * warps_per_block + w:
-// phases 0 .. L-1 are the forward levels (height = phase), phases L .. 2L-1
-// the backward levels (height = 2L-1-phase). The descriptors of warp w in
-// phase ph are units[wo[ph (warps+1) + w] .. wo[ph (warps+1) + w + 1]),
-// warps = blocks x warps_per_block,
-// processed in that order; C and I hold each unit's coefficients and operand
-// indices contiguously.
+// The gather form of both sweeps (coarse_solve.cu): C and I hold each
+// unit's coefficients and operand indices contiguously; for each launch shape
+// s (blocks[s] x warps_per_block[s] warps, warp w of block b being warp
+// b * warps_per_block[s] + w) the descriptors of warp w in phase ph are
+// units[s][wo[s][ph (warps+1) + w] .. wo[s][ph (warps+1) + w + 1]), processed
+// in that order. Phases 0 .. L-1 are the forward levels (height = phase),
+// phases L .. 2L-1 the backward levels (height = 2L-1-phase).
 struct CoarseFactor;
 struct GatherLayout {
-  std::vector<CGUnit> units;
   std::vector<double> C;
-  std::vector<int32_t> I, wo;
+  std::vector<int32_t> I;
+  std::vector<std::vector<CGUnit>> units;
+  std::vector<std::vector<int32_t>> wo;
 };
-void gather_layout(const CoarseFactor& cf, int blocks, int warps_per_block, GatherLayout& g);
+void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const int* warps_per_block,
+                   GatherLayout& g);
 // One contribution to a receiving dof: an M row of a node and its operand.
 struct CContrib {
   int64_t row_off;  // offset of the M row in the forward matrices
@@ -236,10 +237,12 @@ struct bddc_handle_s {
   int32_t* d_clvl4 = nullptr;
   // gather form of the sweeps (one right-hand side): coefficients and operand
   // indices in warp order, unit descriptors, per-phase per-warp offsets
+  // [0]: blocks of 512 threads (the sweeps alone), [1]: blocks of 256
+  // threads (half an SM's registers: beside the interface operator)
   double* d_gC = nullptr;
   int32_t* d_gI = nullptr;
-  bddc::CGUnit* d_gU = nullptr;
-  int32_t* d_gwo = nullptr;           // [2 L][warps + 1]
+  bddc::CGUnit* d_gU[2] = {nullptr, nullptr};
+  int32_t* d_gwo[2] = {nullptr, nullptr};   // [2 L][warps + 1]
   int g_blocks = 0;                   // grid the warp assignment was made for (requested: 0 = SMs)
   int64_t g_entries = 0;
   int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0, c_sms = 0;
