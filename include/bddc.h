@@ -127,6 +127,11 @@ typedef struct {
     int32_t coarse_blocks; /* blocks of the one-column sparse coarse solve (one per SM at
                               most); 0 = one per SM. Fewer blocks give each warp more
                               units of every level (for small coarse problems). >= 0 */
+    int32_t full_operators; /* 1: store the symmetric local operators in full. 0 (default):
+                              in the FP32 and BF16 forms on the CUDA cores with
+                              nrhs_max = 1, A_II^-1 and K_GG are stored as their lower
+                              triangles (about half the bytes) and applied by the
+                              symmetric streamed GEMV; elsewhere in full */
 } bddc_options_t;
 
 typedef struct {
@@ -159,6 +164,7 @@ typedef struct {
                                            (a conditional WHILE node over the iteration), 0 if it
                                            replays one captured iteration at a time or launches
                                            directly */
+    int32_t symmetric_operators;        /* 1 if A_II^-1 and K_GG are stored as lower triangles */
 } bddc_info_t;
 
 /* Build the preconditioner (all factorisations in float64 on the host,

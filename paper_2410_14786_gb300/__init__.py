@@ -62,12 +62,15 @@ class BDDC:
     tune_cache=path keeps those results in a JSON file keyed by the problem's
     shape, partition and form, so a later handle for the same problem reuses
     them without measuring again; coarse_blocks: blocks of the one-column
-    sparse coarse solve (0 = one per SM).
+    sparse coarse solve (0 = one per SM); full_operators=True stores the
+    symmetric local operators in full where they would otherwise be stored
+    as lower triangles (fp32 / bf16 on the CUDA cores with nrhs_max = 1).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
-                 phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None, coarse_blocks=0):
+                 phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None, coarse_blocks=0,
+                 full_operators=False):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -80,7 +83,8 @@ class BDDC:
         opts = _lib.Options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
                             COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
-                            1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores], int(coarse_blocks))
+                            1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores], int(coarse_blocks),
+                            1 if full_operators else 0)
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim
@@ -112,7 +116,7 @@ class BDDC:
         import json
         import os
         key = "|".join([f"dim{self.dim}", f"ne{self.ne}", f"nrhs{self.nrhs_max}", f"prec{self.precision}",
-                        f"tc{self.info()['tensor_cores']}",
+                        f"tc{self.info()['tensor_cores']}", f"sym{self.info()['symmetric_operators']}",
                         hashlib.sha1(np.ascontiguousarray(part, dtype=np.int32).tobytes()).hexdigest()[:16]])
         table = {}
         if cache is not None and os.path.exists(cache):

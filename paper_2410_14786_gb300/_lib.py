@@ -49,7 +49,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
                 ("no_graph", C.c_int32), ("phi_fp64", C.c_int32),
-                ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32), ("full_operators", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -61,7 +61,7 @@ class Info(C.Structure):
         "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
         ("device_error", C.c_int32), ("phi_precision", C.c_int32),
-        ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32)]
+        ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32), ("symmetric_operators", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

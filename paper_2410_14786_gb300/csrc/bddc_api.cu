@@ -98,6 +98,34 @@ std::vector<T> pack_arena(const std::vector<std::vector<double>>& ops, const std
   return out;
 }
 
+// Pack per-subdomain symmetric operators as their lower triangles: row g
+// holds columns 0 .. g (entries averaged with their transposes, the diagonal
+// halved), zero-padded to 16 bytes; blocks aligned to 256 bytes. The
+// operator is L' + L'^T.
+template <typename T>
+std::vector<T> pack_lower(const std::vector<std::vector<double>>& ops, const std::vector<int>& dims, int prec,
+                          std::vector<int64_t>& off, T (*cvt)(double)) {
+  const int64_t align = 256 / (int)sizeof(T);
+  off.assign(ops.size(), 0);
+  int64_t cur = 0;
+  for (size_t s = 0; s < ops.size(); ++s) {
+    cur = (cur + align - 1) / align * align;
+    off[s] = cur;
+    cur += sym_packed_elems(prec, dims[s]);
+  }
+  std::vector<T> out((size_t)std::max<int64_t>(cur, 1), cvt(0.0));
+  for (size_t s = 0; s < ops.size(); ++s) {
+    const int n = dims[s];
+    const std::vector<double>& A = ops[s];
+    for (int g = 0; g < n; ++g) {
+      T* row = &out[off[s] + sym_packed_elems(prec, g)];
+      for (int c = 0; c < g; ++c) row[c] = cvt(0.5 * (A[(size_t)g * n + c] + A[(size_t)c * n + g]));
+      row[g] = cvt(0.5 * A[(size_t)g * n + g]);
+    }
+  }
+  return out;
+}
+
 // Pack per-subdomain rectangular float64 blocks (rows x cols, row-major on
 // the host) with rows padded to 16 bytes of the storage type (eb bytes per
 // element) and blocks aligned to 32 elements.
@@ -318,6 +346,45 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     h->allocations.push_back(pB);
     h->d_tcB = pB;
     h->use_tma = false;
+  } else if (!h->full_operators && h->nrhs_max == 1 && (prec == BDDC_PREC_FP32 || prec == BDDC_PREC_BF16) &&
+             sgemv_tma_supported(prec, std::max(dI.empty() ? 0 : *std::max_element(dI.begin(), dI.end()),
+                                                dG.empty() ? 0 : *std::max_element(dG.begin(), dG.end())))) {
+    // symmetric operators, one right-hand side: lower triangles, one work
+    // item per operator (largest first)
+    auto up_sym = [&](const std::vector<std::vector<double>>& ops, const std::vector<int>& dims,
+                      const std::vector<int32_t>& voff, void** arena, WorkItem** items, int* n_items, int* max_n,
+                      int64_t* bytes) -> cudaError_t {
+      std::vector<int64_t> off;
+      cudaError_t e;
+      if (prec == BDDC_PREC_FP32) {
+        auto a = pack_lower<float>(ops, dims, prec, off, cvt_f);
+        arena_bytes += a.size() * sizeof(float);
+        e = upload(h, reinterpret_cast<float**>(arena), a);
+      } else {
+        auto a = pack_lower<__nv_bfloat16>(ops, dims, prec, off, cvt_b);
+        arena_bytes += a.size() * sizeof(__nv_bfloat16);
+        e = upload(h, reinterpret_cast<__nv_bfloat16**>(arena), a);
+      }
+      if (e != cudaSuccess) return e;
+      std::vector<WorkItem> it;
+      *bytes = 0;
+      *max_n = 0;
+      for (size_t s = 0; s < dims.size(); ++s) {
+        if (dims[s] == 0) continue;
+        it.push_back(WorkItem{off[s], padded_ld(dims[s], elem_bytes(prec)), dims[s], 0, dims[s], voff[s], voff[s]});
+        *bytes += sym_packed_elems(prec, dims[s]) * elem_bytes(prec);
+        *max_n = std::max(*max_n, dims[s]);
+      }
+      std::stable_sort(it.begin(), it.end(), [](const WorkItem& a, const WorkItem& b) { return a.ncols > b.ncols; });
+      *n_items = (int)it.size();
+      return upload(h, items, it);
+    };
+    CUDA_TRY(up_sym(hs.AIIinv, dI, ioff, reinterpret_cast<void**>(&h->d_aii), &h->d_wsy_I, &h->n_wsy_I,
+                    &h->max_n_I, &opbytes_I));
+    CUDA_TRY(up_sym(hs.Kgg, dG, goff, reinterpret_cast<void**>(&h->d_kgg), &h->d_wsy_G, &h->n_wsy_G, &h->max_n_G,
+                    &opbytes_G));
+    h->use_sym = true;
+    h->use_tma = true;
   } else {
     CUDA_TRY(up_arena(hs.AIIinv, dI, offI, ldI, &h->d_aii));
     CUDA_TRY(up_arena(hs.Kgg, dG, offG, ldG, &h->d_kgg));
@@ -500,6 +567,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   in.interior_op_bytes = opbytes_I;
   in.interface_op_bytes = opbytes_G;
   in.tensor_cores = h->use_tc ? 1 : 0;
+  in.symmetric_operators = h->use_sym ? 1 : 0;
   in.n_interface_copies = h->nG_tot;
   in.coarse_factor_entries = h->c_nnz;
   in.coarse_update_total = h->c_update_total;
@@ -593,6 +661,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->phi_prec = (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
   h->use_tc = tc_enabled(O);
   h->g_blocks = O->coarse_blocks;
+  h->full_operators = O->full_operators != 0;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -1064,7 +1133,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
       if ((interior ? h->nI_tot : h->nG_tot) == 0) continue;
       float best = -1.0f;
       int best_kb = h->tune_stage_kb[fam], best_tc = h->tune_tile_class[fam];
-      for (int tc = 0; tc < 3; ++tc)
+      for (int tc = 0; tc < (h->use_sym ? 1 : 3); ++tc)
         for (int c : cand) {
           h->tune_stage_kb[fam] = c;
           h->tune_tile_class[fam] = tc;

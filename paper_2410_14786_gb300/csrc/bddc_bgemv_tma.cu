@@ -459,6 +459,292 @@ cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void
   return cudaErrorInvalidValue;
 }
 
+// ---- symmetric operators: packed lower triangle -------------------------------------
+//
+// A symmetric operator A (n x n) is stored as L', its lower triangle with
+// the diagonal halved, row g holding columns 0 .. g zero-padded to a multiple
+// of V (16 bytes), rows consecutive: y = A x = L' x + L'^T x. Each stored
+// entry a = L'[g, c] is read once and used twice, y[g] += a x[c] and
+// yT[c] += a x[g] (the halved diagonal counts once in each), so the operator
+// stream is about half of the full matrix.
+//
+// One block owns one operator at a time (operators dealt round-robin over
+// the blocks); the producer streams its rows in stages of whole rows, as in
+// k_bgemv_tma. Row g is computed by consumer warp g mod 8, all 32 lanes on
+// one row: lane l reads the 16-byte vectors l, l + 32, ... of every row, so
+// it owns the same columns in every row and keeps their transposed partial
+// sums in registers (kSymK vectors). When the operator's last row is done
+// the warps' partials are summed in warp order in shared memory and added to
+// the rows' own sums: the result does not depend on the grid, the stage size
+// or which block ran the operator.
+constexpr int kSymK = 4;   // at most 4 x 32 vectors per row: n <= 128 V
+constexpr int kSymSmemCap = 200 * 1024;
+
+template <int V>
+__host__ __device__ __forceinline__ int64_t tri_off(int g) {
+  const int64_t q = g / V, r = g % V;
+  return (int64_t)V * (V * q * (q + 1) / 2 + r * (q + 1));
+}
+// Rows [g0, g1) of one stage: as many whole rows as fit in stage_elems (at
+// least one); binary search (tri_off is increasing).
+template <int V>
+__device__ __forceinline__ int sym_stage_end(int g0, int n, int64_t stage_elems) {
+  const int64_t base = tri_off<V>(g0);
+  int lo = g0 + 1, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tri_off<V>(mid) - base <= stage_elems) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// Sums of 4 values over the 32 lanes: afterwards every lane of the 8-lane
+// group q = lane >> 3 holds the total of v[q] in v[0] (two halving
+// exchanges, then three full ones).
+template <typename Acc>
+__device__ __forceinline__ Acc warp_sum4(Acc (&v)[4], int lane) {
+  {
+    const bool upper = (lane & 16) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const Acc send = upper ? v[i] : v[i + 2];
+      const Acc keep = upper ? v[i + 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool upper = (lane & 8) != 0;
+    const Acc send = upper ? v[0] : v[1];
+    const Acc keep = upper ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
+    k_sgemv_tma(const WorkItem* __restrict__ items, int n_items, const T* __restrict__ arena,
+                const double* __restrict__ X, double* __restrict__ Y, const int32_t* __restrict__ yscatter,
+                int stage_bytes, int max_n, int32_t* __restrict__ err) {
+  using Acc = typename Op<T>::Acc;
+  constexpr int V = Op<T>::V;
+  using XL = XLayout<Acc, V, 1>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int npad = (max_n + V - 1) / V * V;
+  unsigned char* stages = smem;
+  Acc* xs = reinterpret_cast<Acc*>(smem + (size_t)kStages * stage_bytes);
+  double* xraw = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(xs) + XL::bytes(npad));
+  float* rowp = reinterpret_cast<float*>(xraw + npad);
+  float* red = rowp + npad;
+  uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)kConsumerWarps * npad);
+  uint64_t* empty = full + kStages;
+  __shared__ int abort_flag;
+  __shared__ int stage_end[kStages];   // last row + 1 of the stage in each slot (written by the producer)
+  const int64_t stage_elems = stage_bytes / (int)sizeof(T);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    int slot = 0;
+    uint32_t phase = 0;
+    bool pending[kStages];
+    uint32_t pend_parity[kStages];
+    for (int s = 0; s < kStages; ++s) pending[s] = false;
+    bool ok = true;
+    for (int u = blockIdx.x; u < n_items && ok; u += gridDim.x) {
+      const WorkItem w = items[u];
+      const int n = w.ncols;
+      for (int g0 = 0, g1; g0 < n; g0 = g1) {
+        g1 = sym_stage_end<V>(g0, n, stage_elems);
+        if (!mbar_wait(&empty[slot], phase ^ 1u) || *(volatile int*)&abort_flag) {
+          atomicExch(err, BDDC_ERR_TIMEOUT);
+          abort_flag = 1;
+          ok = false;
+          break;
+        }
+        const uint32_t bytes = (uint32_t)((tri_off<V>(g1) - tri_off<V>(g0)) * (int64_t)sizeof(T));
+        stage_end[slot] = g1;   // published by the arrive below (release), read after the wait (acquire)
+        mbar_expect_tx(&full[slot], bytes);
+        bulk_load(stages + (size_t)slot * stage_bytes, arena + w.moff + tri_off<V>(g0), bytes, &full[slot]);
+        pending[slot] = true;
+        pend_parity[slot] = phase;
+        if (++slot == kStages) { slot = 0; phase ^= 1u; }
+      }
+    }
+    for (int s = 0; s < kStages; ++s)
+      if (pending[s] && !mbar_wait(&full[s], pend_parity[s])) atomicExch(err, BDDC_ERR_TIMEOUT);
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  constexpr int kCT = kConsumerWarps * 32;
+  const int tid = threadIdx.x;
+  int slot = 0;
+  uint32_t phase = 0;
+  bool aborted = false;
+  auto prefetch_operand = [&](int uu) {
+    const WorkItem wn = items[uu];
+    const int np = (wn.ncols + V - 1) / V * V;
+    for (int i = tid; i < np; i += kCT) {
+      if (i < wn.ncols)
+        cp_async8(xraw + i, X + wn.xoff + i);
+      else
+        xraw[i] = 0.0;
+    }
+    cp_async_commit();
+  };
+  if (blockIdx.x < n_items) prefetch_operand(blockIdx.x);
+  for (int u = blockIdx.x; u < n_items; u += gridDim.x) {
+    const WorkItem w = items[u];
+    const int n = w.ncols;
+    const int np = (n + V - 1) / V * V;
+    cp_async_wait_all();
+    consumer_sync();                          // operand landed; xs, rowp, red free
+    for (int i = tid; i < np; i += kCT) xs[XL::index(i, 0)] = (Acc)xraw[i];
+    consumer_sync();                          // xs complete; xraw free
+    if (u + (int)gridDim.x < n_items) prefetch_operand(u + gridDim.x);
+    Acc accT[K][V];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) accT[k][v] = Acc(0);
+    for (int g0 = 0, g1; g0 < n; g0 = g1) {
+      if (!aborted && (*(volatile int*)&abort_flag || !mbar_wait(&full[slot], phase))) {
+        if (lane == 0) atomicExch(err, BDDC_ERR_TIMEOUT);
+        abort_flag = 1;
+        aborted = true;
+      }
+      g1 = aborted ? sym_stage_end<V>(g0, n, stage_elems) : stage_end[slot];
+      if (!aborted) {
+        const T* tile = reinterpret_cast<const T*>(stages + (size_t)slot * stage_bytes);
+        const int64_t base = tri_off<V>(g0);
+        // rows g = warp (mod 8) of this stage, four at a time (one reduction)
+        for (int gb = g0 + ((warp - g0 % kConsumerWarps + kConsumerWarps) % kConsumerWarps); gb < g1;
+             gb += 4 * kConsumerWarps) {
+          Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int g = gb + q * kConsumerWarps;
+            if (g < g1) {
+              const T* row = tile + (tri_off<V>(g) - base);
+              const int nvec = g / V + 1;
+              const Acc xg = xs[XL::index(g, 0)];
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const int vi = k * 32 + lane;
+                if (vi < nvec) {
+                  Acc a[V];
+                  Op<T>::load(row + (size_t)vi * V, a);
+                  const Acc* xb = xs + vi * XL::XB;
+#pragma unroll
+                  for (int uu = 0; uu < XL::U; ++uu) {
+                    Acc xq[XL::Q];
+                    load16(xb + uu * XL::Q, xq);
+#pragma unroll
+                    for (int jj = 0; jj < XL::Q; ++jj) acc[q] = fma(a[uu * XL::Q + jj], xq[jj], acc[q]);
+                  }
+#pragma unroll
+                  for (int v = 0; v < V; ++v) accT[k][v] = fma(a[v], xg, accT[k][v]);
+                }
+              }
+            }
+          }
+          const Acc tot = warp_sum4(acc, lane);
+          const int g = gb + (lane >> 3) * kConsumerWarps;
+          if ((lane & 7) == 0 && g < g1) rowp[g] = (float)tot;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == kStages) { slot = 0; phase ^= 1u; }
+    }
+    // the warps' transposed partials, summed in warp order, plus the row sums
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = (k * 32 + lane) * V + v;
+        if (c < n) red[(size_t)warp * npad + c] = (float)accT[k][v];
+      }
+    consumer_sync();
+    if (!aborted)
+      for (int c = tid; c < n; c += kCT) {
+        float y = rowp[c];
+#pragma unroll
+        for (int ww = 0; ww < kConsumerWarps; ++ww) y += red[(size_t)ww * npad + c];
+        const int64_t jy = (int64_t)w.yoff + c;
+        Y[yscatter ? (int64_t)yscatter[jy] : jy] = (double)y;
+      }
+  }
+  cp_async_wait_all();
+}
+
+template <typename T>
+size_t sym_smem(int stage_bytes, int max_n) {
+  constexpr int V = Op<T>::V;
+  const int npad = (max_n + V - 1) / V * V;
+  return (size_t)kStages * stage_bytes + XLayout<typename Op<T>::Acc, V, 1>::bytes(npad) + (size_t)npad * 8 +
+         (size_t)npad * 4 * (1 + kConsumerWarps) + 2 * kStages * sizeof(uint64_t);
+}
+
+template <typename T, int K>
+cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* arena, const double* X, double* Y,
+                    const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb, int max_per_sm) {
+  constexpr int V = Op<T>::V;
+  // a stage holds at least one whole row (the longest: max_n padded), and
+  // the block's shared memory stays within kSymSmemCap
+  const int64_t row = (int64_t)((max_n + V - 1) / V * V) * (int64_t)sizeof(T);
+  const int64_t row128 = (row + 127) / 128 * 128;
+  const int64_t room = ((int64_t)kSymSmemCap - (int64_t)sym_smem<T>(0, max_n)) / kStages / 128 * 128;
+  const int64_t want = ((int64_t)stage_kb * 1024 + 127) / 128 * 128;
+  const int stage_bytes = (int)std::max<int64_t>(row128, std::min<int64_t>(want, room));
+  const size_t smem = sym_smem<T>(stage_bytes, max_n);
+  if (smem > (size_t)kSymSmemCap) return cudaErrorInvalidValue;
+  auto kern = k_sgemv_tma<T, K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (!g_num_sms) {
+    int dev;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, per_sm);
+  if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
+  const int grid = std::max(1, std::min(n_items, g_num_sms * per_sm));
+  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, max_n, err);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_sym(const WorkItem* items, int n_items, int max_n, const void* arena, const double* X,
+                         double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb,
+                         int max_per_sm) {
+  constexpr int V = Op<T>::V;
+  const T* A = static_cast<const T*>(arena);
+  if (max_n <= 32 * V)
+    return run_sym<T, 1>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+  if (max_n <= 64 * V)
+    return run_sym<T, 2>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+  if (max_n <= kSymK * 32 * V)
+    return run_sym<T, kSymK>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 bool bgemv_tma_supported(int precision, int max_lda) {
@@ -468,6 +754,34 @@ bool bgemv_tma_supported(int precision, int max_lda) {
                                                   : x_bytes<__nv_bfloat16, 1>(max_lda);
   const size_t row = ((size_t)max_lda * eb + 127) / 128 * 128;
   return kStages * row + xb + 64 <= 200 * 1024;
+}
+
+int64_t sym_packed_elems(int precision, int n) {
+  return precision == BDDC_PREC_FP32 ? tri_off<4>(n) : tri_off<8>(n);
+}
+
+bool sgemv_tma_supported(int precision, int max_n) {
+  if (precision != BDDC_PREC_FP32 && precision != BDDC_PREC_BF16) return false;
+  const int V = precision == BDDC_PREC_FP32 ? 4 : 8;
+  if (max_n > kSymK * 32 * V) return false;
+  // the smallest stage: one whole row
+  const size_t row = ((size_t)((max_n + V - 1) / V * V) * (precision == BDDC_PREC_FP32 ? 4 : 2) + 127) / 128 * 128;
+  const size_t smem = precision == BDDC_PREC_FP32 ? sym_smem<float>((int)row, max_n)
+                                                  : sym_smem<__nv_bfloat16>((int)row, max_n);
+  return smem <= (size_t)kSymSmemCap;
+}
+
+cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
+                             const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
+                             int stage_kb, int max_per_sm) {
+  if (n_items == 0) return cudaSuccess;
+  if (stage_kb < 1 || stage_kb > 48) return cudaErrorInvalidValue;
+  if (precision == BDDC_PREC_FP32)
+    return dispatch_sym<float>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+  if (precision == BDDC_PREC_BF16)
+    return dispatch_sym<__nv_bfloat16>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb,
+                                       max_per_sm);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bgemv_tma(int precision, const WorkItem* items, int n_items, int max_lda, const void* arena,

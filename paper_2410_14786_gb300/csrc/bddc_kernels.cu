@@ -451,6 +451,14 @@ cudaError_t bgemv(int precision, const WorkItem* items, int n_items, int max_lda
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
                      cudaStream_t st, int max_per_sm = 0) {
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
+  if (h->use_sym) {
+    if (nrhs != 1) return cudaErrorInvalidValue;   // nrhs_max is 1 on this path
+    h->launches += (interior ? h->n_wsy_I : h->n_wsy_G) > 0;
+    return interior ? launch_sgemv_tma(h->precision, h->d_wsy_I, h->n_wsy_I, h->max_n_I, h->d_aii, X, Y, yscatter,
+                                       h->d_err, st, h->tune_stage_kb[0], max_per_sm)
+                    : launch_sgemv_tma(h->precision, h->d_wsy_G, h->n_wsy_G, h->max_n_G, h->d_kgg, X, Y, yscatter,
+                                       h->d_err, st, h->tune_stage_kb[1], max_per_sm);
+  }
   h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)
     return interior ? launch_bgemv_tma(h->precision, h->d_wtx_I[h->tune_tile_class[0]],

@@ -254,6 +254,12 @@ struct bddc_handle_s {
   bddc::WorkItem* d_wtx_I[3] = {nullptr, nullptr, nullptr}; int n_wtx_I[3] = {0, 0, 0};
   bddc::WorkItem* d_wtx_G[3] = {nullptr, nullptr, nullptr}; int n_wtx_G[3] = {0, 0, 0};
   bool use_tma = false;
+  // symmetric operators as packed lower triangles (one work item per operator)
+  bool use_sym = false;
+  bool full_operators = false;        // option: keep them in full
+  bddc::WorkItem* d_wsy_I = nullptr; int n_wsy_I = 0;
+  bddc::WorkItem* d_wsy_G = nullptr; int n_wsy_G = 0;
+  int max_n_I = 0, max_n_G = 0;
   // tensor-core path: tiled arenas (d_aii / d_kgg then hold the tiled layout)
   bool use_tc = false;
   bddc::TcUnit* d_tcu_I = nullptr; int n_tcu_I = 0;

@@ -20,6 +20,16 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
 // copies through shared memory (bddc_bgemv_tma.cu). err receives
 // BDDC_ERR_TIMEOUT if a bounded wait runs out.
 bool bgemv_tma_supported(int precision, int max_lda);
+// Symmetric operators as their packed lower triangle (diagonal halved, rows
+// padded to 16 bytes): elements of one n x n operator, whether the streamed
+// symmetric GEMV supports the precision (FP32, BF16) and size, and
+// Y = Op X for one right-hand side (one work item per operator: moff,
+// ncols = n, xoff, yoff).
+int64_t sym_packed_elems(int precision, int n);
+bool sgemv_tma_supported(int precision, int max_n);
+cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
+                             const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
+                             int stage_kb, int max_per_sm = 0);
 // stage_kb: target bytes of one shared-memory stage, in KB (1..64; 12 by default,
 // the autotuner may choose another per operator family); max_per_sm > 0 caps
 // the blocks per SM (to leave room for a concurrent kernel).

@@ -194,13 +194,17 @@ def test_tensor_core_option_rejects_invalid(L, precision, tc):
     assert rc == _lib.ERR_INVALID_ARG
 
 
-def test_coarse_blocks_option_validated(L):
+def test_coarse_blocks_and_full_operators_options_validated(L):
     from paper_2410_14786_gb300 import _lib
     prob, opts, keep = _structs(synth.config(1))
     info = _lib.Info()
     opts.coarse_blocks = -1
     assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == _lib.ERR_INVALID_ARG
     opts.coarse_blocks = 4
+    assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == 0
+    opts.full_operators = 2
+    assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == _lib.ERR_INVALID_ARG
+    opts.full_operators = 1
     assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == 0
 
 
