@@ -38,7 +38,8 @@ RTOL = 1e-8
 # DRAM bytes (read + write) of the three operator passes of one apply, from
 # one ncu capture (--set full) of the streamed GEMV on this workload in the
 # bf16 form; no figure for other workloads or kernels (traffic is then null).
-MEASURED_TRAFFIC = {(WORKLOAD, "bf16", "k_bgemv_tma"): 1.2897e9}
+MEASURED_TRAFFIC = {(WORKLOAD, "bf16", "k_bgemv_tma"): 1.2897e9,   # full operators (full_operators=True)
+                    (WORKLOAD, "bf16", "k_sgemv_tma"): 6.6234e8}   # lower triangles (default)
 SAMPLE_NE, SAMPLE_NSUB, SAMPLE_SCALE = 32, 4, 27
 
 
