@@ -36,8 +36,8 @@ METRIC = "BDDC-PCG time to rtol 1e-8 & M^-1 applies/s, mixed vs FP64, 1 GB300"
 WORKLOAD = "3d_q1_96cubed_12cubed_subdomains_lognormal_sigma_1rhs"
 RTOL = 1e-8
 # DRAM bytes (read + write) of the three operator passes of one apply, from
-# one ncu capture (--set full) of the streamed GEMV on this workload in the
-# bf16 form; no figure for other workloads or kernels (traffic is then null).
+# ncu captures of the operator kernel on this workload in the bf16 form; no
+# figure for other workloads or kernels (traffic is then null).
 MEASURED_TRAFFIC = {(WORKLOAD, "bf16", "k_bgemv_tma"): 1.2897e9,   # full operators (full_operators=True)
                     (WORKLOAD, "bf16", "k_sgemv_tma"): 6.6234e8}   # lower triangles (default)
 SAMPLE_NE, SAMPLE_NSUB, SAMPLE_SCALE = 32, 4, 27
@@ -109,6 +109,24 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The largest x over the ranks of the process group (x itself when there
+    is no group or one rank): step times are those of the slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, seconds_per_step: float) -> float:
+    """Solves per second of the whole job: each of the ws replicas solves one
+    problem per step; seconds_per_step is the slowest replica's."""
+    return ws / seconds_per_step
 
 
 def oracle_solve_time(reps: int = 1):
@@ -216,11 +234,7 @@ def run_gb300(args):
         e1.record(stream)
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = e0.elapsed_time(e1) / args.steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         launches = g.info()["kernel_launches"] - launches0
         tr = float(((b - g64.matvec(x)).norm() / b.norm()).item())
         forms[prec].update({"ms_per_solve": ms, "iters": iters[-1], "true_relres": tr,
@@ -281,11 +295,7 @@ def run_gb300(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         g.pcg_solve_host(bn, rtol=RTOL, out=xn)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config == 2:
@@ -297,7 +307,8 @@ def run_gb300(args):
 
     ms = head["ms_per_solve"]
     line = {
-        "metric": METRIC, "value": ws * 1e3 / ms, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": whole_job_rate(ws, ms * 1e-3), "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+" + headline if headline != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.config == 2 and nrhs == 1 else p.name, "elements": f"{p.ne}^{p.dim}",
@@ -305,7 +316,7 @@ def run_gb300(args):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(b.numel() * 8),
+        "e2e": {"value": whole_job_rate(ws, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(b.numel() * 8)},
         "gpu_launches": int(head["launches_per_solve"] * args.steps),
         "clocks": head.get("clocks"),
