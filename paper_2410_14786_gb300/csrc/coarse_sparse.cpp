@@ -147,6 +147,151 @@ void coarse_renumber(CoarseFactor& cf, std::vector<int32_t>& perm) {
   for (int64_t i = 0; i < cf.n; ++i) cf.order[i] = (int32_t)i;
 }
 
+// Gather form of both sweeps: phases 0 .. L-1 are the forward levels (height
+// lv), phases L .. 2L-1 the backward levels (height 2L-1-phase). The
+// coefficients and indices of the units of a phase are stored longest unit
+// first; for each launch shape the units are assigned to warps longest first,
+// each to the warp with the least work so far, and their descriptors stored
+// warp by warp.
+
+void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const int* warps_per_block,
+                   GatherLayout& g) {
+  const int L = cf.n_levels;
+  const int nn = (int)cf.nodes.size();
+  const int32_t n = (int32_t)cf.n;
+  std::vector<int32_t> pos(n), first(nn);
+  for (int32_t i = 0; i < n; ++i) pos[cf.order[i]] = i;
+  for (int t = 0; t < nn; ++t) first[t] = cf.nodes[t].last - cf.nodes[t].p + 1;
+  // kind 0: row i of node a (forward); kind 1: receiving position a with
+  // contributions [cb, ce) of rlist; kind 2: row i of node a (backward)
+  struct GU {
+    int32_t kind, a, i, len, cb, ce;
+  };
+  std::vector<int8_t> has(n, 0);   // r' at this position updated by an earlier level
+  auto xf = [&](int32_t q) { return has[q] ? q : n + cf.order[q]; };
+  std::vector<std::vector<int32_t>> recv(n);
+  std::vector<int32_t> touched, rlist, ord;
+  std::vector<GU> us;
+  std::vector<CGUnit> desc;
+  std::vector<double>& gC = g.C;
+  std::vector<int32_t>& gI = g.I;
+  gC.clear();
+  gI.clear();
+  g.units.assign(nshapes, {});
+  g.wo.assign(nshapes, {});
+  for (int sh = 0; sh < nshapes; ++sh)
+    g.wo[sh].assign((size_t)2 * L * (blocks[sh] * warps_per_block[sh] + 1), 0);
+  int64_t total = 0;
+  for (const CoarseNode& T : cf.nodes) total += 2 * (int64_t)T.p * (T.p + T.u);
+  gC.reserve((size_t)total);
+  gI.reserve((size_t)total);
+  std::vector<std::vector<int32_t>> per;
+  for (int ph = 0; ph < 2 * L; ++ph) {
+    const bool fwd = ph < L;
+    const int lv = fwd ? ph : 2 * L - 1 - ph;
+    us.clear();
+    rlist.clear();
+    touched.clear();
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      if (T.height != lv || T.p == 0) continue;
+      for (int i = 0; i < T.p; ++i) us.push_back(GU{fwd ? 0 : 2, t, i, fwd ? i + 1 : T.p - i + T.u, 0, 0});
+      if (!fwd) continue;
+      for (int b = 0; b < T.u; ++b) {
+        const int32_t w = pos[T.upd[b]];
+        if (recv[w].empty()) touched.push_back(w);
+        recv[w].push_back(t);
+        recv[w].push_back(b);
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int32_t w : touched) {
+      const int32_t cb = (int32_t)rlist.size();
+      int32_t len = 0;
+      for (size_t q = 0; q < recv[w].size(); q += 2) {
+        rlist.push_back(recv[w][q]);
+        rlist.push_back(recv[w][q + 1]);
+        len += cf.nodes[recv[w][q]].p;
+      }
+      us.push_back(GU{1, w, 0, len, cb, (int32_t)rlist.size()});
+      recv[w].clear();
+    }
+    // coefficients and indices of every unit, longest unit first
+    ord.resize(us.size());
+    for (size_t k = 0; k < us.size(); ++k) ord[k] = (int32_t)k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return us[x].len > us[y].len; });
+    desc.resize(us.size());
+    for (int32_t k : ord) {
+      const GU& x = us[k];
+      CGUnit d{(int64_t)gC.size(), x.len, 0, -1, 0};
+      if (x.kind == 0) {
+        const CoarseNode& T = cf.nodes[x.a];
+        const int32_t pos0 = first[x.a];
+        for (int j = 0; j <= x.i; ++j) {
+          gC.push_back(T.Fm[(size_t)x.i * T.p + j]);
+          gI.push_back(xf(pos0 + j));
+        }
+        d.dst = pos0 + x.i;
+      } else if (x.kind == 1) {
+        for (int32_t q = x.cb; q < x.ce; q += 2) {
+          const CoarseNode& T = cf.nodes[rlist[q]];
+          const int32_t pos0 = first[rlist[q]], b = rlist[q + 1];
+          for (int j = 0; j < T.p; ++j) {
+            gC.push_back(T.Fm[(size_t)(T.p + b) * T.p + j]);
+            gI.push_back(xf(pos0 + j));
+          }
+        }
+        d.dst = x.a;
+        d.aux = xf(x.a);
+      } else {
+        const CoarseNode& T = cf.nodes[x.a];
+        const int32_t pos0 = first[x.a];
+        const size_t f = (size_t)T.p + T.u;
+        for (int j = x.i; j < T.p; ++j) {
+          gC.push_back(T.Bm[(size_t)x.i * f + j]);
+          gI.push_back(pos0 + j);
+        }
+        for (int b = 0; b < T.u; ++b) {
+          gC.push_back(T.Bm[(size_t)x.i * f + T.p + b]);
+          gI.push_back(n + pos[T.upd[b]]);
+        }
+        d.dst = pos0 + x.i;
+        d.aux = cf.order[pos0 + x.i];
+      }
+      desc[k] = d;
+    }
+    // per launch shape: longest first to the least-loaded warp (cost: batches
+    // of kGatherBatch, and a quarter batch per unit for its reduction and store);
+    // the h-th least-loaded warp is warp h / blocks of block h % blocks, so
+    // the work of a small level spreads over all SMs (their FP64 pipes)
+    for (int sh = 0; sh < nshapes; ++sh) {
+      const int nb = blocks[sh], wpb = warps_per_block[sh], nw = nb * wpb;
+      per.assign(nw, {});
+      std::vector<std::pair<int64_t, int32_t>> heap;
+      heap.reserve(nw);
+      for (int w = 0; w < nw; ++w) heap.emplace_back(0, w);
+      auto gt = [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) { return x > y; };
+      for (int32_t k : ord) {
+        std::pop_heap(heap.begin(), heap.end(), gt);
+        auto& top = heap.back();
+        per[top.second].push_back(k);
+        top.first += 4 * ((us[k].len + kGatherBatch - 1) / kGatherBatch) + 1;
+        std::push_heap(heap.begin(), heap.end(), gt);
+      }
+      std::vector<CGUnit>& gu = g.units[sh];
+      int32_t* wrow = &g.wo[sh][(size_t)ph * (nw + 1)];
+      for (int w = 0; w < nw; ++w) {
+        wrow[w] = (int32_t)gu.size();
+        for (int32_t k : per[(w % wpb) * nb + w / wpb]) gu.push_back(desc[k]);
+      }
+      wrow[nw] = (int32_t)gu.size();
+    }
+    if (fwd)
+      for (const GU& x : us)
+        if (x.kind == 1) has[x.a] = 1;
+  }
+}
+
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
                   const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {

@@ -38,7 +38,8 @@ struct CGUnit {
   int64_t off;
   int32_t len, dst, aux, pad;
 };
-// The gather form of both sweeps (coarse_solve.cu): C and I hold each
+// The gather form of both sweeps (built on the host in coarse_sparse.cpp,
+// applied by coarse_solve.cu): C and I hold each
 // unit's coefficients and operand indices contiguously; for each launch shape
 // s (blocks[s] x warps_per_block[s] warps, warp w of block b being warp
 // b * warps_per_block[s] + w) the descriptors of warp w in phase ph are
@@ -46,6 +47,7 @@ struct CGUnit {
 // in that order. Phases 0 .. L-1 are the forward levels (height = phase),
 // phases L .. 2L-1 the backward levels (height = 2L-1-phase).
 struct CoarseFactor;
+constexpr int kGatherBatch = 256;   // coefficients a warp reads per step of a unit (cost unit of the assignment)
 struct GatherLayout {
   std::vector<double> C;
   std::vector<int32_t> I;
