@@ -470,10 +470,12 @@ cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void
 //
 // One block owns one operator at a time (operators dealt round-robin over
 // the blocks); the producer streams its rows in stages of whole rows, as in
-// k_bgemv_tma. Row g is computed by consumer warp g mod 8, all 32 lanes on
-// one row: lane l reads the 16-byte vectors l, l + 32, ... of every row, so
-// it owns the same columns in every row and keeps their transposed partial
-// sums in registers (kSymK vectors). When the operator's last row is done
+// k_bgemv_tma, and publishes each stage's last row in shared memory (found
+// by binary search over the row offsets). Row g is computed by consumer warp
+// g mod 8, all 32 lanes on one row, four rows per reduction: lane l reads the
+// 16-byte vectors l, l + 32, ... of every row, so it owns the same columns
+// in every row and keeps their transposed partial sums in registers (up to
+// kSymK vectors). When the operator's last row is done
 // the warps' partials are summed in warp order in shared memory and added to
 // the rows' own sums: the result does not depend on the grid, the stage size
 // or which block ran the operator.
