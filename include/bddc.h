@@ -36,7 +36,9 @@
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream). Calls on one handle are not re-entrant: do not run two
- * calls on the same handle concurrently, on any streams.
+ * calls on the same handle concurrently, on any streams or host threads.
+ * Devices: a call makes the handle's device current while it runs and
+ * restores the caller's current device before it returns.
  *
  * Errors: every int-returning call returns BDDC_OK (0) on success, a
  * negative BDDC_ERR_* code on failure, or BDDC_NOT_CONVERGED (positive) from
@@ -132,6 +134,8 @@ typedef struct {
                               nrhs_max = 1, A_II^-1 and K_GG are stored as their lower
                               triangles (about half the bytes) and applied by the
                               symmetric streamed GEMV; elsewhere in full */
+    int32_t history;       /* PCG iterations whose scalars (||r_k||, alpha_k, beta_k) the
+                              handle keeps for bddc_pcg_history, 0..100000; 0 = none */
 } bddc_options_t;
 
 typedef struct {
@@ -167,7 +171,11 @@ typedef struct {
     int32_t symmetric_operators;        /* 1 if A_II^-1 and K_GG are stored as lower triangles */
 } bddc_info_t;
 
-/* Build the preconditioner (all factorisations in float64 on the host,
+/* Build the preconditioner (Sec. 2: the subdomain matrices A_i of A = sum
+ * R_i^T A_i R_i, the weights W_i, the corner / edge / face constraints C_i,
+ * the coarse basis Phi_i from Eq. saddlepoint, A_c = sum R_ci^T Phi_i^T A_i
+ * Phi_i R_ci and its factorisation, and the operators of the local solves
+ * of Eqs. compzi and inner; all factorisations in float64 on the host,
  * operators uploaded once to the device). Copies what it needs from
  * `problem`; the caller keeps ownership of every input. On success *out
  * holds a new handle (free it with bddc_destroy); on failure *out is NULL.
@@ -188,22 +196,38 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * memory allocated on their behalf, for example a host program whose own
  * allocator owns the whole device and forbids cudaMalloc / cudaFree from
  * libraries, or a program that fixes all device memory at start-up. The call
- * itself never calls cudaMalloc, cudaFree or any allocating routine.
+ * itself never calls cudaMalloc, cudaFree or any allocating routine. What
+ * moves to the array are the vectors one apply writes and reads (compact
+ * interior, interface-copy, constraint and coarse vectors); the handle's
+ * other device buffers, allocated once by bddc_setup, are still used: the
+ * packed tensor-core operand, the coarse solve's barrier counter and the
+ * device error flag.
  * Limit: the temporaries of one apply, (3 n_interior + 3 n_interface_copies
  * + 2 sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
  * the dense coarse solve and 2 n_c for the sparse one
  * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
- * larger problems get BDDC_ERR_INVALID_ARG. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, with that device current); make
- * that first call before any stream capture. Every call on every handle of
+ * larger problems get BDDC_ERR_INVALID_ARG. The driver places the array in
+ * the device's memory when it loads the library's device code on that device:
+ * under CUDA's default lazy module loading that happens in the first call on
+ * the device (8 MiB less free memory from then on), with
+ * CUDA_MODULE_LOADING=EAGER when the context is created. The first call on a
+ * device also looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and keeps
+ * it for the life of the process; make that first call before any stream
+ * capture, and do not use this entry point after cudaDeviceReset or any
+ * other teardown of the device's primary context. Every call on every handle of
  * a device shares the one array, and no part of it needs to start at zero
  * (each call writes every element it reads before reading it): calls that
- * overlap on the GPU, on any streams, race and give wrong results. */
+ * overlap on the GPU, on any streams, race and give wrong results. While the
+ * call runs it points the handle's workspace at the array, so, as for every
+ * call on a handle, no other host thread may use the same handle meanwhile. */
 int bddc_apply_static_scratch(bddc_handle_t h, const double *r, double *z, int32_t nrhs,
                               void *stream);
 
-/* y = A x (the global stiffness matrix on the free nodes; Dirichlet entries
- * of y are written 0). Device vectors; asynchronous on `stream`. */
+/* y = A x (Sec. 2: the global stiffness matrix A = sum R_i^T A_i R_i of
+ * the Q1 discretisation on the free nodes, the matrix of the CG iteration of
+ * Sec. 3; Dirichlet entries of y are written 0). Device vectors;
+ * asynchronous on `stream`. */
 int bddc_matvec(bddc_handle_t h, const double *x, double *y, int32_t nrhs, void *stream);
 
 /* b = M f restricted to the free nodes: the load vector of the nodal values
@@ -253,8 +277,10 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t *in);
 int bddc_elem_grad(bddc_handle_t h, const double *u, const double *lambda, double *g, int32_t nrhs,
                    void *stream);
 
-/* Solve A x = b by PCG with M^-1 from the start x0 = P_I b (the interior
- * correction of b), independently per column, until ||r_k||_2 <= rtol *
+/* Solve A x = b by the BDDC-preconditioned conjugate gradient method of
+ * Sec. 3 (preconditioner M^-1 of Sec. 2, applied as in bddc_apply) from the
+ * start x0 = P_I b (the interior correction of Eq. inner applied to b),
+ * independently per column, until ||r_k||_2 <= rtol *
  * ||b||_2 on the updated residual. b, x: device vectors. iters[nrhs] and
  * relres[nrhs] are HOST arrays (may be NULL) receiving the iteration count
  * and ||r||/||b|| of each column. Synchronises `stream`. Returns OK,
@@ -269,6 +295,20 @@ int bddc_pcg_solve(bddc_handle_t h, const double *b, double *x, int32_t nrhs,
 int bddc_pcg_solve_host(bddc_handle_t h, const double *b_host, double *x_host,
                         int32_t nrhs, double rtol, int32_t maxit, int32_t *iters,
                         double *relres, void *stream);
+
+/* Scalars of every iteration of the most recent bddc_pcg_solve(_host) on
+ * this handle (Sec. 3: the BDDC-preconditioned CG iteration; per column k:
+ * alpha_k = rho_k / p_k^T A p_k, x_k+1 = x_k + alpha_k p_k, r_k+1 = r_k -
+ * alpha_k A p_k, beta_k = r_k+1^T z_k+1 / rho_k, or r_k+1^T (z_k+1 - z_k) /
+ * rho_k in the flexible forms). rnorm, alpha, beta: HOST arrays (each may
+ * be NULL) of (n_iter + 1) * nrhs doubles, entry (k, column j) at k * nrhs
+ * + j: rnorm = ||r_k||_2 (r_0 = b - A x_0) for k = 0 .. iters_j; alpha =
+ * alpha_k for k < iters_j; beta = the beta computed after iteration k + 1
+ * (the one that forms p_k+1) for k < iters_j - 1; NaN elsewhere and for
+ * iterations beyond bddc_options_t.history. n_iter must be in [0,
+ * history] and nrhs in [1, nrhs_max]. Synchronises the device. */
+int bddc_pcg_history(bddc_handle_t h, int32_t nrhs, int32_t n_iter, double *rnorm, double *alpha,
+                     double *beta);
 
 /* Copy the coarse residual r_c and the coarse solution u_c = A_c^-1 r_c of
  * the most recent bddc_apply (n_c * nrhs doubles each, coarse dof major,
@@ -300,6 +340,23 @@ int bddc_profile_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs
  * INVALID_ARG. Same argument checks and errors as bddc_setup. */
 int bddc_setup_inspect(const bddc_problem_t *problem, const bddc_options_t *options,
                        int32_t numerics, bddc_info_t *info, double *Ac, int64_t Ac_capacity);
+
+/* Test hook for the bounded device waits (no counterpart in the paper).
+ * With enable = 1, every grid barrier of the sparse coarse solve waits for
+ * one arrival more than its grid makes, so the first barrier of every later
+ * coarse solve runs out after limit_cycles SM clock cycles (1 .. 4e9; about
+ * 2 cycles per ns): the block records BDDC_ERR_TIMEOUT in the handle's
+ * device flag and every block of that launch returns (no bulk copy or MMA is
+ * in flight in that kernel). The flag then stops PCG (bddc_pcg_solve returns
+ * BDDC_ERR_TIMEOUT) and shows in bddc_query().device_error until
+ * bddc_clear_device_error. enable = 0 restores the normal barrier and its
+ * 2 s limit. Needs the sparse coarse solve (INVALID_ARG otherwise). The
+ * handle's captured solve graphs are dropped and captured again. */
+int bddc_test_coarse_stall(bddc_handle_t h, int32_t enable, int64_t limit_cycles);
+
+/* Synchronise the handle's device and clear the device error flag that a
+ * bounded wait set (bddc_query().device_error). */
+int bddc_clear_device_error(bddc_handle_t h);
 
 /* Free the handle and all device memory it holds. NULL is allowed. */
 void bddc_destroy(bddc_handle_t h);

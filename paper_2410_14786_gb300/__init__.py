@@ -64,13 +64,15 @@ class BDDC:
     them without measuring again; coarse_blocks: blocks of the one-column
     sparse coarse solve (0 = one per SM); full_operators=True stores the
     symmetric local operators in full where they would otherwise be stored
-    as lower triangles (fp32 / bf16 on the CUDA cores with nrhs_max = 1).
+    as lower triangles (fp32 / bf16 on the CUDA cores with nrhs_max = 1);
+    history: PCG iterations whose scalars (||r_k||, alpha_k, beta_k) the
+    handle keeps for `pcg_history()` (0 = none).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
                  phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None, coarse_blocks=0,
-                 full_operators=False):
+                 full_operators=False, history=0):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -84,11 +86,12 @@ class BDDC:
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
                             COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
                             1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores], int(coarse_blocks),
-                            1 if full_operators else 0)
+                            1 if full_operators else 0, int(history))
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim
         self.precision = precision
+        self.history = int(history)
         self.tuned_from_cache = False
         if tune_cache is not None or autotune:
             self._tune(part, tune_cache, autotune)
@@ -199,15 +202,17 @@ class BDDC:
         _lib.check(self._L.bddc_coarse_vectors(self.handle, _dev_ptr(rc), _dev_ptr(uc), nrhs, _stream_ptr(stream)))
         return rc, uc
 
-    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=1000, stream=None) -> tuple:
-        """Solve A x = b; returns (x, SolveResult). Device tensors."""
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=1000, stream=None, allow_breakdown=False) -> tuple:
+        """Solve A x = b; returns (x, SolveResult). Device tensors. With
+        allow_breakdown=True a PCG breakdown in some column (status
+        ERR_BREAKDOWN) returns the per-column results instead of raising."""
         nrhs = self._nrhs(b)
         x = x if x is not None else self.empty(nrhs)
         iters = (C.c_int32 * nrhs)()
         rel = (C.c_double * nrhs)()
         st = self._L.bddc_pcg_solve(self.handle, _dev_ptr(b), _dev_ptr(x), nrhs, float(rtol), int(maxit),
                                     iters, rel, _stream_ptr(stream))
-        _lib.check(st, allow=(_lib.OK, _lib.NOT_CONVERGED))
+        _lib.check(st, allow=(_lib.OK, _lib.NOT_CONVERGED) + ((_lib.ERR_BREAKDOWN,) if allow_breakdown else ()))
         return x, SolveResult(np.array(iters[:]), np.array(rel[:]), st)
 
     def pcg_solve_host(self, b: np.ndarray, rtol=1e-8, maxit=1000, out: np.ndarray | None = None, stream=None):
@@ -221,6 +226,25 @@ class BDDC:
                                          float(rtol), int(maxit), iters, rel, _stream_ptr(stream))
         _lib.check(st, allow=(_lib.OK, _lib.NOT_CONVERGED))
         return x, SolveResult(np.array(iters[:]), np.array(rel[:]), st)
+
+    def pcg_history(self, nrhs=1, n_iter=None) -> dict:
+        """Per-iteration scalars of the most recent PCG solve: arrays of shape
+        (n_iter + 1, nrhs) named rnorm (||r_k||), alpha (alpha_k) and beta (the
+        beta computed after iteration k + 1); NaN where not recorded."""
+        n_iter = self.history if n_iter is None else int(n_iter)
+        out = {k: np.empty((n_iter + 1) * nrhs) for k in ("rnorm", "alpha", "beta")}
+        ptr = {k: v.ctypes.data_as(C.POINTER(C.c_double)) for k, v in out.items()}
+        _lib.check(self._L.bddc_pcg_history(self.handle, int(nrhs), n_iter, ptr["rnorm"], ptr["alpha"],
+                                            ptr["beta"]))
+        return {k: v.reshape(n_iter + 1, nrhs) for k, v in out.items()}
+
+    def test_coarse_stall(self, enable: bool, limit_cycles: int = 2_000_000):
+        """Test hook: make every grid barrier of the sparse coarse solve wait
+        for an arrival that never comes (bounded by limit_cycles), or restore it."""
+        _lib.check(self._L.bddc_test_coarse_stall(self.handle, 1 if enable else 0, int(limit_cycles)))
+
+    def clear_device_error(self):
+        _lib.check(self._L.bddc_clear_device_error(self.handle))
 
     def profile_apply(self, r, reps=5, stream=None):
         z = self.empty(self._nrhs(r))

@@ -31,6 +31,7 @@ EXPORTED = [
     "bddc_pcg_solve_host", "bddc_coarse_vectors", "bddc_query", "bddc_profile_apply",
     "bddc_destroy", "bddc_strerror", "bddc_last_error", "bddc_setup_inspect",
     "bddc_apply_static_scratch", "bddc_elem_grad", "bddc_autotune", "bddc_get_tuning", "bddc_set_tuning",
+    "bddc_pcg_history", "bddc_test_coarse_stall", "bddc_clear_device_error",
 ]
 
 
@@ -49,7 +50,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraints", C.c_uint32), ("nrhs_max", C.c_int32),
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
                 ("no_graph", C.c_int32), ("phi_fp64", C.c_int32),
-                ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32), ("full_operators", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32), ("full_operators", C.c_int32),
+                ("history", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -89,6 +91,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "bddc_pcg_solve": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
         "bddc_pcg_solve_host": (C.c_int, [vp, vp, vp, i32, dbl, i32, pi32, pdbl, vp]),
         "bddc_coarse_vectors": (C.c_int, [vp, vp, vp, i32, vp]),
+        "bddc_pcg_history": (C.c_int, [vp, i32, i32, pdbl, pdbl, pdbl]),
+        "bddc_test_coarse_stall": (C.c_int, [vp, i32, C.c_int64]),
+        "bddc_clear_device_error": (C.c_int, [vp]),
         "bddc_query": (C.c_int, [vp, C.POINTER(Info)]),
         "bddc_profile_apply": (C.c_int, [vp, vp, vp, i32, i32, pdbl, vp]),
         "bddc_setup_inspect": (C.c_int, [C.POINTER(Problem), C.POINTER(Options), i32, C.POINTER(Info), pdbl,

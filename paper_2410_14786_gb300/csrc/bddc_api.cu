@@ -536,6 +536,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(cudaMemset(h->d_iscal, 0, sizeof(int32_t) * (I_COUNT * R + kGlobalFlags)));
   CUDA_TRY(cudaMallocHost(&h->h_flags, sizeof(int32_t) * (I_COUNT * R + kGlobalFlags)));
   h->d_err = h->d_iscal + I_COUNT * R + 2;
+  if (h->hist_cap > 0) CUDA_TRY(dev_alloc(h, &h->d_hist, (size_t)3 * (h->hist_cap + 1) * R));
   // ---- info ------------------------------------------------------------------------
   bddc_info_t& in = h->info;
   in.n_nodes = hs.n_nodes;
@@ -579,15 +580,29 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   return BDDC_OK;
 }
 
+// Drop the captured PCG graphs (they hold launch arguments that changed).
+void drop_graphs(bddc_handle_t h) {
+  if (h->iter_graph) {
+    cudaGraphExecDestroy(h->iter_graph);
+    h->iter_graph = nullptr;
+  }
+  if (h->solve_graph) {
+    cudaGraphExecDestroy(h->solve_graph);
+    h->solve_graph = nullptr;
+  }
+}
+
 int check_handle(bddc_handle_t h, int nrhs) {
   if (!h) return fail(BDDC_ERR_INVALID_ARG, "null handle");
   if (nrhs < 1 || nrhs > h->nrhs_max)
     return fail(BDDC_ERR_INVALID_ARG, "nrhs " + std::to_string(nrhs) + " outside [1, nrhs_max=" +
                                           std::to_string(h->nrhs_max) + "]");
-  cudaError_t e = cudaSetDevice(h->device);
-  if (e != cudaSuccess) return fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
   return BDDC_OK;
 }
+
+#define ENTER_DEVICE(dev)                                                                   \
+  DeviceGuard device_guard_(dev);                                                           \
+  if (!device_guard_.ok) return fail(BDDC_ERR_CUDA, "could not make the handle's device current")
 
 }  // namespace
 
@@ -614,7 +629,7 @@ const char* bddc_last_error(void) { return g_last_error.c_str(); }
 
 void bddc_destroy(bddc_handle_t h) {
   if (!h) return;
-  cudaSetDevice(h->device);
+  DeviceGuard device_guard_(h->device);
   if (h->iter_graph) cudaGraphExecDestroy(h->iter_graph);
   if (h->solve_graph) cudaGraphExecDestroy(h->solve_graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -642,7 +657,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(BDDC_ERR_NO_DEVICE, "no CUDA device");
   if (O->device < 0 || O->device >= ndev) return fail(BDDC_ERR_INVALID_ARG, "device ordinal out of range");
-  CUDA_TRY(cudaSetDevice(O->device));
+  ENTER_DEVICE(O->device);
   cudaDeviceProp prop;
   CUDA_TRY(cudaGetDeviceProperties(&prop, O->device));
   if (prop.major != 10 || prop.minor != 3)
@@ -662,6 +677,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->use_tc = tc_enabled(O);
   h->g_blocks = O->coarse_blocks;
   h->full_operators = O->full_operators != 0;
+  h->hist_cap = O->history;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -734,7 +750,7 @@ int bddc_query(bddc_handle_t h, bddc_info_t* info) {
   if (!h || !info) return fail(BDDC_ERR_INVALID_ARG, "null argument");
   h->info.kernel_launches = h->launches;
   h->info.solve_graph = h->use_graph && !h->solve_graph_unsupported ? 1 : 0;
-  CUDA_TRY(cudaSetDevice(h->device));
+  ENTER_DEVICE(h->device);
   CUDA_TRY(cudaMemcpy(&h->info.device_error, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
   *info = h->info;
   return BDDC_OK;
@@ -743,6 +759,7 @@ int bddc_query(bddc_handle_t h, bddc_info_t* info) {
 int bddc_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!r || !z || r == z) return fail(BDDC_ERR_INVALID_ARG, "r and z must be distinct device pointers");
   CUDA_TRY(launch_apply(h, r, z, nrhs, static_cast<cudaStream_t>(stream)));
   return BDDC_OK;
@@ -751,6 +768,7 @@ int bddc_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs, void* 
 int bddc_matvec(bddc_handle_t h, const double* x, double* y, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!x || !y || x == y) return fail(BDDC_ERR_INVALID_ARG, "x and y must be distinct device pointers");
   CUDA_TRY(launch_spmv(h, x, y, nrhs, -1, 0.0, 0, static_cast<cudaStream_t>(stream)));
   return BDDC_OK;
@@ -759,6 +777,7 @@ int bddc_matvec(bddc_handle_t h, const double* x, double* y, int32_t nrhs, void*
 int bddc_rhs(bddc_handle_t h, const double* f, double* b, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!f || !b || f == b) return fail(BDDC_ERR_INVALID_ARG, "f and b must be distinct device pointers");
   CUDA_TRY(launch_rhs(h, f, b, nrhs, static_cast<cudaStream_t>(stream)));
   return BDDC_OK;
@@ -767,6 +786,7 @@ int bddc_rhs(bddc_handle_t h, const double* f, double* b, int32_t nrhs, void* st
 int bddc_elem_grad(bddc_handle_t h, const double* u, const double* lambda, double* g, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!u || !lambda || !g) return fail(BDDC_ERR_INVALID_ARG, "u, lambda and g must be device pointers");
   CUDA_TRY(launch_elem_grad(h, u, lambda, g, nrhs, static_cast<cudaStream_t>(stream)));
   return BDDC_OK;
@@ -775,6 +795,7 @@ int bddc_elem_grad(bddc_handle_t h, const double* u, const double* lambda, doubl
 int bddc_coarse_vectors(bddc_handle_t h, double* rc_out, double* uc_out, int32_t nrhs, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)h->n_c * nrhs * sizeof(double);
   if (bytes == 0) return BDDC_OK;
@@ -794,6 +815,7 @@ int bddc_profile_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs
                        void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!r || !z || !out_ms || reps < 1) return fail(BDDC_ERR_INVALID_ARG, "bad profile arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t ev[10];
@@ -980,6 +1002,9 @@ static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, doubl
   };
   auto finish = [&](int status) { return pcg_finish(h, nrhs, iters, relres, st, status); };
   int rc;
+  // iteration history: all NaN (0xff bytes) until the solve writes it
+  if (h->d_hist)
+    CUDA_TRY(cudaMemsetAsync(h->d_hist, 0xff, sizeof(double) * 3 * (h->hist_cap + 1) * R, st));
   int status = BDDC_OK;
   if (h->use_graph && maxit > 0 && !h->solve_graph_unsupported) {
     if ((rc = capture_solve(h, b, x, nrhs, rtol, maxit, flexible)) != BDDC_OK) {
@@ -1037,6 +1062,7 @@ int bddc_pcg_solve(bddc_handle_t h, const double* b, double* x, int32_t nrhs, do
                    int32_t* iters, double* relres, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!b || !x || b == x) return fail(BDDC_ERR_INVALID_ARG, "b and x must be distinct device pointers");
   if (!(rtol > 0.0) || maxit < 0) return fail(BDDC_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
   return pcg_core(h, b, x, nrhs, rtol, maxit, iters, relres, static_cast<cudaStream_t>(stream));
@@ -1046,6 +1072,7 @@ int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, i
                         int32_t maxit, int32_t* iters, double* relres, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   if (!b_host || !x_host) return fail(BDDC_ERR_INVALID_ARG, "null host vector");
   if (!(rtol > 0.0) || maxit < 0) return fail(BDDC_ERR_INVALID_ARG, "rtol must be > 0 and maxit >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1056,6 +1083,50 @@ int bddc_pcg_solve_host(bddc_handle_t h, const double* b_host, double* x_host, i
   CUDA_TRY(cudaMemcpyAsync(x_host, h->s_x, bytes, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   return status;
+}
+
+int bddc_pcg_history(bddc_handle_t h, int32_t nrhs, int32_t n_iter, double* rnorm, double* alpha, double* beta) {
+  int rc = check_handle(h, nrhs);
+  if (rc) return rc;
+  ENTER_DEVICE(h->device);
+  if (n_iter < 0 || n_iter > h->hist_cap)
+    return fail(BDDC_ERR_INVALID_ARG, "n_iter " + std::to_string(n_iter) + " outside [0, history=" +
+                                          std::to_string(h->hist_cap) + "]");
+  const int R = h->nrhs_max;
+  const size_t per = (size_t)(h->hist_cap + 1) * R;
+  std::vector<double> hv(h->d_hist ? 3 * per : 0);
+  if (h->d_hist) CUDA_TRY(cudaMemcpy(hv.data(), h->d_hist, hv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  double* out[3] = {rnorm, alpha, beta};
+  for (int slot = 0; slot < 3; ++slot) {
+    if (!out[slot]) continue;
+    for (int k = 0; k <= n_iter; ++k)
+      for (int j = 0; j < nrhs; ++j)
+        out[slot][(size_t)k * nrhs + j] = h->d_hist ? hv[slot * per + (size_t)k * R + j] : std::nan("");
+  }
+  return BDDC_OK;
+}
+
+int bddc_test_coarse_stall(bddc_handle_t h, int32_t enable, int64_t limit_cycles) {
+  if (!h) return fail(BDDC_ERR_INVALID_ARG, "null handle");
+  if (enable != 0 && enable != 1) return fail(BDDC_ERR_INVALID_ARG, "enable must be 0 or 1");
+  if (enable && (limit_cycles < 1 || limit_cycles > kBarrierWaitCycles))
+    return fail(BDDC_ERR_INVALID_ARG, "limit_cycles must be in [1, 4e9]");
+  if (!h->n_c || h->coarse_dense) return fail(BDDC_ERR_INVALID_ARG, "needs the sparse coarse solve");
+  ENTER_DEVICE(h->device);
+  CUDA_TRY(cudaDeviceSynchronize());   // no coarse launch in flight while the arguments change
+  h->cbar_extra = enable ? 1u : 0u;
+  h->cbar_cycles = enable ? (long long)limit_cycles : kBarrierWaitCycles;
+  drop_graphs(h);
+  return BDDC_OK;
+}
+
+int bddc_clear_device_error(bddc_handle_t h) {
+  if (!h) return fail(BDDC_ERR_INVALID_ARG, "null handle");
+  ENTER_DEVICE(h->device);
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int32_t)));
+  h->info.device_error = 0;
+  return BDDC_OK;
 }
 
 int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
@@ -1083,20 +1154,14 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
   h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
-  if (h->iter_graph) {   // captured graphs hold the old launch parameters
-    cudaGraphExecDestroy(h->iter_graph);
-    h->iter_graph = nullptr;
-  }
-  if (h->solve_graph) {
-    cudaGraphExecDestroy(h->solve_graph);
-    h->solve_graph = nullptr;
-  }
+  drop_graphs(h);   // captured graphs hold the old launch parameters
   return BDDC_OK;
 }
 
 int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* stream) {
   int rc = check_handle(h, nrhs);
   if (rc) return rc;
+  ENTER_DEVICE(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -381,7 +382,26 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(Blocking<NRB>::wide ?
   cp_async_wait_all();
 }
 
-int g_num_sms = 0;
+// SM count of the current device, cached per device (every thread that
+// fills an entry writes the same value).
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_num_sms[kMaxDevices];
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev >= kMaxDevices) {
+    int n = 1;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(n, 1);
+  }
+  int n = g_num_sms[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    n = std::max(n, 1);
+    g_num_sms[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 
 // Shared memory of one block: kStages stages, two operand buffers, barriers.
 template <typename T, int NRB>
@@ -423,18 +443,13 @@ cudaError_t run_tma(const WorkItem* items, int n_items, int max_lda, const T* ar
   auto kern = k_bgemv_tma<T, NRB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (!g_num_sms) {
-    int dev;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, per_sm);
   if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
   const int units = n_items * ((nrhs + NRB - 1) / NRB);
-  const int grid = std::max(1, std::min(units, g_num_sms * per_sm));
+  const int grid = std::max(1, std::min(units, num_sms() * per_sm));
   kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, nrhs, stage_bytes, max_lda, err);
   return cudaGetLastError();
 }
@@ -717,17 +732,12 @@ cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* aren
   auto kern = k_sgemv_tma<T, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (!g_num_sms) {
-    int dev;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem);
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, per_sm);
   if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
-  const int grid = std::max(1, std::min(n_items, g_num_sms * per_sm));
+  const int grid = std::max(1, std::min(n_items, num_sms() * per_sm));
   kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, max_n, err);
   return cudaGetLastError();
 }

@@ -99,10 +99,19 @@ struct PcgState {
   int32_t* iscal;        // [I_COUNT][nrhs_max] + global flags
   double* partials;      // [blocks][3][nrhs]
   unsigned int* counter; // blocks done (reset by the last block)
+  double* hist;          // [3][hist_cap + 1][nrhs_max]: ||r_k||, alpha_k, beta_k (null: not kept)
+  int hist_cap;
   int nrhs_max;
   double rtol;
   int flexible;
 };
+
+// Iteration history: slot 0 = ||r_k|| (k = 0 .. iterations), 1 = alpha_k
+// (k = 0 .. iterations - 1), 2 = beta_k, the beta computed after iteration
+// k + 1 (k = 0 .. iterations - 2); entries beyond hist_cap are not kept.
+__device__ __forceinline__ void hist_put(const PcgState& S, int slot, int it, int k, double v) {
+  if (S.hist && it >= 0 && it <= S.hist_cap) S.hist[((int64_t)slot * (S.hist_cap + 1) + it) * S.nrhs_max + k] = v;
+}
 
 // Per-column PCG scalar update from the totals t[0..2] of column k.
 __device__ void finalize_op(int op, int k, const double t[3], const PcgState& S, int* cnt, int* brk) {
@@ -122,6 +131,10 @@ __device__ void finalize_op(int op, int k, const double t[3], const PcgState& S,
     relres[k] = bn > 0 ? rn / bn : 0.0;
     active[k] = (bn > 0 && !(rn <= S.rtol * bn)) ? 1 : 0;
     iters[k] = 0; status[k] = 0; alpha[k] = 0; beta[k] = 0;
+    hist_put(S, 0, 0, k, rn);
+    if (!isfinite(t[0]) || !isfinite(t[1])) {   // a non-finite right-hand side or start
+      relres[k] = rn; active[k] = 0; status[k] = BDDC_ERR_BREAKDOWN; atomicAdd(brk, 1);
+    }
   } else if (op == FIN_RHO) {      // t0 = r.z
     rho[k] = t[0];
   } else if (op == FIN_ALPHA) {    // t0 = p.q
@@ -130,6 +143,7 @@ __device__ void finalize_op(int op, int k, const double t[3], const PcgState& S,
         active[k] = 0; status[k] = BDDC_ERR_BREAKDOWN; alpha[k] = 0; atomicAdd(brk, 1);
       } else {
         alpha[k] = rho[k] / t[0];
+        hist_put(S, 1, iters[k], k, alpha[k]);
       }
     } else {
       alpha[k] = 0;
@@ -140,6 +154,7 @@ __device__ void finalize_op(int op, int k, const double t[3], const PcgState& S,
       rr[k] = t[0];
       const double bn = sqrt(bb[k]), rn = sqrt(t[0]);
       relres[k] = rn / bn;
+      hist_put(S, 0, iters[k], k, rn);
       if (rn <= S.rtol * bn) active[k] = 0;
       else if (!isfinite(rn)) { active[k] = 0; status[k] = BDDC_ERR_BREAKDOWN; atomicAdd(brk, 1); }
     }
@@ -147,6 +162,7 @@ __device__ void finalize_op(int op, int k, const double t[3], const PcgState& S,
     if (active[k]) {
       beta[k] = (S.flexible ? t[0] - t[1] : t[0]) / rho[k];
       rho[k] = t[0];
+      hist_put(S, 2, iters[k] - 1, k, beta[k]);
     } else {
       beta[k] = 0;
     }
@@ -266,7 +282,8 @@ __global__ void __launch_bounds__(kThreads) k_dots_fin(int64_t n_nodes, int nrhs
 }
 
 PcgState state(bddc_handle_s* h, double rtol, int flexible) {
-  return PcgState{h->d_scal, h->d_iscal, h->d_partials, h->d_counter, h->nrhs_max, rtol, flexible};
+  return PcgState{h->d_scal, h->d_iscal, h->d_partials, h->d_counter, h->d_hist, h->hist_cap, h->nrhs_max, rtol,
+                  flexible};
 }
 
 void stencil_coefs(int dim, double h, double c[4]) {

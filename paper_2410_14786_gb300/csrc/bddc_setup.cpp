@@ -75,6 +75,7 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
   if (O->coarse < BDDC_COARSE_AUTO || O->coarse > BDDC_COARSE_SPARSE) { err = "unknown coarse mode"; return BDDC_ERR_INVALID_ARG; }
   if (O->coarse_blocks < 0) { err = "coarse_blocks must be >= 0"; return BDDC_ERR_INVALID_ARG; }
   if (O->full_operators != 0 && O->full_operators != 1) { err = "full_operators must be 0 or 1"; return BDDC_ERR_INVALID_ARG; }
+  if (O->history < 0 || O->history > 100000) { err = "history must be in [0, 100000]"; return BDDC_ERR_INVALID_ARG; }
   const int64_t ne = P->ne;
   const int64_t n_el = P->dim == 2 ? ne * ne : ne * ne * ne;
   for (int64_t e = 0; e < n_el; ++e) {

@@ -66,7 +66,8 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
                                 "bddc_apply_static_scratch: this problem needs " + std::to_string(need) +
                                     " doubles of temporaries, more than the " + std::to_string(kScratchDoubles) +
                                     " reserved; use bddc_apply");
-  if (cudaSetDevice(h->device) != cudaSuccess) return bddc::set_last_error(BDDC_ERR_CUDA, "cudaSetDevice failed");
+  bddc::DeviceGuard device_guard(h->device);   // the caller's current device is restored on return
+  if (!device_guard.ok) return bddc::set_last_error(BDDC_ERR_CUDA, "could not make the handle's device current");
   double* base = nullptr;
   cudaError_t ae = scratch_address(h->device, &base);
   if (ae != cudaSuccess)

@@ -43,7 +43,7 @@ namespace bddc {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr long long kBarrierCycles = 4000000000LL;   // about 2 s at 2 GHz
+
 
 struct CoarseArgs {
   const CNodeDev* nodes;
@@ -61,6 +61,8 @@ struct CoarseArgs {
   unsigned int* bar;         // [0] barrier arrivals
   int32_t* err;
   int levels, nrhs;
+  unsigned int bar_extra;    // arrivals a barrier waits for beyond the grid (0; > 0 only to test the waits)
+  long long bar_cycles;      // limit of one barrier wait, clock cycles
 };
 
 // Grid-wide barrier; false when a wait ran out (here or in another block).
@@ -69,9 +71,10 @@ struct CoarseArgs {
 // Ordering: the block's writes precede thread 0's release increment (block
 // barrier, then red.release at GPU scope); thread 0's acquire load of the
 // final count precedes the block's later reads (then the block barrier).
-__device__ bool grid_sync(unsigned int* bar, int32_t* err, unsigned int& epoch) {
+__device__ bool grid_sync(unsigned int* bar, int32_t* err, unsigned int& epoch, unsigned int extra,
+                          long long limit) {
   __shared__ int ok;
-  const unsigned int target = ++epoch * gridDim.x;
+  const unsigned int target = ++epoch * gridDim.x + extra;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
@@ -81,7 +84,7 @@ __device__ bool grid_sync(unsigned int* bar, int32_t* err, unsigned int& epoch) 
       unsigned int v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if (v >= target) break;
-      if (*(volatile int32_t*)err == BDDC_ERR_TIMEOUT || clock64() - t0 > kBarrierCycles) {
+      if (*(volatile int32_t*)err == BDDC_ERR_TIMEOUT || clock64() - t0 > limit) {
         atomicExch(err, BDDC_ERR_TIMEOUT);
         ok = 0;
         break;
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
     a.rp[i] = a.r[(int64_t)a.order[pos] * a.nrhs + (i - pos * a.nrhs)];
   }
   unsigned int epoch = 0;
-  if (!grid_sync(a.bar, a.err, epoch)) return;
+  if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
   for (int lv = 0; lv < L; ++lv) {
     for (int64_t t = (int64_t)off_f[lv] * nrb + gw; t < (int64_t)off_f[lv + 1] * nrb; t += nw) {
       const int64_t ui = t / nrb;
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
       else
         forward_unit(a, w, lane, kb, ke);
     }
-    if (!grid_sync(a.bar, a.err, epoch)) return;
+    if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
   }
   for (int lv = L - 1; lv >= 0; --lv) {
     for (int64_t t = (int64_t)off_b[lv] * nrb + gw; t < (int64_t)off_b[lv + 1] * nrb; t += nw) {
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(RB == 1 ? kThreads : kThreads / 2, 1) k_coarse
       else
         backward_unit(a, a.units[ui], lane, kb, ke);
     }
-    if (lv > 0 && !grid_sync(a.bar, a.err, epoch)) return;
+    if (lv > 0 && !grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
   }
 }
 
@@ -436,6 +439,8 @@ struct GatherArgs {
   unsigned int* bar;
   int32_t* err;
   int levels, n_c;
+  unsigned int bar_extra;
+  long long bar_cycles;
 };
 
 // Coefficients and operand indices of one batch: elements base + lane + 32 i
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
         pre = true;
       }
     }
-    if (ph + 1 < P && !grid_sync(a.bar, a.err, epoch)) return;
+    if (ph + 1 < P && !grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
     beg = nbeg;
     cnt = ncnt;
     dl = ndl;
@@ -737,7 +742,7 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   if (nrhs == 1 && h->d_gC) {
     const int sh = narrow ? 1 : 0;
     GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
-                 h->c_levels, (int)h->n_c};
+                 h->c_levels, (int)h->n_c, h->cbar_extra, h->cbar_cycles};
     if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->g_blocks);
@@ -753,7 +758,7 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
   CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
                blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
-               h->c_levels, nrhs};
+               h->c_levels, nrhs, h->cbar_extra, h->cbar_cycles};
   if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(narrow ? h->c_sms : blocked ? h->c_grid4 : h->c_grid);

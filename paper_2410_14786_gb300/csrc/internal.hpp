@@ -48,6 +48,7 @@ struct CGUnit {
 // phases L .. 2L-1 the backward levels (height = 2L-1-phase).
 struct CoarseFactor;
 constexpr int kGatherBatch = 256;   // coefficients a warp reads per step of a unit (cost unit of the assignment)
+constexpr long long kBarrierWaitCycles = 4000000000LL;   // grid-barrier wait limit: about 2 s at 2 GHz
 struct GatherLayout {
   std::vector<double> C;
   std::vector<int32_t> I;
@@ -156,6 +157,26 @@ struct HostSetup {
   std::vector<double> Ac_val;
   CoarseFactor cfac;                         // its sparse Cholesky factorisation
   int error_subdomain = -1;
+};
+
+// Makes `device` current for the lifetime of the guard and restores the
+// caller's current device afterwards (every entry point of the C ABI).
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
 
 // Record `msg` for bddc_last_error() on this thread; returns `code`.
@@ -289,6 +310,13 @@ struct bddc_handle_s {
   int32_t* d_iscal = nullptr;              // per-column flags / counters
   int32_t* h_flags = nullptr;              // pinned host mirror of the global flags
   int32_t* d_err = nullptr;                // device error flag (inside d_iscal)
+  double* d_hist = nullptr;                // [3][hist_cap + 1][nrhs_max] PCG history (null if not kept)
+  int hist_cap = 0;                        // iterations whose scalars are kept
+  // fault injection for tests of the bounded waits: the coarse solve's grid
+  // barriers wait for cbar_extra arrivals more than the grid makes, with a
+  // wait limit of cbar_cycles clock cycles
+  unsigned int cbar_extra = 0;
+  long long cbar_cycles = bddc::kBarrierWaitCycles;
   int n_red_blocks = 0;
   double* d_stencil = nullptr;             // [stencil points][n_nodes] assembled Q1 stencil
   unsigned int* d_counter = nullptr;       // blocks finished in the current reducing kernel

@@ -25,10 +25,38 @@ def _oracle(p, mask=0):
 
 
 def _bddc(p, precision="fp64", mask=0, nrhs_max=1, coarse="auto", phi_fp64=False, coarse_blocks=0,
-          full_operators=False):
+          full_operators=False, history=0, graph=True):
     from paper_2410_14786_gb300 import BDDC
     return BDDC.from_problem(p, precision=precision, constraints=mask, nrhs_max=nrhs_max, coarse=coarse,
-                             phi_fp64=phi_fp64, coarse_blocks=coarse_blocks, full_operators=full_operators)
+                             phi_fp64=phi_fp64, coarse_blocks=coarse_blocks, full_operators=full_operators,
+                             history=history, graph=graph)
+
+
+def _assert_history_matches(hg, ho, col, tol=1e-10, tol_r=1e-12):
+    """Per-iteration PCG scalars of one column against the oracle's: alpha_k
+    for k < iters and the beta after iteration k + 1 for k < iters - 1, each
+    to `tol` relative; ||r_k|| for k = 0 .. iters to tol_r ||r_0||; NaN
+    beyond. The residual is updated recursively (r_k+1 = r_k - alpha_k A p_k),
+    so both sides carry absolute rounding of order eps ||r_0|| in it: by
+    iteration k its norm has fallen to about 1e-8 ||r_0|| and agrees only to
+    about 1e-8 of itself, but to 1e-15 ||r_0|| (measured on GB300; alpha and
+    beta agree to 7e-12 relative at every k)."""
+    it = ho["iters"]
+    rn = hg["rnorm"][:, col]
+    al = hg["alpha"][:, col]
+    be = hg["beta"][:, col]
+    want_rn = np.asarray(ho["rnorm"])
+    assert np.all(np.abs(rn[:it + 1] - want_rn) <= tol_r * want_rn[0]), (rn[:it + 1], want_rn)
+    assert np.all(np.isnan(rn[it + 1:]))
+    if it:
+        want_al = np.asarray(ho["alpha"])
+        assert np.all(np.abs(al[:it] - want_al) <= tol * np.abs(want_al)), (al[:it], want_al)
+    assert np.all(np.isnan(al[it:]))
+    if it > 1:
+        want_be = np.asarray(ho["beta"])
+        assert want_be.size == it - 1
+        assert np.all(np.abs(be[:it - 1] - want_be) <= tol * np.abs(want_be)), (be[:it - 1], want_be)
+    assert np.all(np.isnan(be[max(it - 1, 0):]))
 
 
 def _small_voronoi():
@@ -209,10 +237,15 @@ def test_apply_ignores_dirichlet_input_and_multi_rhs():
     assert _rel(z1, want[:, 2]) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["cfg1_2d", "3d_24_3cubed", "3d_voronoi"])
-def test_pcg_fp64_matches_oracle(name):
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("name", ["cfg1_2d", "3d_24_3cubed", "3d_voronoi", "3d_corners_only"])
+def test_pcg_fp64_matches_oracle(name, graph):
+    """The FP64 PCG iterates match the oracle's: the same iteration count, the
+    solution to 1e-10, and at every iteration k the residual norm ||r_k||,
+    alpha_k and beta_k to 1e-10 relative (whole-solve graph and direct
+    launches)."""
     p, mask, o = _case(name)
-    g = _bddc(p, mask=mask)
+    g = _bddc(p, mask=mask, history=200, graph=graph)
     b = o.rhs(p.f[:, 0])
     xo, h = o.pcg(b, 1e-8)
     x, res = g.pcg_solve(_cuda(b), rtol=1e-8, maxit=500)
@@ -221,11 +254,15 @@ def test_pcg_fp64_matches_oracle(name):
     assert int(res.iters[0]) == h[0]["iters"]
     assert _rel(x, xo) < 1e-10
     assert abs(res.relres[0] - h[0]["rnorm"][-1] / np.linalg.norm(o.to_free(b))) < 1e-10
+    _assert_history_matches(g.pcg_history(), h[0], 0)
+    g.close()
 
 
 def test_pcg_multi_rhs_and_zero_column():
+    """Independent columns (one of them zero): per-column iteration counts,
+    solutions and per-iteration histories match the oracle's."""
     p, mask, o = _case("cfg1_2d")
-    g = _bddc(p, mask=mask, nrhs_max=3)
+    g = _bddc(p, mask=mask, nrhs_max=3, history=100)
     f = synth.uniform(35, o.n_nodes * 3).reshape(-1, 3)
     b = o.rhs(f)
     b[:, 1] = 0.0
@@ -235,6 +272,10 @@ def test_pcg_multi_rhs_and_zero_column():
     assert list(res.iters) == [hh["iters"] for hh in h]
     assert np.all(x[:, 1] == 0)
     assert _rel(x, xo) < 1e-10
+    hg = g.pcg_history(nrhs=3)
+    for k in (0, 2):
+        _assert_history_matches(hg, h[k], k)
+    assert hg["rnorm"][0, 1] == 0.0 and np.all(np.isnan(hg["rnorm"][1:, 1]))
 
 
 @pytest.mark.parametrize("name,nrhs", [("3d_24_3cubed", 8), ("3d_voronoi", 64), ("cfg1_2d", 16)])
@@ -428,3 +469,33 @@ def test_whole_solve_graph(prec):
     assert int(r3.iters[0]) == 3 and r3.status == 1
     x4, r4 = gg.pcg_solve(b, rtol=1e-8)
     assert torch.equal(x4, xg)
+
+
+def test_history_graph_equals_direct_and_mixed_form():
+    """The flexible (BF16) PCG records its history too: the graph replay and
+    direct launches give bitwise equal scalars, ||r_k|| decreases to below
+    rtol ||b||, and a history shorter than the solve keeps its first entries."""
+    p, mask, o = _case("3d_24_3cubed")
+    b = _cuda(o.rhs(p.f[:, 0]))
+    hs = []
+    for graph in (True, False):
+        g = _bddc(p, precision="bf16", mask=mask, history=64, graph=graph)
+        x, res = g.pcg_solve(b, rtol=1e-8)
+        hs.append((g.pcg_history(), int(res.iters[0])))
+        g.close()
+    (h1, it1), (h2, it2) = hs
+    assert it1 == it2
+    for key in ("rnorm", "alpha", "beta"):
+        assert np.array_equal(h1[key], h2[key], equal_nan=True)
+    rn = h1["rnorm"][:it1 + 1, 0]
+    assert rn[-1] <= 1e-8 * float(b.norm()) < rn[-2]
+    g = _bddc(p, mask=mask, history=4)
+    g.pcg_solve(b, rtol=1e-8)
+    short = g.pcg_history()
+    gl = _bddc(p, mask=mask, history=64)
+    gl.pcg_solve(b, rtol=1e-8)
+    long = gl.pcg_history()
+    assert np.array_equal(short["rnorm"], long["rnorm"][:5])
+    from paper_2410_14786_gb300 import BDDCError
+    with pytest.raises(BDDCError):
+        g.pcg_history(n_iter=5)
