@@ -11,11 +11,13 @@ coarse solve, prolongation, SpMV, dot products), inputs resident in HBM.
 `value` is solves per second of the headline mixed form (bf16 local and
 interior operators with float32 accumulation inside flexible PCG; everything
 else float64). The FP64, FP32 and TF32 (tensor-core) forms are timed beside it.
+`forms_cfg5` times the 192^3 workload (24^3 subdomains, 8 right-hand sides,
+whole solve as one CUDA graph) in FP64 and in the mixed BF16 tensor-core form.
 
-`--impl reference` times the CPU oracle (the plain NumPy/SciPy definitions
-of the paper's Sec. 2) on a bounded sample of the same workload: the same
-shape of problem on 32^3 elements with 4^3 subdomains of 8^3 (1/27 of the
-subdomains), its solve time scaled by 27.
+`cpu_baseline` and `--impl reference` time the CPU oracle (the plain
+NumPy/SciPy definitions of the paper's Sec. 2) on this same workload: its
+setup untimed, then whole PCG solves to rtol 1e-8 (the reference arm times as
+many whole solves as its time budget allows and reports that count as steps).
 """
 from __future__ import annotations
 
@@ -39,8 +41,9 @@ RTOL = 1e-8
 # ncu captures of the operator kernel on this workload in the bf16 form; no
 # figure for other workloads or kernels (traffic is then null).
 MEASURED_TRAFFIC = {(WORKLOAD, "bf16", "k_bgemv_tma"): 1.2897e9,   # full operators (full_operators=True)
-                    (WORKLOAD, "bf16", "k_sgemv_tma"): 6.6234e8}   # lower triangles (default)
-SAMPLE_NE, SAMPLE_NSUB, SAMPLE_SCALE = 32, 4, 27
+                    (WORKLOAD, "bf16", "k_sgemv_tma"): 6.6318e8}   # lower triangles, block-row kernel (default)
+WORKLOAD5 = "3d_q1_192cubed_24cubed_subdomains_lognormal_sigma_8rhs"
+REF_BUDGET_S = 150.0      # reference arm: whole oracle solves are timed until this much time has passed
 
 
 def _peaks():
@@ -59,10 +62,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
+        import tempfile
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"bddc_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -129,40 +133,100 @@ def whole_job_rate(ws: int, seconds_per_step: float) -> float:
     return ws / seconds_per_step
 
 
-def oracle_solve_time(reps: int = 1):
-    """Oracle (CPU) PCG solve on the 1/27 sample; returns seconds per solve."""
+def _blas_threads() -> int | None:
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads") or 0) for i in threadpool_info()) or None
+    except Exception:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            if os.environ.get(k):
+                return int(os.environ[k])
+        return None
+
+
+def oracle_measure(budget_s: float, max_solves: int, warm_applies: int = 0) -> dict:
+    """The CPU oracle on the benchmark workload itself (96^3 elements, 12^3
+    subdomains): setup (untimed), then whole PCG solves to rtol 1e-8 until
+    budget_s has passed or max_solves are done (at least one)."""
     import synth
     from oracle import Oracle
-    p = synth.make_problem(3, SAMPLE_NE, SAMPLE_NSUB, "lognormal", k=2)
+    p = synth.config(2)
+    t0 = time.perf_counter()
     o = Oracle(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub)
+    setup_s = time.perf_counter() - t0
     b = o.rhs(p.f[:, 0])
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
+    for _ in range(warm_applies):
+        o.apply(o.to_free(b))
+    times, iters = [], 0
+    t_start = time.perf_counter()
+    while not times or (len(times) < max_solves and time.perf_counter() - t_start < budget_s):
+        t1 = time.perf_counter()
         _, h = o.pcg(b, RTOL)
-        times.append(time.perf_counter() - t0)
-    return times, h[0]["iters"]
+        times.append(time.perf_counter() - t1)
+        iters = h[0]["iters"]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"setup_s": setup_s, "solve_s": times, "iters": iters, "cores": cores, "blas_threads": _blas_threads()}
+
+
+def start_oracle_worker(reserve: int = 2):
+    """The oracle baseline in a fresh interpreter (exec, not fork), on the host
+    cores other than the first `reserve` ones, which the GPU process keeps."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ)
+    cores = list(range(reserve, n)) if n > reserve + 1 else list(range(n))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(len(cores))
+    env["BDDC_ORACLE_CORES"] = ",".join(map(str, cores))
+    return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker"], env=env,
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+
+
+def collect_oracle_worker(proc, timeout_s: float) -> dict:
+    try:
+        out, err = proc.communicate(timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        proc.communicate()
+        return {"value": None, "unit": "solves/s", "kind": "oracle",
+                "sample": f"not measured: the oracle did not finish within {timeout_s:.0f} s"}
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    if proc.returncode != 0 or not lines:
+        return {"value": None, "unit": "solves/s", "kind": "oracle",
+                "sample": "not measured: oracle worker failed: " + (err.strip().splitlines() or ["?"])[-1][:200]}
+    r = json.loads(lines[-1])
+    per = float(np.mean(r["solve_s"]))
+    return {"value": 1.0 / per, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
+            "blas_threads": r["blas_threads"], "setup_s": r["setup_s"], "solve_s": per, "iters": r["iters"],
+            "sample": f"one whole oracle PCG solve to rtol 1e-8 of this workload (96^3 elements, 12^3 subdomains, "
+                      f"{r['iters']} iterations) after an untimed oracle setup of {r['setup_s']:.0f} s"}
+
+
+def oracle_worker_main() -> int:
+    cores = os.environ.get("BDDC_ORACLE_CORES")
+    if cores and hasattr(os, "sched_setaffinity"):
+        os.sched_setaffinity(0, {int(c) for c in cores.split(",")})
+    print(json.dumps(oracle_measure(budget_s=0.0, max_solves=1)))
+    return 0
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import synth  # noqa: F401
-    t_all, iters = oracle_solve_time(args.warmup + args.steps)
-    t = t_all[args.warmup:]
-    per_solve = SAMPLE_SCALE * float(np.mean(t))
-    value = 1.0 / per_solve
-    cores = os.cpu_count()
-    sample = (f"oracle PCG solve of the same problem family on {SAMPLE_NE}^3 elements with {SAMPLE_NSUB}^3 "
-              f"subdomains of 8^3 (1/{SAMPLE_SCALE} of the workload's subdomains, {iters} iterations), "
-              f"time x {SAMPLE_SCALE}")
+    r = oracle_measure(budget_s=REF_BUDGET_S, max_solves=max(1, args.steps), warm_applies=1)
+    per = float(np.mean(r["solve_s"]))
+    value = 1.0 / per
+    n = len(r["solve_s"])
+    sample = (f"whole oracle PCG solves to rtol 1e-8 of this workload ({r['iters']} iterations each): {n} timed "
+              f"(as many as fit in {REF_BUDGET_S:.0f} s), after an untimed oracle setup of {r['setup_s']:.0f} s "
+              f"and one untimed apply")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "steps": n, "warmup": 1, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1/27 scaled"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "elements": "96^3", "subdomains": 1728, "nrhs": 1,
+                                            "rtol": RTOL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
+                             "blas_threads": r["blas_threads"], "setup_s": r["setup_s"], "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -176,6 +240,11 @@ def run_gb300(args):
     from paper_2410_14786_gb300 import BDDC, build
 
     ws, rank, local = _dist()
+    # the oracle baseline runs in its own process on the other host cores
+    # while the GPU forms are timed (started before any CUDA call)
+    oracle_proc = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config == 2:
+        oracle_proc = start_oracle_worker(reserve=2)
     if ws > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl")
@@ -283,6 +352,12 @@ def run_gb300(args):
                 "kernel": ("k_tc_gemm + k_tc_pack" if inf["tensor_cores"] else kname) + " (3 operator passes per apply"
                           + (", operators stored as lower triangles)" if inf["symmetric_operators"] else ")"),
                 "bytes_per_apply": op_bytes}
+    # the whole apply (every launch of M^-1 r) against the same peak
+    apply_roofline = {"bytes_per_apply": inf["apply_bytes_1rhs"] * nrhs if nrhs == 1 else None,
+                      "apply_ms": head["apply_ms"],
+                      "achieved_GBps": inf["apply_bytes_1rhs"] / (head["apply_ms"] * 1e-3) / 1e9 if nrhs == 1 else None}
+    if nrhs == 1:
+        apply_roofline["frac"] = apply_roofline["achieved_GBps"] / peak
 
     # end to end through the public API with host buffers (pinned)
     bh = torch.empty(b.shape, dtype=torch.float64, pin_memory=True)
@@ -297,13 +372,14 @@ def run_gb300(args):
         g.pcg_solve_host(bn, rtol=RTOL, out=xn)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config == 2:
-        times, it_o = oracle_solve_time(1)
-        per = SAMPLE_SCALE * times[0]
-        cpu = {"value": 1.0 / per, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one oracle PCG solve on {SAMPLE_NE}^3 elements / {SAMPLE_NSUB}^3 subdomains of 8^3 "
-                         f"({it_o} iterations), x {SAMPLE_SCALE} for the 12^3-subdomain workload"}
+    for gg in handles.values():
+        gg.close()
+    handles.clear()
+    cfg5 = None
+    if args.config == 2 and not args.no_cfg5:
+        cfg5 = run_cfg5(args, barrier, peak, peak_kind)
+
+    cpu = collect_oracle_worker(oracle_proc, timeout_s=1200.0) if oracle_proc is not None else None
 
     ms = head["ms_per_solve"]
     line = {
@@ -315,6 +391,7 @@ def run_gb300(args):
                    "subdomains": p.n_sub, "nrhs": nrhs, "n_c": inf["n_c"], "rtol": RTOL, "mixed_form": headline, "l2": f"inputs larger than L2 (operators {inf['operator_bytes'] / 1e9:.2f} GB)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roofline,
+        "apply_roofline": apply_roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_rate(ws, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": int(b.numel() * 8),
                 "d2h_bytes_per_step": int(b.numel() * 8)},
@@ -323,14 +400,72 @@ def run_gb300(args):
         "forms": forms,
         "time_to_rtol_ms": {k: v["ms_per_solve"] for k, v in forms.items()},
         "applies_per_s": {k: v["applies_per_s"] for k, v in forms.items()},
+        "forms_cfg5": cfg5,
     }
     if rank == 0:
         print(json.dumps(line))
-    for gg in handles.values():
-        gg.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_cfg5(args, barrier, peak, peak_kind) -> dict:
+    """The 192^3 workload (24^3 subdomains of 8^3, 8 right-hand sides, whole
+    solve as one CUDA graph): FP64 and the mixed BF16 form on the tensor
+    cores, time to rtol 1e-8 per block of 8 solves (steps capped at 3 after
+    one untimed solve: a FP64 solve takes seconds), iterations, true
+    residual, difference from FP64, and the roofline of the tensor-core
+    operator passes."""
+    import torch
+
+    import synth
+    from paper_2410_14786_gb300 import BDDC
+    p = synth.config(5)
+    nrhs = p.nrhs
+    f = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
+    out = {"workload": WORKLOAD5, "elements": f"{p.ne}^{p.dim}", "subdomains": p.n_sub, "nrhs": nrhs, "rtol": RTOL,
+           "steps": min(args.steps, 3), "warmup": 1, "forms": {}}
+    x64 = None
+    g64 = None
+    for prec in ("fp64", "bf16"):
+        g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs)
+        fm = {"setup_s": g.info()["setup_seconds"], "tensor_cores": g.info()["tensor_cores"]}
+        if not args.no_autotune:
+            fm["tuning"] = g.autotune(nrhs)
+        b = g.rhs(f)
+        x = torch.empty_like(b)
+        g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(out["steps"]):
+            _, res = g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+        e1.record()
+        barrier()
+        fm["ms_per_solve_block"] = e0.elapsed_time(e1) / out["steps"]
+        fm["iters_max"] = int(res.iters.max())
+        gm = g64 if g64 is not None else g
+        fm["true_relres_max"] = float(((b - gm.matvec(x)).norm(dim=0) / b.norm(dim=0)).max().item())
+        prof = g.profile_apply(torch.rand_like(b), reps=3)
+        fm["apply_launch_ms"] = prof
+        inf = g.info()
+        if prec == "fp64":
+            x64, g64 = x.clone(), g
+        else:
+            fm["rel_diff_vs_fp64"] = float(((x - x64).norm() / x64.norm()).item())
+            op_ms = prof["interior_op"] + prof["interface_op"] + prof["interior_op_final"]
+            op_bytes = (2 * inf["interior_op_bytes"] + inf["interface_op_bytes"]
+                        + 8 * 2 * nrhs * (2 * inf["n_interior"] + inf["n_interface_copies"]))
+            ach = op_bytes / (op_ms * 1e-3) / 1e9
+            fm["roofline"] = {"bound": "hbm", "kernel": "k_tc_gemm + k_tc_pack (3 operator passes per apply)",
+                              "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "peak_kind": peak_kind, "bytes_per_apply": op_bytes, "traffic": None}
+            g.close()
+        out["forms"][prec] = fm
+    if g64 is not None:
+        g64.close()
+    out["mixed_speedup_vs_fp64"] = out["forms"]["fp64"]["ms_per_solve_block"] / out["forms"]["bf16"]["ms_per_solve_block"]
+    return out
 
 
 def run_apply_only(args):
@@ -460,7 +595,11 @@ def main():
                     help="workload (2 = the metric's configuration; others for development)")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling aid: set up the headline form, run this many applies and one solve, exit")
+    ap.add_argument("--no-cfg5", action="store_true", help="skip the 192^3 workload (forms_cfg5)")
+    ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_worker:
+        return oracle_worker_main()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -248,11 +248,15 @@ typedef struct {
     int32_t gemv_rows_interface;
     int32_t coarse_overlap;           /* 1: the interface operator runs on a second stream, concurrently
                                          with the coarse residual and solve (default 0) */
+    int32_t sym_stages_interior;      /* shared-memory stages of the symmetric (lower-triangle) GEMV,
+                                         3 or 4 (default 4) */
+    int32_t sym_stages_interface;
 } bddc_tuning_t;
 
 /* Time the candidate launch parameters for blocks of nrhs columns (row
  * tiles of 64, 128 and 256 rows and stage sizes of 6, 12, 24 and 48 KB of
- * the streamed GEMV of each operator family when the handle uses it;
+ * the streamed GEMV of each operator family when the handle uses it, or for
+ * the symmetric GEMV 3 or 4 stages of 10 to 24 KB;
  * one-row against four-row coarse sweep units when nrhs >= 2; whole applies
  * with and without the coarse overlap), apply the fastest and return them in
  * *out (may be NULL).
@@ -319,7 +323,7 @@ int bddc_coarse_vectors(bddc_handle_t h, double *rc, double *uc, int32_t nrhs, v
 /* Sizes, byte counts and timings of a handle. */
 int bddc_query(bddc_handle_t h, bddc_info_t *info);
 
-/* Device time (milliseconds, CUDA events, mean over `reps` applies of the
+/* Device time (milliseconds, CUDA events, median over `reps` applies of the
  * device vector r on `stream`) of each launch of one apply: out_ms[0..8] =
  * restriction, interior operator (t_I = A_II^-1 r_I), condensed interface
  * right-hand side, interface operator (z_G = K_GG y'_G), coarse residual,

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["bddc_kernels.cu", "bddc_bgemv_tma.cu", "bddc_pcg.cu", "coarse_solve.cu", "bddc_api.cu",
               "bddc_static_scratch.cu", "bddc_tc_gemm.cu"]
 CXX_SOURCES = ["bddc_setup.cpp", "coarse_sparse.cpp"]
-HEADERS = ["dense.hpp", "internal.hpp", "kernels.cuh"]
+HEADERS = ["dense.hpp", "internal.hpp", "kernels.cuh", "sym_layout.hpp"]
 
 
 def _nvcc() -> str:

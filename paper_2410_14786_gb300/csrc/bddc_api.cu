@@ -825,15 +825,18 @@ int bddc_profile_apply(bddc_handle_t h, const double* r, double* z, int32_t nrhs
   // interface operator on a second stream) is off while profiling
   const int keep_overlap = h->tune_overlap;
   h->tune_overlap = 0;
+  std::vector<float> t(9 * (size_t)reps, 0.0f);
   for (int rep = 0; rep < reps && rc == BDDC_OK; ++rep) {
     cudaError_t e = launch_apply(h, r, z, nrhs, st, ev);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[9]);
-    float ms;
-    for (int i = 0; i < 9 && e == cudaSuccess; ++i) {
-      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-      out_ms[i] += ms / reps;
-    }
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&t[(size_t)i * reps + rep], ev[i], ev[i + 1]);
     if (e != cudaSuccess) rc = fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
+  }
+  // the median of the repetitions (robust to a late launch on a busy host)
+  for (int i = 0; i < 9 && rc == BDDC_OK; ++i) {
+    float* b = &t[(size_t)i * reps];
+    std::nth_element(b, b + reps / 2, b + reps);
+    out_ms[i] = b[reps / 2];
   }
   h->tune_overlap = keep_overlap;
   for (auto& e : ev) cudaEventDestroy(e);
@@ -1132,7 +1135,8 @@ int bddc_clear_device_error(bddc_handle_t h) {
 int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
   if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
   *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min,
-                       64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1], h->tune_overlap};
+                       64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1], h->tune_overlap,
+                       h->tune_sym_stages[0], h->tune_sym_stages[1]};
   return BDDC_OK;
 }
 
@@ -1148,11 +1152,16 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
     return fail(BDDC_ERR_INVALID_ARG, "GEMV row tile must be 64, 128 or 256");
   if (in->coarse_overlap != 0 && in->coarse_overlap != 1)
     return fail(BDDC_ERR_INVALID_ARG, "coarse_overlap must be 0 or 1");
+  if (in->sym_stages_interior < 3 || in->sym_stages_interior > 4 || in->sym_stages_interface < 3 ||
+      in->sym_stages_interface > 4)
+    return fail(BDDC_ERR_INVALID_ARG, "symmetric GEMV stages must be 3 or 4");
   h->tune_tile_class[0] = tile_class(in->gemv_rows_interior);
   h->tune_tile_class[1] = tile_class(in->gemv_rows_interface);
   h->tune_overlap = in->coarse_overlap;
   h->tune_stage_kb[0] = in->gemv_stage_kb_interior;
   h->tune_stage_kb[1] = in->gemv_stage_kb_interface;
+  h->tune_sym_stages[0] = in->sym_stages_interior;
+  h->tune_sym_stages[1] = in->sym_stages_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
   drop_graphs(h);   // captured graphs hold the old launch parameters
   return BDDC_OK;
@@ -1182,7 +1191,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     return best[1];
   };
   bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
-                  64 << h->tune_tile_class[1], h->tune_overlap};
+                  64 << h->tune_tile_class[1], h->tune_overlap, h->tune_sym_stages[0], h->tune_sym_stages[1]};
   cudaError_t ce = cudaSuccess;
   if ((ce = cudaMemsetAsync(h->w_rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
       (ce = cudaMemsetAsync(h->w_yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
@@ -1191,31 +1200,42 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     return fail(BDDC_ERR_CUDA, cudaGetErrorString(ce));
   }
   if (h->use_tma && !h->use_tc) {
-    // every (row tile, stage size) pair of each operator family
+    // every (row tile, stage size) pair of each operator family; for the
+    // symmetric GEMV (one work item per operator) every (stages, stage size)
+    // pair instead
     const int cand[4] = {6, 12, 24, 48};
+    const int sym_cand[7][2] = {{4, 10}, {4, 12}, {4, 16}, {4, 20}, {3, 16}, {3, 20}, {3, 24}};
     for (int fam = 0; fam < 2; ++fam) {
       const bool interior = fam == 0;
       if ((interior ? h->nI_tot : h->nG_tot) == 0) continue;
       float best = -1.0f;
-      int best_kb = h->tune_stage_kb[fam], best_tc = h->tune_tile_class[fam];
-      for (int tc = 0; tc < (h->use_sym ? 1 : 3); ++tc)
-        for (int c : cand) {
-          h->tune_stage_kb[fam] = c;
-          h->tune_tile_class[fam] = tc;
-          const float ms = timed([&] {
-            return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs,
-                                   st);
-          });
-          if (ms >= 0.0f && (best < 0.0f || ms < best)) {
-            best = ms;
-            best_kb = c;
-            best_tc = tc;
-          }
+      int best_kb = h->tune_stage_kb[fam], best_tc = h->tune_tile_class[fam], best_ns = h->tune_sym_stages[fam];
+      auto try_one = [&](int kb, int tc, int ns) {
+        h->tune_stage_kb[fam] = kb;
+        h->tune_tile_class[fam] = tc;
+        h->tune_sym_stages[fam] = ns;
+        const float ms = timed([&] {
+          return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs, st);
+        });
+        if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+          best = ms;
+          best_kb = kb;
+          best_tc = tc;
+          best_ns = ns;
         }
+      };
+      if (h->use_sym) {
+        for (const auto& c : sym_cand) try_one(c[1], best_tc, c[0]);
+      } else {
+        for (int tc = 0; tc < 3; ++tc)
+          for (int c : cand) try_one(c, tc, best_ns);
+      }
       h->tune_stage_kb[fam] = best_kb;
       h->tune_tile_class[fam] = best_tc;
+      h->tune_sym_stages[fam] = best_ns;
       (interior ? t.gemv_stage_kb_interior : t.gemv_stage_kb_interface) = best_kb;
       (interior ? t.gemv_rows_interior : t.gemv_rows_interface) = 64 << best_tc;
+      (interior ? t.sym_stages_interior : t.sym_stages_interface) = best_ns;
     }
   }
   if (h->n_c && !h->coarse_dense && nrhs >= 2) {

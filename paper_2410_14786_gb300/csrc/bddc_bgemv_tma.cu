@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "sym_layout.hpp"
 
 namespace bddc {
 
@@ -50,12 +51,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// A waiting thread is suspended until the phase completes or kSuspendNs
+// nanoseconds have passed, instead of polling.
+constexpr uint32_t kSuspendNs = 1000000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "n"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -483,90 +487,175 @@ cudaError_t dispatch(const WorkItem* items, int n_items, int max_lda, const void
 // yT[c] += a x[g] (the halved diagonal counts once in each), so the operator
 // stream is about half of the full matrix.
 //
-// One block owns one operator at a time (operators dealt round-robin over
-// the blocks); the producer streams its rows in stages of whole rows, as in
-// k_bgemv_tma, and publishes each stage's last row in shared memory (found
-// by binary search over the row offsets). Row g is computed by consumer warp
-// g mod 8, all 32 lanes on one row, four rows per reduction: lane l reads the
-// 16-byte vectors l, l + 32, ... of every row, so it owns the same columns
-// in every row and keeps their transposed partial sums in registers (up to
-// kSymK vectors). When the operator's last row is done
-// the warps' partials are summed in warp order in shared memory and added to
-// the rows' own sums: the result does not depend on the grid, the stage size
-// or which block ran the operator.
-constexpr int kSymK = 4;   // at most 4 x 32 vectors per row: n <= 128 V
+// The kernel reads the triangle in block-rows: block-row G is rows V G ..
+// V G + V - 1, every one of them holding the G + 1 vectors of columns 0 ..
+// V G + V - 1, so a block-row is a V x (G + 1) array of V x V tiles,
+// contiguous in the arena. One block owns one operator at a time (operators
+// dealt round-robin over the blocks); its producer lane streams stages of
+// whole block-rows with bulk copies (as in k_bgemv_tma) and publishes each
+// stage's last block-row. Block-row G is computed by consumer warp G mod 8:
+// lane l takes the tile columns j = l + 32 s (s < K) of all V rows, so a
+// lane owns the same columns in every block-row, keeps their x values and
+// their transposed partial sums in registers, and accumulates the V row
+// sums, which the warp reduces once per block-row. Products are formed in
+// pairs with the packed float32 FMA (fma.rn.f32x2). When the operator's
+// last block-row is done the warps' transposed partials are summed in warp
+// order in shared memory and added to the row sums: the result depends
+// neither on the grid, nor on the stage size, nor on the block that ran the
+// operator.
+constexpr int kSymK = 4;   // at most 4 x 32 tile columns: n <= 128 V
 constexpr int kSymSmemCap = 200 * 1024;
+constexpr int kSymMinStages = 2;   // shared-memory ring of the symmetric GEMV: 2 to 8 stages
+constexpr int kSymMaxStages = 8;
+constexpr int kSymStages = 4;      // the deepest ring the tuning may choose (the support check assumes it)
 
-template <int V>
-__host__ __device__ __forceinline__ int64_t tri_off(int g) {
-  const int64_t q = g / V, r = g % V;
-  return (int64_t)V * (V * q * (q + 1) / 2 + r * (q + 1));
+
+// Packed pairs of float32 values (fma.rn.f32x2, sm_100 and later).
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
-// Rows [g0, g1) of one stage: as many whole rows as fit in stage_elems (at
-// least one); binary search (tri_off is increasing).
-template <int V>
-__device__ __forceinline__ int sym_stage_end(int g0, int n, int64_t stage_elems) {
-  const int64_t base = tri_off<V>(g0);
-  int lo = g0 + 1, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tri_off<V>(mid) - base <= stage_elems) lo = mid; else hi = mid - 1;
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ float f2_sum(uint64_t v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return lo + hi;
+}
+// One 16-byte operator vector as V / 2 pairs of float32 values.
+template <typename T> struct SymVec;
+template <> struct SymVec<float> {
+  static constexpr int P = 2;
+  __device__ static void load(const float* p, uint64_t (&o)[2]) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    o[0] = v.x; o[1] = v.y;
   }
-  return lo;
-}
-// Sums of 4 values over the 32 lanes: afterwards every lane of the 8-lane
-// group q = lane >> 3 holds the total of v[q] in v[0] (two halving
-// exchanges, then three full ones).
-template <typename Acc>
-__device__ __forceinline__ Acc warp_sum4(Acc (&v)[4], int lane) {
-  {
-    const bool upper = (lane & 16) != 0;
+};
+template <> struct SymVec<__nv_bfloat16> {
+  static constexpr int P = 4;
+  __device__ static void load(const __nv_bfloat16* p, uint64_t (&o)[4]) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const Acc send = upper ? v[i] : v[i + 2];
-      const Acc keep = upper ? v[i + 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    for (int i = 0; i < 4; ++i) o[i] = f2_pack(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
+  }
+};
+
+// Sums of V values over the 32 lanes: log2(V) halving exchanges (the lanes
+// with the exchange bit set keep the upper half), then full ones. Afterwards
+// lane l holds in v[0] the total of value sym_row(l).
+template <int V>
+__device__ __forceinline__ float warp_sum_rows(float (&v)[V], int lane) {
+#pragma unroll
+  for (int o = 16, n = V; n > 1; o >>= 1, n >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = upper ? v[i] : v[i + n / 2];
+      const float keep = upper ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  {
-    const bool upper = (lane & 8) != 0;
-    const Acc send = upper ? v[0] : v[1];
-    const Acc keep = upper ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  for (int o = 16 / V; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
   return v[0];
 }
+template <int V>
+__device__ __forceinline__ int sym_row(int lane) {
+  int q = 0;
+#pragma unroll
+  for (int o = 16, n = V; n > 1; o >>= 1, n >>= 1) q = 2 * q + ((lane & o) != 0);
+  return q;
+}
+
+// One 16-byte vector from shared memory (32-bit shared-space address) as
+// V / 2 pairs of float32 values.
+template <typename T> struct SymLds;
+template <> struct SymLds<float> {
+  __device__ static void load(uint32_t addr, uint64_t (&o)[2]) {
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(o[0]), "=l"(o[1]) : "r"(addr));
+  }
+};
+template <> struct SymLds<__nv_bfloat16> {
+  __device__ static void load(uint32_t addr, uint64_t (&o)[4]) {
+    uint32_t w[4];
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(addr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = f2_pack(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
+  }
+};
+
+// R rows of one block-row against the lane's NS active tile slots.
+// ad[s] / st[s]: shared address of the lane's vector in the first row and
+// the row pitch in bytes, or the address of a zero vector and 0 for a lane
+// with no tile in slot s (its products are then 0). Rows from nr on are
+// absent (the last block-row of an operator); PARTIAL selects the check.
+template <typename T, int K, int NS, int R, bool PARTIAL>
+__device__ __forceinline__ void sym_rows(uint32_t (&ad)[K], const uint32_t (&st)[K], const float* xrow, int nr,
+                                         const uint64_t (&xj)[K][SymVec<T>::P],
+                                         uint64_t (&accT)[K][SymVec<T>::P], float (&rs)[R]) {
+  constexpr int P = SymVec<T>::P;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    rs[r] = 0.0f;
+    if (!PARTIAL || r < nr) {
+      const float xr = xrow[r];
+      const uint64_t xrr = f2_pack(xr, xr);
+      uint64_t racc = 0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        uint64_t a[P];
+        SymLds<T>::load(ad[s], a);
+        ad[s] += st[s];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          racc = f2_fma(a[i], xj[s][i], racc);
+          accT[s][i] = f2_fma(a[i], xrr, accT[s][i]);
+        }
+      }
+      rs[r] = f2_sum(racc);
+    }
+  }
+}
+// Rows of one warp unit: a whole block-row (splitting BF16 block-rows over
+// two warps was measured 9 % slower on GB300).
+template <typename T> struct SymUnit { static constexpr int R = Op<T>::V; };
 
 template <typename T, int K>
 __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
     k_sgemv_tma(const WorkItem* __restrict__ items, int n_items, const T* __restrict__ arena,
                 const double* __restrict__ X, double* __restrict__ Y, const int32_t* __restrict__ yscatter,
-                int stage_bytes, int max_n, int32_t* __restrict__ err) {
-  using Acc = typename Op<T>::Acc;
+                int stage_bytes, int nst, int max_n, int32_t* __restrict__ err) {
   constexpr int V = Op<T>::V;
-  using XL = XLayout<Acc, V, 1>;
+  constexpr int P = SymVec<T>::P;   // float pairs per 16-byte vector
   extern __shared__ __align__(128) unsigned char smem[];
-  const int npad = (max_n + V - 1) / V * V;
+  constexpr int nx = 32 * K * V;                 // x as float, padded to whole lane slots
+  const int npad = (max_n + V - 1) / V * V;      // x (float64), row sums, transposed partials
   unsigned char* stages = smem;
-  Acc* xs = reinterpret_cast<Acc*>(smem + (size_t)kStages * stage_bytes);
-  double* xraw = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(xs) + XL::bytes(npad));
+  float* xs = reinterpret_cast<float*>(smem + (size_t)nst * stage_bytes);
+  double* xraw = reinterpret_cast<double*>(xs + nx);
   float* rowp = reinterpret_cast<float*>(xraw + npad);
   float* red = rowp + npad;
   uint64_t* full = reinterpret_cast<uint64_t*>(red + (size_t)kConsumerWarps * npad);
-  uint64_t* empty = full + kStages;
+  uint64_t* empty = full + nst;
   __shared__ int abort_flag;
-  __shared__ int stage_end[kStages];   // last row + 1 of the stage in each slot (written by the producer)
-  const int64_t stage_elems = stage_bytes / (int)sizeof(T);
+  __shared__ int stage_end[kSymMaxStages];   // last block-row + 1 of the stage in each slot (written by the producer)
+  __shared__ __align__(16) uint4 zvec;  // the vector a lane without a tile reads
+  const int stage_elems = stage_bytes / (int)sizeof(T);
+  const uint32_t zero_addr = smem_addr(&zvec);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
     }
     abort_flag = 0;
+    zvec = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -576,31 +665,33 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
     if (lane != 0) return;
     int slot = 0;
     uint32_t phase = 0;
-    bool pending[kStages];
-    uint32_t pend_parity[kStages];
-    for (int s = 0; s < kStages; ++s) pending[s] = false;
+    bool pending[kSymMaxStages];
+    uint32_t pend_parity[kSymMaxStages];
+    for (int s = 0; s < kSymMaxStages; ++s) pending[s] = false;
     bool ok = true;
     for (int u = blockIdx.x; u < n_items && ok; u += gridDim.x) {
       const WorkItem w = items[u];
-      const int n = w.ncols;
-      for (int g0 = 0, g1; g0 < n; g0 = g1) {
-        g1 = sym_stage_end<V>(g0, n, stage_elems);
+      const int n = w.ncols, nblk = (n + V - 1) / V;
+      for (int G0 = 0, G1; G0 < nblk; G0 = G1) {
+        G1 = sym_stage_end<V>(G0, nblk, n, stage_elems);
         if (!mbar_wait(&empty[slot], phase ^ 1u) || *(volatile int*)&abort_flag) {
           atomicExch(err, BDDC_ERR_TIMEOUT);
           abort_flag = 1;
           ok = false;
           break;
         }
-        const uint32_t bytes = (uint32_t)((tri_off<V>(g1) - tri_off<V>(g0)) * (int64_t)sizeof(T));
-        stage_end[slot] = g1;   // published by the arrive below (release), read after the wait (acquire)
+        const int32_t e0 = blk_off<V>(G0, n), e1 = blk_off<V>(G1, n);
+        const uint32_t bytes = (uint32_t)(e1 - e0) * (uint32_t)sizeof(T);
+        stage_end[slot] = G1;   // published by the arrive below (release), read after the wait (acquire)
         mbar_expect_tx(&full[slot], bytes);
-        bulk_load(stages + (size_t)slot * stage_bytes, arena + w.moff + tri_off<V>(g0), bytes, &full[slot]);
+        bulk_load(stages + (size_t)slot * stage_bytes, arena + w.moff + e0, bytes, &full[slot]);
+
         pending[slot] = true;
         pend_parity[slot] = phase;
-        if (++slot == kStages) { slot = 0; phase ^= 1u; }
+        if (++slot == nst) { slot = 0; phase ^= 1u; }
       }
     }
-    for (int s = 0; s < kStages; ++s)
+    for (int s = 0; s < nst; ++s)
       if (pending[s] && !mbar_wait(&full[s], pend_parity[s])) atomicExch(err, BDDC_ERR_TIMEOUT);
     return;
   }
@@ -613,8 +704,7 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
   bool aborted = false;
   auto prefetch_operand = [&](int uu) {
     const WorkItem wn = items[uu];
-    const int np = (wn.ncols + V - 1) / V * V;
-    for (int i = tid; i < np; i += kCT) {
+    for (int i = tid; i < npad; i += kCT) {
       if (i < wn.ncols)
         cp_async8(xraw + i, X + wn.xoff + i);
       else
@@ -622,80 +712,99 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
     }
     cp_async_commit();
   };
-  if (blockIdx.x < n_items) prefetch_operand(blockIdx.x);
+  // Two block barriers per operator: after the operand of the first
+  // operator has landed, each operator is computed, then (barrier A: all
+  // partials written, the next operand landed) the result is summed while
+  // the next operand is converted to float32, then (barrier B: xs complete,
+  // the partials and xraw free) the operand after it is prefetched.
+  auto convert_operand = [&]() {
+    for (int i = tid; i < nx; i += kCT) xs[i] = i < npad ? (float)xraw[i] : 0.0f;
+  };
+  if (blockIdx.x < n_items) {
+    prefetch_operand(blockIdx.x);
+    cp_async_wait_all();
+    consumer_sync();                          // operand landed
+    convert_operand();
+    consumer_sync();                          // xs complete; xraw free
+    if (blockIdx.x + (int)gridDim.x < n_items) prefetch_operand(blockIdx.x + gridDim.x);
+  }
   for (int u = blockIdx.x; u < n_items; u += gridDim.x) {
     const WorkItem w = items[u];
-    const int n = w.ncols;
-    const int np = (n + V - 1) / V * V;
-    cp_async_wait_all();
-    consumer_sync();                          // operand landed; xs, rowp, red free
-    for (int i = tid; i < np; i += kCT) xs[XL::index(i, 0)] = (Acc)xraw[i];
-    consumer_sync();                          // xs complete; xraw free
-    if (u + (int)gridDim.x < n_items) prefetch_operand(u + gridDim.x);
-    Acc accT[K][V];
+    const int n = w.ncols, nblk = (n + V - 1) / V;
+    const bool has_next = u + (int)gridDim.x < n_items;
+    // this lane's columns: tile columns j = lane + 32 s, x in pairs
+    uint64_t xj[K][P], accT[K][P];
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+    for (int s = 0; s < K; ++s)
 #pragma unroll
-      for (int v = 0; v < V; ++v) accT[k][v] = Acc(0);
-    for (int g0 = 0, g1; g0 < n; g0 = g1) {
+      for (int i = 0; i < P; i += 2) {   // 16-byte loads: two pairs each
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(xs + (s * 32 + lane) * V + 2 * i);
+        xj[s][i] = v.x;
+        xj[s][i + 1] = v.y;
+        accT[s][i] = 0;
+        accT[s][i + 1] = 0;
+      }
+    for (int G0 = 0, G1; G0 < nblk; G0 = G1) {
+      // every warp visits every stage in order, so that no warp reaches a
+      // slot whose barriers are a whole phase behind the stage it wants
       if (!aborted && (*(volatile int*)&abort_flag || !mbar_wait(&full[slot], phase))) {
         if (lane == 0) atomicExch(err, BDDC_ERR_TIMEOUT);
         abort_flag = 1;
         aborted = true;
       }
-      g1 = aborted ? sym_stage_end<V>(g0, n, stage_elems) : stage_end[slot];
+      G1 = aborted ? sym_stage_end<V>(G0, nblk, n, stage_elems) : stage_end[slot];
       if (!aborted) {
-        const T* tile = reinterpret_cast<const T*>(stages + (size_t)slot * stage_bytes);
-        const int64_t base = tri_off<V>(g0);
-        // rows g = warp (mod 8) of this stage, four at a time (one reduction)
-        for (int gb = g0 + ((warp - g0 % kConsumerWarps + kConsumerWarps) % kConsumerWarps); gb < g1;
-             gb += 4 * kConsumerWarps) {
-          Acc acc[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+        const uint32_t tile_addr = smem_addr(stages + (size_t)slot * stage_bytes);
+        const int32_t base = blk_off<V>(G0, n);
+        // warp units: rows [h R, h R + R) of block-row G, unit index G H + h,
+        // dealt round-robin over the warps by that index
+        constexpr int R = SymUnit<T>::R, H = V / R;
+        const int U0 = G0 * H, U1 = G1 * H;
+        for (int U = U0 + ((warp - U0 % kConsumerWarps + kConsumerWarps) % kConsumerWarps); U < U1;
+             U += kConsumerWarps) {
+          const int G = U / H, r0 = (U - G * H) * R;
+          const int nr = min(V, n - V * G) - r0;        // rows of this unit (R but in the last block-row)
+          if (nr <= 0) continue;
+          const uint32_t pitch = (uint32_t)(G + 1) * 16u;  // bytes per row: G + 1 vectors
+          const uint32_t row0 =
+              tile_addr + (uint32_t)(blk_off<V>(G, n) - base) * (uint32_t)sizeof(T) + (uint32_t)r0 * pitch;
+          uint32_t ad[K], st[K];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int g = gb + q * kConsumerWarps;
-            if (g < g1) {
-              const T* row = tile + (tri_off<V>(g) - base);
-              const int nvec = g / V + 1;
-              const Acc xg = xs[XL::index(g, 0)];
-#pragma unroll
-              for (int k = 0; k < K; ++k) {
-                const int vi = k * 32 + lane;
-                if (vi < nvec) {
-                  Acc a[V];
-                  Op<T>::load(row + (size_t)vi * V, a);
-                  const Acc* xb = xs + vi * XL::XB;
-#pragma unroll
-                  for (int uu = 0; uu < XL::U; ++uu) {
-                    Acc xq[XL::Q];
-                    load16(xb + uu * XL::Q, xq);
-#pragma unroll
-                    for (int jj = 0; jj < XL::Q; ++jj) acc[q] = fma(a[uu * XL::Q + jj], xq[jj], acc[q]);
-                  }
-#pragma unroll
-                  for (int v = 0; v < V; ++v) accT[k][v] = fma(a[v], xg, accT[k][v]);
-                }
-              }
-            }
+          for (int s = 0; s < K; ++s) {
+            const int j = 32 * s + lane;
+            ad[s] = j <= G ? row0 + 16u * (uint32_t)j : zero_addr;
+            st[s] = j <= G ? pitch : 0u;
           }
-          const Acc tot = warp_sum4(acc, lane);
-          const int g = gb + (lane >> 3) * kConsumerWarps;
-          if ((lane & 7) == 0 && g < g1) rowp[g] = (float)tot;
+          const float* xrow = xs + V * G + r0;          // zero beyond n
+          const int ns = min(K, G / 32 + 1);            // tile slots with a tile of this block-row
+          float rs[R];
+          if (nr >= R) {
+            if (K == 1 || ns == 1) sym_rows<T, K, 1, R, false>(ad, st, xrow, nr, xj, accT, rs);
+            else if (K == 2 || ns == 2) sym_rows<T, K, (K >= 2 ? 2 : 1), R, false>(ad, st, xrow, nr, xj, accT, rs);
+            else if (ns == 3) sym_rows<T, K, (K >= 3 ? 3 : 1), R, false>(ad, st, xrow, nr, xj, accT, rs);
+            else sym_rows<T, K, K, R, false>(ad, st, xrow, nr, xj, accT, rs);
+          } else {
+            sym_rows<T, K, K, R, true>(ad, st, xrow, nr, xj, accT, rs);   // last block-row: all slots (zero vectors beyond)
+          }
+          const float tot = warp_sum_rows<R>(rs, lane);
+          const int row = V * G + r0 + sym_row<R>(lane);
+          if ((lane & (32 / R - 1)) == 0 && row < n) rowp[row] = tot;
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
-      if (++slot == kStages) { slot = 0; phase ^= 1u; }
+      if (++slot == nst) { slot = 0; phase ^= 1u; }
     }
     // the warps' transposed partials, summed in warp order, plus the row sums
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+    for (int s = 0; s < K; ++s)
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int c = (k * 32 + lane) * V + v;
-        if (c < n) red[(size_t)warp * npad + c] = (float)accT[k][v];
+      for (int i = 0; i < P; i += 2) {   // 16-byte stores: two pairs each
+        const int c = (s * 32 + lane) * V + 2 * i;
+        if (c < npad) *reinterpret_cast<ulonglong2*>(red + (size_t)warp * npad + c) = make_ulonglong2(accT[s][i], accT[s][i + 1]);
       }
-    consumer_sync();
+    cp_async_wait_all();                      // this thread's copies of the next operand landed
+    consumer_sync();                          // A: partials and row sums written; xs no longer read
     if (!aborted)
       for (int c = tid; c < n; c += kCT) {
         float y = rowp[c];
@@ -704,30 +813,40 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
         const int64_t jy = (int64_t)w.yoff + c;
         Y[yscatter ? (int64_t)yscatter[jy] : jy] = (double)y;
       }
+    if (has_next) convert_operand();
+    consumer_sync();                          // B: xs complete; red, rowp and xraw free
+    if (u + 2 * (int)gridDim.x < n_items) prefetch_operand(u + 2 * gridDim.x);
   }
   cp_async_wait_all();
 }
 
-template <typename T>
-size_t sym_smem(int stage_bytes, int max_n) {
+template <typename T, int K>
+size_t sym_smem(int stage_bytes, int nst, int max_n) {
   constexpr int V = Op<T>::V;
   const int npad = (max_n + V - 1) / V * V;
-  return (size_t)kStages * stage_bytes + XLayout<typename Op<T>::Acc, V, 1>::bytes(npad) + (size_t)npad * 8 +
-         (size_t)npad * 4 * (1 + kConsumerWarps) + 2 * kStages * sizeof(uint64_t);
+  return (size_t)nst * stage_bytes + (size_t)32 * K * V * 4 + (size_t)npad * (8 + 4 + 4 * kConsumerWarps) +
+         2 * (size_t)nst * sizeof(uint64_t);
+}
+
+// Bytes of the widest block-row (V rows of the longest row), rounded up to
+// 128: the smallest stage.
+template <typename T>
+int64_t sym_min_stage(int max_n) {
+  constexpr int V = Op<T>::V;
+  const int64_t q = (max_n + V - 1) / V;
+  return (q * V * V * (int64_t)sizeof(T) + 127) / 128 * 128;
 }
 
 template <typename T, int K>
 cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* arena, const double* X, double* Y,
-                    const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb, int max_per_sm) {
-  constexpr int V = Op<T>::V;
-  // a stage holds at least one whole row (the longest: max_n padded), and
-  // the block's shared memory stays within kSymSmemCap
-  const int64_t row = (int64_t)((max_n + V - 1) / V * V) * (int64_t)sizeof(T);
-  const int64_t row128 = (row + 127) / 128 * 128;
-  const int64_t room = ((int64_t)kSymSmemCap - (int64_t)sym_smem<T>(0, max_n)) / kStages / 128 * 128;
+                    const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb, int nst, int max_per_sm) {
+  // a stage holds at least one whole block-row (the widest), and the
+  // block's shared memory stays within kSymSmemCap
+  const int64_t minst = sym_min_stage<T>(max_n);
+  const int64_t room = ((int64_t)kSymSmemCap - (int64_t)sym_smem<T, K>(0, nst, max_n)) / nst / 128 * 128;
   const int64_t want = ((int64_t)stage_kb * 1024 + 127) / 128 * 128;
-  const int stage_bytes = (int)std::max<int64_t>(row128, std::min<int64_t>(want, room));
-  const size_t smem = sym_smem<T>(stage_bytes, max_n);
+  const int stage_bytes = (int)std::max<int64_t>(minst, std::min<int64_t>(want, room));
+  const size_t smem = sym_smem<T, K>(stage_bytes, nst, max_n);
   if (smem > (size_t)kSymSmemCap) return cudaErrorInvalidValue;
   auto kern = k_sgemv_tma<T, K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -738,22 +857,22 @@ cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* aren
   per_sm = std::max(1, per_sm);
   if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
   const int grid = std::max(1, std::min(n_items, num_sms() * per_sm));
-  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, max_n, err);
+  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, nst, max_n, err);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t dispatch_sym(const WorkItem* items, int n_items, int max_n, const void* arena, const double* X,
                          double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb,
-                         int max_per_sm) {
+                         int nst, int max_per_sm) {
   constexpr int V = Op<T>::V;
   const T* A = static_cast<const T*>(arena);
   if (max_n <= 32 * V)
-    return run_sym<T, 1>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+    return run_sym<T, 1>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   if (max_n <= 64 * V)
-    return run_sym<T, 2>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+    return run_sym<T, 2>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   if (max_n <= kSymK * 32 * V)
-    return run_sym<T, kSymK>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+    return run_sym<T, kSymK>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   return cudaErrorInvalidValue;
 }
 
@@ -776,22 +895,24 @@ bool sgemv_tma_supported(int precision, int max_n) {
   if (precision != BDDC_PREC_FP32 && precision != BDDC_PREC_BF16) return false;
   const int V = precision == BDDC_PREC_FP32 ? 4 : 8;
   if (max_n > kSymK * 32 * V) return false;
-  // the smallest stage: one whole row
-  const size_t row = ((size_t)((max_n + V - 1) / V * V) * (precision == BDDC_PREC_FP32 ? 4 : 2) + 127) / 128 * 128;
-  const size_t smem = precision == BDDC_PREC_FP32 ? sym_smem<float>((int)row, max_n)
-                                                  : sym_smem<__nv_bfloat16>((int)row, max_n);
+  // the smallest stage: one whole block-row
+  const size_t smem = precision == BDDC_PREC_FP32
+                          ? sym_smem<float, kSymK>((int)sym_min_stage<float>(max_n), kSymStages, max_n)
+                          : sym_smem<__nv_bfloat16, kSymK>((int)sym_min_stage<__nv_bfloat16>(max_n), kSymStages, max_n);
   return smem <= (size_t)kSymSmemCap;
 }
 
 cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
-                             int stage_kb, int max_per_sm) {
+                             int stage_kb, int n_stages, int max_per_sm) {
   if (n_items == 0) return cudaSuccess;
-  if (stage_kb < 1 || stage_kb > 48) return cudaErrorInvalidValue;
+  if (stage_kb < 1 || stage_kb > 48 || n_stages < kSymMinStages || n_stages > kSymMaxStages)
+    return cudaErrorInvalidValue;
   if (precision == BDDC_PREC_FP32)
-    return dispatch_sym<float>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, max_per_sm);
+    return dispatch_sym<float>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, n_stages,
+                               max_per_sm);
   if (precision == BDDC_PREC_BF16)
-    return dispatch_sym<__nv_bfloat16>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb,
+    return dispatch_sym<__nv_bfloat16>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, n_stages,
                                        max_per_sm);
   return cudaErrorInvalidValue;
 }

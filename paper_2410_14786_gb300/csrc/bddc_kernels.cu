@@ -455,9 +455,9 @@ cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y
     if (nrhs != 1) return cudaErrorInvalidValue;   // nrhs_max is 1 on this path
     h->launches += (interior ? h->n_wsy_I : h->n_wsy_G) > 0;
     return interior ? launch_sgemv_tma(h->precision, h->d_wsy_I, h->n_wsy_I, h->max_n_I, h->d_aii, X, Y, yscatter,
-                                       h->d_err, st, h->tune_stage_kb[0], max_per_sm)
+                                       h->d_err, st, h->tune_stage_kb[0], h->tune_sym_stages[0], max_per_sm)
                     : launch_sgemv_tma(h->precision, h->d_wsy_G, h->n_wsy_G, h->max_n_G, h->d_kgg, X, Y, yscatter,
-                                       h->d_err, st, h->tune_stage_kb[1], max_per_sm);
+                                       h->d_err, st, h->tune_stage_kb[1], h->tune_sym_stages[1], max_per_sm);
   }
   h->launches += (interior ? h->n_wi_I : h->n_wi_G) > 0;
   if (h->use_tma)

@@ -197,6 +197,7 @@ struct bddc_handle_s {
   bool use_graph = true;
   // launch parameters chosen by the autotuner (or set by the caller)
   int tune_stage_kb[2] = {12, 12};   // streamed GEMV stage size: interior, interface operators
+  int tune_sym_stages[2] = {4, 4};   // stages of the symmetric GEMV: interior, interface operators
   int tune_tile_class[2] = {1, 1};   // streamed GEMV row tile 64 << class: interior, interface
   int tune_coarse_rb_min = 16;       // row-blocked coarse sweeps from this many right-hand sides on
   int tune_overlap = 0;              // interface operator concurrent with the coarse residual and solve

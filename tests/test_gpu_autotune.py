@@ -35,8 +35,11 @@ def test_autotune_one_rhs_is_bitwise_neutral():
     r = _r(g.n_nodes, 1, 101)
     z0 = g.apply(r).clone()
     t = g.autotune()
-    assert t["gemv_stage_kb_interior"] in (6, 12, 24, 48)
-    assert t["gemv_stage_kb_interface"] in (6, 12, 24, 48)
+    # one right-hand side in bf16: the symmetric GEMV, tuned over (stages, stage size)
+    assert g.info()["symmetric_operators"] == 1
+    assert t["gemv_stage_kb_interior"] in (10, 12, 16, 20, 24)
+    assert t["gemv_stage_kb_interface"] in (10, 12, 16, 20, 24)
+    assert t["sym_stages_interior"] in (3, 4) and t["sym_stages_interface"] in (3, 4)
     assert t["gemv_rows_interior"] in (64, 128, 256) and t["gemv_rows_interface"] in (64, 128, 256)
     assert g.get_tuning() == t
     z1 = g.apply(r)
@@ -64,7 +67,8 @@ def test_set_tuning_rejects_out_of_range():
     g = BDDC.from_problem(_p())
     before = g.get_tuning()
     for bad in ({"gemv_stage_kb_interior": 0}, {"gemv_stage_kb_interface": 65}, {"coarse_rowblock_min_nrhs": 1},
-                {"gemv_rows_interior": 100}, {"coarse_overlap": 2}):
+                {"gemv_rows_interior": 100}, {"coarse_overlap": 2}, {"sym_stages_interior": 5},
+                {"sym_stages_interface": 2}):
         t = dict(before)
         t.update(bad)
         with pytest.raises(BDDCError):
