@@ -267,7 +267,9 @@ def run_gb300(args):
                               tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores]
                               if prec in ("bf16", "tf32") else "auto")
         handles[prec] = g
-        forms[prec] = {"setup_s": g.info()["setup_seconds"]}
+        gi = g.info()
+        forms[prec] = {"setup_s": gi["setup_seconds"], "tensor_cores": gi["tensor_cores"],
+                       "runs_as": ["fp64", "fp32", "bf16", "tf32"][gi["precision"]]}
         if not args.no_autotune:
             # launch parameters measured on this handle (part of setup, untimed)
             t0 = time.perf_counter()

@@ -81,9 +81,12 @@ extern "C" {
                                (tcgen05 kind::tf32), float32 accumulation */
 
 /* Where the local and interior operators run. AUTO: tensor cores (tcgen05,
- * operators stored in the MMA tile layout) for TF32, and for BF16 when
- * nrhs_max >= 8; the streamed CUDA-core GEMV otherwise. ON: tensor cores
- * for BF16 and TF32 whatever nrhs_max. OFF: CUDA cores (invalid with TF32).
+ * operators stored in the MMA tile layout) for BF16 and TF32 when nrhs_max
+ * >= 8, the streamed CUDA-core GEMV otherwise; below 8 right-hand sides a
+ * TF32 request runs the FP32 form (float32 operators on the CUDA cores, as
+ * BDDC_PREC_FP32), because an MMA of N = 16 would waste most of its work:
+ * bddc_info_t.precision then reports BDDC_PREC_FP32. ON: tensor cores for
+ * BF16 and TF32 whatever nrhs_max. OFF: CUDA cores (invalid with TF32).
  * On the tensor cores the float64 operand is split into a high and a low
  * part in the operator's format (two MMAs per K step), so only the operator
  * carries the form's rounding. */
@@ -158,7 +161,8 @@ typedef struct {
     int64_t coarse_update_total;        /* sum of the coarse supernodes' update-set sizes */
     int64_t coarse_levels;              /* levels of the coarse elimination tree (0: dense) */
     double setup_seconds;               /* wall time of bddc_setup */
-    int32_t precision;
+    int32_t precision;                  /* the precision the operators run in (BDDC_PREC_*; see
+                                           BDDC_TC_AUTO for TF32 at few right-hand sides) */
     int32_t error_subdomain;            /* subdomain of the last SINGULAR error, else -1 */
     int32_t device_error;               /* BDDC_ERR_TIMEOUT if a bounded device wait of an
                                            earlier call ran out, else 0 (bddc_query synchronises) */

@@ -55,12 +55,19 @@ cudaError_t upload(bddc_handle_s* h, T** p, const std::vector<T>& v) {
   return e;
 }
 
-// The local operators run on the tensor cores: TF32 always, BF16 when asked
-// or when blocks of at least kTcMinRhs right-hand sides are expected.
+// The local operators run on the tensor cores for BF16 and TF32 when asked,
+// or (AUTO) when blocks of at least kTcMinRhs right-hand sides are expected.
 bool tc_enabled(const bddc_options_t* O) {
-  return O->precision == BDDC_PREC_TF32 ||
-         (O->precision == BDDC_PREC_BF16 &&
-          (O->tensor_cores == BDDC_TC_ON || (O->tensor_cores == BDDC_TC_AUTO && O->nrhs_max >= kTcMinRhs)));
+  return (O->precision == BDDC_PREC_TF32 || O->precision == BDDC_PREC_BF16) &&
+         (O->tensor_cores == BDDC_TC_ON || (O->tensor_cores == BDDC_TC_AUTO && O->nrhs_max >= kTcMinRhs));
+}
+
+// The precision the operators are stored and applied in: a TF32 request
+// that AUTO keeps off the tensor cores (fewer than kTcMinRhs right-hand
+// sides, where an MMA of N = 16 would waste most of its work) runs the FP32
+// form on the CUDA cores.
+int effective_precision(const bddc_options_t* O) {
+  return O->precision == BDDC_PREC_TF32 && !tc_enabled(O) ? BDDC_PREC_FP32 : O->precision;
 }
 
 int elem_bytes(int precision) {
@@ -671,7 +678,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   bddc_handle_s* h = new (std::nothrow) bddc_handle_s();
   if (!h) return fail(BDDC_ERR_OOM, "handle allocation");
   h->dim = P->dim; h->ne = P->ne; h->n1 = P->ne + 1; h->n_sub = P->n_sub;
-  h->precision = O->precision; h->nrhs_max = O->nrhs_max; h->device = O->device;
+  h->precision = effective_precision(O); h->nrhs_max = O->nrhs_max; h->device = O->device;
   h->use_graph = O->no_graph == 0;
   h->phi_prec = (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
   h->use_tc = tc_enabled(O);
@@ -694,7 +701,7 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
     bddc_destroy(h);
     return fail(BDDC_ERR_CUDA, cudaGetErrorString(e));
   }
-  h->info.precision = O->precision;
+  h->info.precision = h->precision;
   h->info.error_subdomain = -1;
   h->info.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h;
@@ -732,7 +739,7 @@ int bddc_setup_inspect(const bddc_problem_t* P, const bddc_options_t* O, int32_t
     }
     for (int64_t n = 0; n < hs.n_nodes; ++n) info->n_interface_nodes += hs.kappa[n] >= 2;
     info->error_subdomain = -1;
-    info->precision = O->precision;
+    info->precision = effective_precision(O);
     info->phi_precision =
         (O->precision == BDDC_PREC_FP64 || O->phi_fp64) ? BDDC_PREC_FP64 : BDDC_PREC_FP32;
     info->tensor_cores = tc_enabled(O) ? 1 : 0;

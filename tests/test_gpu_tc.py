@@ -91,7 +91,7 @@ def test_tc_tf32_apply_error_bound(name):
     # operators read as TF32 (u = 2^-10 or 2^-11), operand split hi + lo in
     # float32 (about 2^-21), float32 accumulation over n <= 729 terms
     p, mask, o = _case(name)
-    g = _bddc(p, mask, precision="tf32", nrhs_max=4)
+    g = _bddc(p, mask, precision="tf32", nrhs_max=4, tensor_cores=True)
     assert g.info()["tensor_cores"] == 1
     r = synth.uniform(41, o.n_nodes * 3).reshape(o.n_nodes, 3)
     r[o.dir] = 0
@@ -138,3 +138,24 @@ def test_tc_pcg_many_rhs():
     assert abs(int(res.iters[7]) - int(r7.iters[0])) <= 1
     xs = o.pcg(o.rhs(f[:, [7]]), 1e-10)[0][:, 0]
     assert np.linalg.norm(X[:, 7].cpu().numpy() - xs) / np.linalg.norm(xs) < 1e-6
+
+
+@pytest.mark.parametrize("nrhs_max", [1, 4])
+def test_tf32_auto_below_eight_rhs_runs_the_fp32_form(nrhs_max):
+    """AUTO keeps TF32 off the tensor cores below 8 right-hand sides: the
+    handle stores and applies float32 operators on the CUDA cores, exactly
+    what the FP32 form does (bitwise the same apply and solve)."""
+    p, mask, o = _case("3d_24_3cubed")
+    gt = _bddc(p, mask, precision="tf32", nrhs_max=nrhs_max)
+    gf = _bddc(p, mask, precision="fp32", nrhs_max=nrhs_max)
+    it, jf = gt.info(), gf.info()
+    assert it["tensor_cores"] == 0 and it["precision"] == 1
+    assert it["symmetric_operators"] == jf["symmetric_operators"]
+    r = synth.uniform(44, o.n_nodes * nrhs_max).reshape(o.n_nodes, nrhs_max)
+    r[o.dir] = 0
+    R = _cuda(r if nrhs_max > 1 else r[:, 0])
+    assert torch.equal(gt.apply(R), gf.apply(R))
+    b = _cuda(o.rhs(p.f[:, 0]))
+    xt, rt = gt.pcg_solve(b, rtol=1e-8)
+    xf, rf = gf.pcg_solve(b, rtol=1e-8)
+    assert rt.status == 0 and list(rt.iters) == list(rf.iters) and torch.equal(xt, xf)

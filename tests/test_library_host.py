@@ -169,12 +169,13 @@ def test_phi_precision_follows_the_form(L, precision, phi_fp64, expect):
     assert info.phi_precision == expect
 
 
-@pytest.mark.parametrize("precision,tc,nrhs_max,expect", [
-    (2, 0, 1, 0), (2, 0, 4, 0), (2, 0, 8, 1), (2, 1, 1, 1), (2, 2, 64, 0), (3, 0, 1, 1), (3, 1, 8, 1),
-    (1, 0, 64, 0)])
-def test_tensor_core_selection(L, precision, tc, nrhs_max, expect):
-    """TF32 always runs on the tensor cores; BF16 from 8 right-hand sides or
-    when asked; FP32 / FP64 on CUDA cores."""
+@pytest.mark.parametrize("precision,tc,nrhs_max,expect,runs_as", [
+    (2, 0, 1, 0, 2), (2, 0, 4, 0, 2), (2, 0, 8, 1, 2), (2, 1, 1, 1, 2), (2, 2, 64, 0, 2), (3, 0, 1, 0, 1),
+    (3, 0, 7, 0, 1), (3, 0, 8, 1, 3), (3, 1, 1, 1, 3), (3, 1, 8, 1, 3), (1, 0, 64, 0, 1)])
+def test_tensor_core_selection(L, precision, tc, nrhs_max, expect, runs_as):
+    """BF16 and TF32 run on the tensor cores from 8 right-hand sides or when
+    asked; below 8 a TF32 request under AUTO runs the FP32 form on the CUDA
+    cores (the reported precision says so); FP32 / FP64 on CUDA cores."""
     from paper_2410_14786_gb300 import _lib
     prob, opts, keep = _structs(synth.config(1), precision=precision, nrhs_max=nrhs_max)
     opts.tensor_cores = tc
@@ -182,6 +183,7 @@ def test_tensor_core_selection(L, precision, tc, nrhs_max, expect):
     rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0)
     assert rc == 0, L.bddc_last_error()
     assert info.tensor_cores == expect
+    assert info.precision == runs_as
 
 
 @pytest.mark.parametrize("precision,tc", [(3, 2), (0, 1), (1, 1), (2, 3), (4, 0)])
