@@ -21,6 +21,7 @@ Plain, slow and literal, in float64:
     local correction v2 (Eq. localsubdomain), r1 = r - A (v1 + v2) with the
     global A, interior correction v3 (Eq. inner).
   * PCG from the static-condensation start x0 = P_I b, standard or flexible.
+  * Optionally the coarse system solved inexactly by plain CG (Sec. 3).
 
 Readings where the paper is silent (each is listed with its reason in the
 design notes): Dirichlet nodes are eliminated; b = M f; globs are classes of
@@ -339,7 +340,45 @@ class Oracle:
         return rc
 
     def coarse_solve(self, rc: np.ndarray) -> np.ndarray:
+        """u_c = A_c^-1 r_c: a sparse direct solve, or, after set_coarse_cg,
+        the inexact solve by plain CG."""
+        cg = getattr(self, "coarse_cg", None)
+        if cg is not None and self.n_c:
+            return self.coarse_solve_cg(rc, *cg)[0]
         return self.Ac_lu.solve(rc) if self.n_c else rc.copy()
+
+    def set_coarse_cg(self, rtol, maxit=10000):
+        """Solve the coarse system of Eq. coarsegrid inexactly by plain CG
+        (Sec. 3, implementation paragraph: the coarse system is solved with a
+        plain CG solver) to ||r_k|| <= rtol ||r_c||; None restores the direct
+        solve."""
+        self.coarse_cg = None if rtol is None else (float(rtol), int(maxit))
+
+    def coarse_solve_cg(self, rc: np.ndarray, rtol: float, maxit: int = 10000):
+        """Plain (unpreconditioned) conjugate gradients on A_c u = r_c from
+        u_0 = 0: alpha_k = rho_k / p_k^T A_c p_k, u += alpha p, r -= alpha A_c p,
+        beta_k = rho_k+1 / rho_k, p = r + beta p, with rho = r^T r; stops
+        before an iteration when ||r_k||_2 <= rtol ||r_c||_2 (or after maxit).
+        Returns u, the iteration count and the residual norms ||r_k||."""
+        A = self.Ac
+        u = np.zeros_like(rc)
+        r = np.array(rc, dtype=np.float64)
+        p = r.copy()
+        rho = float(r @ r)
+        tol = rtol * math.sqrt(rho)
+        norms = [math.sqrt(rho)]
+        it = 0
+        while it < maxit and math.sqrt(rho) > tol:
+            q = A @ p
+            alpha = rho / float(p @ q)
+            u = u + alpha * p
+            r = r - alpha * q
+            rho_new = float(r @ r)
+            p = r + (rho_new / rho) * p
+            rho = rho_new
+            it += 1
+            norms.append(math.sqrt(rho))
+        return u, it, norms
 
     def local_solve(self, i: int, yi: np.ndarray):
         """Eq. compzi: [A_i C_i^T; C_i 0][z_i; lambda_i] = [y_i; 0]."""

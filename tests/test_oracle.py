@@ -340,3 +340,57 @@ def test_zero_rhs_column():
     x, h = o.pcg(b, 1e-8)
     assert h[0]["iters"] == 0 and np.all(x[:, 0] == 0)
     assert h[1]["converged"]
+
+
+# ---------------------------------------------- inexact coarse solve (Sec. 3)
+# The paper solves the coarse system of Eq. coarsegrid with plain CG. Pins of
+# the oracle's CG: properties the method has whatever the matrix.
+def _energy(A, e):
+    return float(np.sqrt(e @ (A @ e)))
+
+
+def test_coarse_cg_energy_error_decreases_and_residuals_are_true(small3d):
+    p, o = small3d
+    rc = o.coarse_residual(o.to_free(o.rhs(p.f[:, 0])))
+    u_star = o.Ac_lu.solve(rc)
+    errs = []
+    for k in range(0, 25):
+        u, it, norms = o.coarse_solve_cg(rc, 0.0, maxit=k)
+        assert it == k
+        errs.append(_energy(o.Ac, u - u_star))
+        # the recursively updated residual norm is the true one
+        assert abs(norms[-1] - np.linalg.norm(rc - o.Ac @ u)) <= 1e-10 * np.linalg.norm(rc)
+    # CG minimises the A-norm error over the Krylov space: strictly decreasing
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_coarse_cg_finite_termination_and_stop_test(cfg1):
+    p, o = cfg1
+    assert o.n_c == 33
+    rc = o.coarse_residual(o.to_free(o.rhs(p.f[:, 0])))
+    u_star = o.Ac_lu.solve(rc)
+    u, it, norms = o.coarse_solve_cg(rc, 1e-13)
+    # exact in at most n_c steps in exact arithmetic; a few more in float64
+    assert it <= o.n_c + 5
+    assert np.linalg.norm(u - u_star) <= 1e-10 * np.linalg.norm(u_star)
+    assert norms[-1] <= 1e-13 * norms[0] < norms[-2]
+    u0, it0, _ = o.coarse_solve_cg(np.zeros_like(rc), 1e-8)
+    assert it0 == 0 and not u0.any()
+
+
+def test_pcg_with_inexact_coarse_solve(small3d):
+    p, o = small3d
+    b = o.rhs(p.f[:, 0])
+    x_ref, h_ref = o.pcg(b, 1e-8)
+    try:
+        o.set_coarse_cg(1e-13)      # tight: the same preconditioner up to rounding
+        x1, h1 = o.pcg(b, 1e-8, flexible=True)
+        o.set_coarse_cg(1e-4)       # loose: the flexible iteration still converges
+        x2, h2 = o.pcg(b, 1e-8, flexible=True)
+    finally:
+        o.set_coarse_cg(None)
+    assert h1[0]["iters"] == h_ref[0]["iters"]
+    assert np.abs(x1 - x_ref).max() < 1e-9 * np.abs(x_ref).max()
+    assert h2[0]["converged"] and h2[0]["iters"] <= h_ref[0]["iters"] + 5
+    xs = spla.spsolve(o.A.tocsc(), o.to_free(b))
+    assert np.linalg.norm(o.to_free(x2) - xs) / np.linalg.norm(xs) < 1e-6
