@@ -263,7 +263,7 @@ def run_gb300(args):
     precs = ["fp64", "fp32", "tf32", "bf16"] if not args.only else args.only.split(",")
     headline = args.precision if args.precision in precs else precs[-1]
     for prec in precs:
-        g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs, graph=not args.no_graph,
+        g = BDDC.from_problem(p, precision=prec, nrhs_max=nrhs, graph=not args.no_graph, coarse=args.coarse,
                               tensor_cores={"auto": "auto", "on": True, "off": False}[args.tensor_cores]
                               if prec in ("bf16", "tf32") else "auto")
         handles[prec] = g
@@ -310,6 +310,8 @@ def run_gb300(args):
         tr = float(((b - g64.matvec(x)).norm() / b.norm()).item())
         forms[prec].update({"ms_per_solve": ms, "iters": iters[-1], "true_relres": tr,
                             "launches_per_solve": launches / args.steps})
+        if args.coarse == "cg":
+            forms[prec]["coarse_cg_iters_last"] = g.info()["coarse_cg_iters"]
         if prec == "fp64":
             x_ref = x.clone()
         elif x_ref is not None:
@@ -598,6 +600,8 @@ def main():
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling aid: set up the headline form, run this many applies and one solve, exit")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 192^3 workload (forms_cfg5)")
+    ap.add_argument("--coarse", default="auto", choices=["auto", "sparse", "dense", "cg"],
+                    help="development aid: coarse solve (auto = sparse factorisation; cg = inexact, by plain CG)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker:

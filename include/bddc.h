@@ -94,14 +94,21 @@ extern "C" {
 #define BDDC_TC_ON   1
 #define BDDC_TC_OFF  2
 
-/* Coarse solve (always exact, float64). DENSE: the explicit inverse of A_c,
- * applied as one matrix-vector product (n_c^2 float64 multiply-adds).
- * SPARSE: a nested-dissection supernodal Cholesky factorisation applied by
+/* Coarse solve (float64). DENSE: the explicit inverse of A_c, applied as
+ * one matrix-vector product (n_c^2 float64 multiply-adds). SPARSE: a
+ * nested-dissection supernodal Cholesky factorisation applied by
  * level-scheduled sweeps (far fewer operations and bytes; needed when the
- * dense inverse does not fit). AUTO = SPARSE. */
+ * dense inverse does not fit). AUTO = SPARSE. Both are exact. CG: the
+ * paper's choice (Sec. 3: the coarse system of Eq. coarsegrid solved with
+ * plain CG): unpreconditioned conjugate gradients on A_c from u_c = 0, every
+ * column until ||r_k|| <= coarse_cg_rtol ||r_c|| or coarse_cg_maxit
+ * iterations, in one cooperative launch; no coarse factorisation at setup.
+ * The preconditioner is then inexact (it varies with r), so bddc_pcg_solve
+ * runs flexible PCG in every precision. */
 #define BDDC_COARSE_AUTO    0
 #define BDDC_COARSE_DENSE   1
 #define BDDC_COARSE_SPARSE  2
+#define BDDC_COARSE_CG      3
 
 /* Constraint families that become coarse (primal) dofs (Sec. 2). */
 #define BDDC_CORNERS 1u
@@ -139,6 +146,10 @@ typedef struct {
                               symmetric streamed GEMV; elsewhere in full */
     int32_t history;       /* PCG iterations whose scalars (||r_k||, alpha_k, beta_k) the
                               handle keeps for bddc_pcg_history, 0..100000; 0 = none */
+    int32_t coarse_cg_maxit; /* BDDC_COARSE_CG: iteration limit of the coarse CG, >= 0;
+                              0 = 2000 */
+    double coarse_cg_rtol; /* BDDC_COARSE_CG: relative residual at which the coarse CG
+                              stops, in [0, 1); 0 = 1e-10 */
 } bddc_options_t;
 
 typedef struct {
@@ -173,6 +184,9 @@ typedef struct {
                                            replays one captured iteration at a time or launches
                                            directly */
     int32_t symmetric_operators;        /* 1 if A_II^-1 and K_GG are stored as lower triangles */
+    int32_t coarse_cg_iters;            /* BDDC_COARSE_CG: most coarse CG iterations over the columns
+                                           of the most recent coarse solve (bddc_query synchronises);
+                                           0 otherwise */
 } bddc_info_t;
 
 /* Build the preconditioner (Sec. 2: the subdomain matrices A_i of A = sum
@@ -210,7 +224,8 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * + 2 sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
  * the dense coarse solve and 2 n_c for the sparse one
  * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
- * larger problems get BDDC_ERR_INVALID_ARG. The driver places the array in
+ * larger problems get BDDC_ERR_INVALID_ARG, and so do handles set up with
+ * BDDC_COARSE_CG (its work vectors are not relocated). The driver places the array in
  * the device's memory when it loads the library's device code on that device:
  * under CUDA's default lazy module loading that happens in the first call on
  * the device (8 MiB less free memory from then on), with

@@ -19,7 +19,7 @@ from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64, PREC_
 
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16, "tf32": PREC_TF32}
 TENSOR_CORES = {"auto": _lib.TC_AUTO, True: _lib.TC_ON, False: _lib.TC_OFF}
-COARSE = {"auto": _lib.COARSE_AUTO, "dense": _lib.COARSE_DENSE, "sparse": _lib.COARSE_SPARSE}
+COARSE = {"auto": _lib.COARSE_AUTO, "dense": _lib.COARSE_DENSE, "sparse": _lib.COARSE_SPARSE, "cg": _lib.COARSE_CG}
 
 
 @dataclass
@@ -66,13 +66,15 @@ class BDDC:
     symmetric local operators in full where they would otherwise be stored
     as lower triangles (fp32 / bf16 on the CUDA cores with nrhs_max = 1);
     history: PCG iterations whose scalars (||r_k||, alpha_k, beta_k) the
-    handle keeps for `pcg_history()` (0 = none).
+    handle keeps for `pcg_history()` (0 = none); coarse="cg" solves the
+    coarse system inexactly by plain CG (the paper's choice) to
+    coarse_cg_rtol (0: 1e-10) within coarse_cg_maxit iterations (0: 2000).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
                  phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None, coarse_blocks=0,
-                 full_operators=False, history=0):
+                 full_operators=False, history=0, coarse_cg_rtol=0.0, coarse_cg_maxit=0):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -86,7 +88,8 @@ class BDDC:
                             int(constraints), int(nrhs_max), int(n_threads), int(device),
                             COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
                             1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores], int(coarse_blocks),
-                            1 if full_operators else 0, int(history))
+                            1 if full_operators else 0, int(history), int(coarse_cg_maxit),
+                            float(coarse_cg_rtol))
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim

@@ -24,7 +24,7 @@ ERR_NO_DEVICE = -7
 PREC_FP64, PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3
 TC_AUTO, TC_ON, TC_OFF = 0, 1, 2
 CORNERS, EDGES, FACES = 1, 2, 4
-COARSE_AUTO, COARSE_DENSE, COARSE_SPARSE = 0, 1, 2
+COARSE_AUTO, COARSE_DENSE, COARSE_SPARSE, COARSE_CG = 0, 1, 2, 3
 
 EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
                 ("no_graph", C.c_int32), ("phi_fp64", C.c_int32),
                 ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32), ("full_operators", C.c_int32),
-                ("history", C.c_int32)]
+                ("history", C.c_int32), ("coarse_cg_maxit", C.c_int32), ("coarse_cg_rtol", C.c_double)]
 
 
 class Info(C.Structure):
@@ -64,7 +64,8 @@ class Info(C.Structure):
         "coarse_factor_entries", "coarse_update_total", "coarse_levels")] + [
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
         ("device_error", C.c_int32), ("phi_precision", C.c_int32),
-        ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32), ("symmetric_operators", C.c_int32)]
+        ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32), ("symmetric_operators", C.c_int32),
+        ("coarse_cg_iters", C.c_int32)]
 
 
 class BDDCError(RuntimeError):

@@ -228,7 +228,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   // the device (r_c, u_c and the factor then share one order, and the sweeps
   // read and write contiguous runs); cperm maps a glob to that number
   std::vector<int32_t> cperm;
-  if (hs.n_c && !hs.coarse_dense) {
+  if (hs.n_c && !hs.coarse_dense && !hs.coarse_cg) {
     coarse_renumber(hs.cfac, cperm);
     for (auto& c : ccdof) c = cperm[c];
   }
@@ -424,7 +424,22 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     }
   }
   h->coarse_dense = hs.coarse_dense;
-  if (hs.n_c && hs.coarse_dense) {
+  h->coarse_cg = hs.coarse_cg;
+  if (hs.n_c && hs.coarse_cg) {
+    // A_c in CSR (both triangles, glob order) for the coarse CG; one block
+    // per SM (cooperative launch)
+    std::vector<int32_t> acp(hs.Ac_ptr.begin(), hs.Ac_ptr.end());
+    CUDA_TRY(upload(h, &h->d_acp, acp));
+    CUDA_TRY(upload(h, &h->d_acc, hs.Ac_col));
+    CUDA_TRY(upload(h, &h->d_acv, hs.Ac_val));
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&h->c_sms, cudaDevAttrMultiProcessorCount, dev));
+    h->c_nnz = (int64_t)hs.Ac_val.size();
+    CUDA_TRY(build_coarse_cg_device(h));
+    in_coarse_bytes = h->c_nnz * 12 + (hs.n_c + 1) * 4;
+    coarse_read_1rhs = in_coarse_bytes;   // one product with A_c (per coarse CG iteration)
+  } else if (hs.n_c && hs.coarse_dense) {
     // A_c^-1, float64, stored as column panels of kPanel columns (each an
     // n_c x width row-major block, blocks aligned to 256 bytes); the panels'
     // partial products are summed by a separate kernel
@@ -521,6 +536,12 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     CUDA_TRY(dev_alloc(h, &h->w_cr, h->n_c * R));
     CUDA_TRY(dev_alloc(h, &h->w_cy, h->n_c * R));
   }
+  if (h->coarse_cg) {
+    CUDA_TRY(dev_alloc(h, &h->w_cq, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->d_cgpart, (size_t)std::max(1, h->c_sms) * 2 * R));
+    CUDA_TRY(dev_alloc(h, &h->d_cgiters, (size_t)R));
+    CUDA_TRY(cudaMemset(h->d_cgiters, 0, sizeof(int32_t) * R));
+  }
   CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   const int64_t NV = h->n_nodes * R;
@@ -579,7 +600,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   in.n_interface_copies = h->nG_tot;
   in.coarse_factor_entries = h->c_nnz;
   in.coarse_update_total = h->c_update_total;
-  in.coarse_levels = h->coarse_dense ? 0 : h->c_levels;
+  in.coarse_levels = h->coarse_dense || h->coarse_cg ? 0 : h->c_levels;
   ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
   in.phi_precision = h->phi_prec;
   in.apply_bytes_1rhs = ops + 2 * (int64_t)elem_bytes(h->phi_prec) * in.sum_nG_nc + coarse_read_1rhs +
@@ -685,6 +706,8 @@ int bddc_setup(const bddc_problem_t* P, const bddc_options_t* O, bddc_handle_t* 
   h->g_blocks = O->coarse_blocks;
   h->full_operators = O->full_operators != 0;
   h->hist_cap = O->history;
+  h->cg_maxit = O->coarse_cg_maxit > 0 ? O->coarse_cg_maxit : 2000;
+  h->cg_rtol = O->coarse_cg_rtol > 0.0 ? O->coarse_cg_rtol : 1e-10;
   h->n_nodes = hs.n_nodes; h->n_elems = hs.n_elems; h->h = hs.h;
   rc = build_device(h, hs, P);
   if (rc != BDDC_OK) {
@@ -759,6 +782,12 @@ int bddc_query(bddc_handle_t h, bddc_info_t* info) {
   h->info.solve_graph = h->use_graph && !h->solve_graph_unsupported ? 1 : 0;
   ENTER_DEVICE(h->device);
   CUDA_TRY(cudaMemcpy(&h->info.device_error, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  h->info.coarse_cg_iters = 0;
+  if (h->d_cgiters) {
+    std::vector<int32_t> it(h->nrhs_max);
+    CUDA_TRY(cudaMemcpy(it.data(), h->d_cgiters, sizeof(int32_t) * h->nrhs_max, cudaMemcpyDeviceToHost));
+    h->info.coarse_cg_iters = *std::max_element(it.begin(), it.end());
+  }
   *info = h->info;
   return BDDC_OK;
 }
@@ -1000,7 +1029,9 @@ static int pcg_finish(bddc_handle_t h, int nrhs, int32_t* iters, double* relres,
 
 static int pcg_core(bddc_handle_t h, const double* b, double* x, int nrhs, double rtol, int maxit,
                     int32_t* iters, double* relres, cudaStream_t st) {
-  const int flexible = h->precision != BDDC_PREC_FP64;
+  // flexible PCG for the low-precision operators and for the inexact coarse
+  // solve (a preconditioner that varies with r)
+  const int flexible = h->precision != BDDC_PREC_FP64 || h->coarse_cg;
   int32_t* hf = h->h_flags;
   const int R = h->nrhs_max;
   auto read_flags = [&]() -> int {
@@ -1245,7 +1276,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
       (interior ? t.sym_stages_interior : t.sym_stages_interface) = best_ns;
     }
   }
-  if (h->n_c && !h->coarse_dense && nrhs >= 2) {
+  if (h->n_c && !h->coarse_dense && !h->coarse_cg && nrhs >= 2) {
     CUDA_TRY(cudaMemsetAsync(h->w_rc, 0, sizeof(double) * h->n_c * nrhs, st));
     const int keep = h->tune_coarse_rb_min;
     h->tune_coarse_rb_min = nrhs;   // blocked

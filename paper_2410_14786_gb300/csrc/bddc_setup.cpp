@@ -72,7 +72,9 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
   if (O->tensor_cores == BDDC_TC_ON && (O->precision == BDDC_PREC_FP64 || O->precision == BDDC_PREC_FP32)) { err = "tensor cores run the BF16 and TF32 forms only"; return BDDC_ERR_INVALID_ARG; }
   if (O->nrhs_max < 1 || O->nrhs_max > 64) { err = "nrhs_max must be in [1, 64]"; return BDDC_ERR_INVALID_ARG; }
   if (O->constraints & ~7u) { err = "unknown constraint bits"; return BDDC_ERR_INVALID_ARG; }
-  if (O->coarse < BDDC_COARSE_AUTO || O->coarse > BDDC_COARSE_SPARSE) { err = "unknown coarse mode"; return BDDC_ERR_INVALID_ARG; }
+  if (O->coarse < BDDC_COARSE_AUTO || O->coarse > BDDC_COARSE_CG) { err = "unknown coarse mode"; return BDDC_ERR_INVALID_ARG; }
+  if (O->coarse_cg_maxit < 0) { err = "coarse_cg_maxit must be >= 0"; return BDDC_ERR_INVALID_ARG; }
+  if (!(O->coarse_cg_rtol >= 0.0 && O->coarse_cg_rtol < 1.0)) { err = "coarse_cg_rtol must be in [0, 1)"; return BDDC_ERR_INVALID_ARG; }
   if (O->coarse_blocks < 0) { err = "coarse_blocks must be >= 0"; return BDDC_ERR_INVALID_ARG; }
   if (O->full_operators != 0 && O->full_operators != 1) { err = "full_operators must be 0 or 1"; return BDDC_ERR_INVALID_ARG; }
   if (O->history < 0 || O->history > 100000) { err = "history must be in [0, 100000]"; return BDDC_ERR_INVALID_ARG; }
@@ -383,7 +385,10 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
       hs.Ac_ptr[g + 1] = (int64_t)hs.Ac_col.size();
     }
     hs.coarse_dense = O->coarse == BDDC_COARSE_DENSE;
-    if (factor_coarse && hs.coarse_dense) {
+    hs.coarse_cg = O->coarse == BDDC_COARSE_CG;
+    if (hs.coarse_cg) {
+      // the coarse CG works on A_c itself: nothing to factorise
+    } else if (factor_coarse && hs.coarse_dense) {
       hs.Acinv.assign((size_t)nC * nC, 0.0);
       for (int64_t r = 0; r < nC; ++r)
         for (int64_t j = hs.Ac_ptr[r]; j < hs.Ac_ptr[r + 1]; ++j) hs.Acinv[(size_t)r * nC + hs.Ac_col[j]] = hs.Ac_val[j];

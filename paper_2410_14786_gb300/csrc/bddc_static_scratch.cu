@@ -51,6 +51,9 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   if (!h) return bddc::set_last_error(BDDC_ERR_INVALID_ARG, "null handle");
   if (nrhs < 1 || nrhs > h->nrhs_max || !r || !z || r == z)
     return bddc::set_last_error(BDDC_ERR_INVALID_ARG, "bad nrhs or vector pointers");
+  if (h->coarse_cg)
+    return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
+                                "bddc_apply_static_scratch: the coarse CG mode is not supported; use bddc_apply");
   // slices: rI, tI, bI (interior), yG, zG, eG (interface copies), g, ucl
   // (local constraints), rc, uc (coarse), then the coarse solve's own
   // temporaries, each nrhs columns wide

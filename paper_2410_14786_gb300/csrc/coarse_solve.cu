@@ -564,6 +564,157 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
   }
 }
 
+
+// ---- inexact coarse solve: plain CG on A_c (all columns in lockstep) ---------------------
+//
+// One cooperative persistent launch per coarse solve. Rows of A_c (CSR, glob
+// order) are dealt over the grid's threads, one (row, column) pair per thread
+// step; every reduction is a per-block partial in a fixed slot, summed in
+// block order by every block after a grid barrier, so all blocks take the
+// same decisions (step lengths, stop test, loop count) and the result does
+// not depend on timing. Three barriers per iteration: after q = A_c p with
+// p.q, after the updates of u and r with r.r, and after the update of p.
+constexpr int kCgThreadsWide = 512, kCgThreadsNarrow = 256;
+constexpr int kCgMaxRhs = 64;
+
+struct CgArgs {
+  const int32_t* ptr;        // [n_c + 1]
+  const int32_t* col;
+  const double* val;
+  const double* rc;          // r_c, n_c x nrhs (dof-major, column fastest)
+  double* u;                 // u_c
+  double* r;                 // residual
+  double* p;                 // search direction
+  double* q;                 // A_c p
+  double* part;              // [grid][2][nrhs] block partial sums
+  int32_t* iters;            // [nrhs] iterations of this solve
+  unsigned int* bar;
+  int32_t* err;
+  int n_c, nrhs, maxit;
+  double rtol;
+  unsigned int bar_extra;
+  long long bar_cycles;
+};
+
+// The block's sums of s per column (thread t holds column t % nrhs) into
+// part[blockIdx.x][slot][k], in a fixed order.
+__device__ void cg_block_partial(double s, const CgArgs& a, int slot, double* red) {
+  const int t = threadIdx.x, per = blockDim.x / a.nrhs;
+  red[t] = t < per * a.nrhs ? s : 0.0;
+  __syncthreads();
+  if (t < a.nrhs) {
+    double v = 0.0;
+    for (int j = 0; j < per; ++j) v += red[j * a.nrhs + t];
+    a.part[((int64_t)blockIdx.x * 2 + slot) * a.nrhs + t] = v;
+  }
+  __syncthreads();
+}
+// Totals of a slot over all blocks, in block order, into tot[k] (shared).
+__device__ void cg_total(const CgArgs& a, int slot, double* tot) {
+  const int t = threadIdx.x;
+  if (t < a.nrhs) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(&a.part[((int64_t)b * 2 + slot) * a.nrhs + t]);
+    tot[t] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCgThreadsWide) k_coarse_cg(CgArgs a) {
+  __shared__ double red[kCgThreadsWide];
+  __shared__ double tot[kCgMaxRhs], rho[kCgMaxRhs], tol2[kCgMaxRhs], alpha[kCgMaxRhs], beta[kCgMaxRhs];
+  __shared__ int active[kCgMaxRhs], n_active;
+  const int nr = a.nrhs, per = blockDim.x / nr;
+  const int sub = threadIdx.x / nr, k = threadIdx.x - sub * nr;
+  const bool live = threadIdx.x < per * nr;
+  const int64_t stride = (int64_t)gridDim.x * per;
+  unsigned int epoch = 0;
+  // u = 0, r = p = r_c, and r.r
+  double s = 0.0;
+  if (live)
+    for (int64_t i = blockIdx.x * (int64_t)per + sub; i < a.n_c; i += stride) {
+      const int64_t e = i * nr + k;
+      const double v = a.rc[e];
+      a.u[e] = 0.0;
+      a.r[e] = v;
+      a.p[e] = v;
+      s = fma(v, v, s);
+    }
+  cg_block_partial(s, a, 0, red);
+  if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
+  cg_total(a, 0, tot);
+  if (threadIdx.x < nr) {
+    const int t = threadIdx.x;
+    rho[t] = tot[t];
+    tol2[t] = a.rtol * a.rtol * tot[t];
+    active[t] = tot[t] > tol2[t] ? 1 : 0;   // a zero column takes no iteration
+    if (blockIdx.x == 0) a.iters[t] = 0;
+  }
+  if (threadIdx.x == 0) n_active = 0;
+  __syncthreads();
+  if (threadIdx.x < nr && active[threadIdx.x]) atomicAdd(&n_active, 1);
+  __syncthreads();
+  for (int it = 0; it < a.maxit && n_active > 0; ++it) {
+    // q = A_c p and p.q
+    s = 0.0;
+    if (live)
+      for (int64_t i = blockIdx.x * (int64_t)per + sub; i < a.n_c; i += stride) {
+        double acc = 0.0;
+        const int j1 = a.ptr[i + 1];
+        for (int j = a.ptr[i]; j < j1; ++j) acc = fma(a.val[j], __ldcg(&a.p[(int64_t)a.col[j] * nr + k]), acc);
+        a.q[i * nr + k] = acc;
+        s = fma(__ldcg(&a.p[i * nr + k]), acc, s);
+      }
+    cg_block_partial(s, a, 1, red);
+    if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
+    cg_total(a, 1, tot);
+    if (threadIdx.x < nr) {
+      const int t = threadIdx.x;
+      alpha[t] = active[t] && tot[t] > 0.0 ? rho[t] / tot[t] : 0.0;
+    }
+    __syncthreads();
+    // u += alpha p, r -= alpha q, and r.r
+    s = 0.0;
+    if (live) {
+      const double al = alpha[k];
+      for (int64_t i = blockIdx.x * (int64_t)per + sub; i < a.n_c; i += stride) {
+        const int64_t e = i * nr + k;
+        const double pe = __ldcg(&a.p[e]);
+        a.u[e] = fma(al, pe, a.u[e]);
+        const double re = fma(-al, a.q[e], a.r[e]);
+        a.r[e] = re;
+        s = fma(re, re, s);
+      }
+    }
+    cg_block_partial(s, a, 0, red);
+    if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
+    cg_total(a, 0, tot);
+    if (threadIdx.x == 0) n_active = 0;
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const int t = threadIdx.x;
+      beta[t] = 0.0;
+      if (active[t]) {
+        if (blockIdx.x == 0) a.iters[t] = it + 1;
+        beta[t] = rho[t] > 0.0 ? tot[t] / rho[t] : 0.0;
+        rho[t] = tot[t];
+        if (!(tot[t] > tol2[t])) active[t] = 0;   // converged (or not finite)
+        else atomicAdd(&n_active, 1);
+      }
+    }
+    __syncthreads();
+    // p = r + beta p (the columns that go on)
+    if (live && active[k]) {
+      const double be = beta[k];
+      for (int64_t i = blockIdx.x * (int64_t)per + sub; i < a.n_c; i += stride) {
+        const int64_t e = i * nr + k;
+        a.p[e] = fma(be, a.p[e], a.r[e]);
+      }
+    }
+    if (!grid_sync(a.bar, a.err, epoch, a.bar_extra, a.bar_cycles)) return;
+  }
+}
+
 template <typename T>
 cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
   void* p = nullptr;
@@ -597,6 +748,20 @@ cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, int blocks) {
 }
 
 }  // namespace
+
+cudaError_t build_coarse_cg_device(bddc_handle_s* h) {
+  cudaError_t e;
+  if ((e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
+  int dev = 0, coop = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return cudaErrorNotSupported;
+  // one block per SM must be resident, in both shapes (cooperative grid)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_cg, kCgThreadsWide, 0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorNotSupported;
+  return cudaSuccess;
+}
 
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   const int L = cf.n_levels;
@@ -739,6 +904,21 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  if (h->coarse_cg) {
+    if (nrhs > kCgMaxRhs) return cudaErrorInvalidValue;
+    CgArgs g{h->d_acp, h->d_acc, h->d_acv, rc, uc, h->w_cr, h->w_cy, h->w_cq, h->d_cgpart, h->d_cgiters,
+             h->d_cbar, h->d_err, (int)h->n_c, nrhs, h->cg_maxit, h->cg_rtol, h->cbar_extra, h->cbar_cycles};
+    if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->c_sms);
+    cfg.blockDim = dim3(narrow ? kCgThreadsNarrow : kCgThreadsWide);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_coarse_cg, g);
+    h->launches++;
+    return e;
+  }
   if (nrhs == 1 && h->d_gC) {
     const int sh = narrow ? 1 : 0;
     GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,

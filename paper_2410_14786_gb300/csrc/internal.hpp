@@ -150,7 +150,8 @@ struct HostSetup {
   std::vector<std::vector<double>> agi_val, aig_val;
   // coarse operator
   int64_t n_c = 0;
-  bool coarse_dense = true;                  // dense inverse (else the sparse factor)
+  bool coarse_dense = true;                  // dense inverse (else the sparse factor or CG)
+  bool coarse_cg = false;                    // inexact coarse solve by plain CG on A_c
   std::vector<double> Acinv;                 // n_c x n_c dense inverse (dense mode)
   std::vector<int64_t> Ac_ptr;               // A_c in CSR (both triangles)
   std::vector<int32_t> Ac_col;
@@ -271,6 +272,14 @@ struct bddc_handle_s {
   int64_t g_entries = 0;
   int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0, c_sms = 0;
   int64_t c_nnz = 0, c_update_total = 0;
+  // inexact coarse solve by CG: A_c in CSR (glob order), work vectors, block partials
+  bool coarse_cg = false;
+  int32_t* d_acp = nullptr; int32_t* d_acc = nullptr; double* d_acv = nullptr;
+  double* w_cq = nullptr;
+  double* d_cgpart = nullptr;          // [c_sms][2][nrhs_max]
+  int32_t* d_cgiters = nullptr;        // [nrhs_max] iterations of the last coarse solve
+  int cg_maxit = 2000;
+  double cg_rtol = 1e-10;
   bddc::WorkItem* d_wi_I = nullptr; int n_wi_I = 0;
   bddc::WorkItem* d_wi_G = nullptr; int n_wi_G = 0;
   // larger row tiles for the streamed (bulk-copy) GEMV

@@ -74,6 +74,9 @@ cudaError_t launch_gather_rows(int64_t n, int nrhs, const int32_t* perm, const d
 // Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
 // u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);
+// Inexact coarse solve by plain CG (A_c uploaded by the caller): barrier
+// counter and launch checks.
+cudaError_t build_coarse_cg_device(bddc_handle_s* h);
 // narrow: one block per SM sized to leave room on every SM for a concurrent
 // kernel (the interface operator) while the sweeps run: 256 threads (half
 // the registers) for one column, 512 threads for several.
