@@ -221,7 +221,7 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * packed tensor-core operand, the coarse solve's barrier counter and the
  * device error flag.
  * Limit: the temporaries of one apply, (3 n_interior + 3 n_interface_copies
- * + 2 sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
+ * + sum n_ci + 2 n_c + C) * nrhs doubles, with C = ceil(n_c / 512) n_c for
  * the dense coarse solve and 2 n_c for the sparse one
  * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
  * larger problems get BDDC_ERR_INVALID_ARG, and so do handles set up with
@@ -237,9 +237,9 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * other teardown of the device's primary context. Every call on every handle of
  * a device shares the one array, and no part of it needs to start at zero
  * (each call writes every element it reads before reading it): calls that
- * overlap on the GPU, on any streams, race and give wrong results. While the
- * call runs it points the handle's workspace at the array, so, as for every
- * call on a handle, no other host thread may use the same handle meanwhile. */
+ * overlap on the GPU, on any streams, race and give wrong results. The call
+ * does not modify the handle; as for every call on a handle, no other host
+ * thread may use the same handle meanwhile. */
 int bddc_apply_static_scratch(bddc_handle_t h, const double *r, double *z, int32_t nrhs,
                               void *stream);
 

@@ -256,17 +256,13 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   // prolongation), float64, as batched operators of the streamed GEMV
   std::vector<int> nGv(S), ncv(S);
   for (int s = 0; s < S; ++s) { nGv[s] = (int)hs.sub_G[s].size(); ncv[s] = (int)hs.sub_globs[s].size(); }
-  std::vector<int64_t> ptoff, poff;
-  std::vector<int32_t> ptld, pld;
+  std::vector<int64_t> ptoff;
+  std::vector<int32_t> ptld;
   const int phi_eb = elem_bytes(h->phi_prec);
   std::vector<double> phit = pack_rect(hs.Phi, ncv, nGv, true, phi_eb, ptoff, ptld);
-  std::vector<double> phi = pack_rect(hs.Phi, nGv, ncv, false, phi_eb, poff, pld);
   auto itPT = make_rect_items(ptoff, ptld, ncv, nGv, goff, coff, 128);
-  auto itP = make_rect_items(poff, pld, nGv, ncv, coff, goff, 128);
   h->n_wi_PT = (int)itPT.size();
-  h->n_wi_P = (int)itP.size();
   h->max_ld_PT = ptld.empty() ? 0 : *std::max_element(ptld.begin(), ptld.end());
-  h->max_ld_P = pld.empty() ? 0 : *std::max_element(pld.begin(), pld.end());
   // coarse gather map: coarse dof -> local constraint positions
   std::vector<int32_t> cg_ptr(hs.n_c + 1, 0), cg_idx(h->nC_tot);
   for (int64_t j = 0; j < h->nC_tot; ++j) cg_ptr[ccdof[j] + 1]++;
@@ -497,16 +493,13 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   if (h->phi_prec == BDDC_PREC_FP32) {
     std::vector<float> f32(phit.begin(), phit.end());
     CUDA_TRY(upload(h, reinterpret_cast<float**>(&h->d_phit), f32));
-    f32.assign(phi.begin(), phi.end());
-    CUDA_TRY(upload(h, reinterpret_cast<float**>(&h->d_phi), f32));
   } else {
     CUDA_TRY(upload(h, reinterpret_cast<double**>(&h->d_phit), phit));
-    CUDA_TRY(upload(h, reinterpret_cast<double**>(&h->d_phi), phi));
   }
-  if (!items_aligned(itPT, phi_eb) || !items_aligned(itP, phi_eb))
-    return fail(BDDC_ERR_INVALID_ARG, "internal: Phi rows not 16-byte aligned");
+  if (!items_aligned(itPT, phi_eb)) return fail(BDDC_ERR_INVALID_ARG, "internal: Phi rows not 16-byte aligned");
   CUDA_TRY(upload(h, &h->d_wi_PT, itPT));
-  CUDA_TRY(upload(h, &h->d_wi_P, itP));
+  CUDA_TRY(upload(h, &h->d_pt_off, ptoff));
+  CUDA_TRY(upload(h, &h->d_pt_ld, ptld));
   CUDA_TRY(upload(h, &h->d_sub_goff, goff));
   CUDA_TRY(upload(h, &h->d_sub_coff, coff));
   CUDA_TRY(upload(h, &h->d_csub, csub));
@@ -520,30 +513,29 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
 
   // ---- workspace ---------------------------------------------------------------------
   const int64_t R = h->nrhs_max;
-  CUDA_TRY(dev_alloc(h, &h->w_rI, h->nI_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_tI, h->nI_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_bI, h->nI_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_yG, h->nG_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_zG, h->nG_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_eG, h->nG_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_ucl, h->nC_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_g, h->nC_tot * R));
-  CUDA_TRY(dev_alloc(h, &h->w_rc, h->n_c * R));
-  CUDA_TRY(dev_alloc(h, &h->w_uc, h->n_c * R));
+  CUDA_TRY(dev_alloc(h, &h->w.rI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.tI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.bI, h->nI_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.yG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.zG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.eG, h->nG_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.g, h->nC_tot * R));
+  CUDA_TRY(dev_alloc(h, &h->w.rc, h->n_c * R));
+  CUDA_TRY(dev_alloc(h, &h->w.uc, h->n_c * R));
   if (h->coarse_dense) {
-    CUDA_TRY(dev_alloc(h, &h->w_cpart, (int64_t)std::max(1, h->n_cpanels) * h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w.cpart, (int64_t)std::max(1, h->n_cpanels) * h->n_c * R));
   } else {
-    CUDA_TRY(dev_alloc(h, &h->w_cr, h->n_c * R));
-    CUDA_TRY(dev_alloc(h, &h->w_cy, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w.cr, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w.cy, h->n_c * R));
   }
   if (h->coarse_cg) {
-    CUDA_TRY(dev_alloc(h, &h->w_cq, h->n_c * R));
+    CUDA_TRY(dev_alloc(h, &h->w.cq, h->n_c * R));
     CUDA_TRY(dev_alloc(h, &h->d_cgpart, (size_t)std::max(1, h->c_sms) * 2 * R));
     CUDA_TRY(dev_alloc(h, &h->d_cgiters, (size_t)R));
     CUDA_TRY(cudaMemset(h->d_cgiters, 0, sizeof(int32_t) * R));
   }
-  CUDA_TRY(cudaMemset(h->w_rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
-  CUDA_TRY(cudaMemset(h->w_uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
+  CUDA_TRY(cudaMemset(h->w.rc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
+  CUDA_TRY(cudaMemset(h->w.uc, 0, std::max<int64_t>(1, h->n_c * R) * sizeof(double)));
   const int64_t NV = h->n_nodes * R;
   CUDA_TRY(dev_alloc(h, &h->p_r, NV));
   CUDA_TRY(dev_alloc(h, &h->p_z, NV));
@@ -838,12 +830,12 @@ int bddc_coarse_vectors(bddc_handle_t h, double* rc_out, double* uc_out, int32_t
   // in glob order (the sparse coarse solve numbers the coarse dofs in its
   // elimination order on the device)
   if (h->d_cperm) {
-    if (rc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w_rc, rc_out, st));
-    if (uc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w_uc, uc_out, st));
+    if (rc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w.rc, rc_out, st));
+    if (uc_out) CUDA_TRY(launch_gather_rows(h->n_c, nrhs, h->d_cperm, h->w.uc, uc_out, st));
     return BDDC_OK;
   }
-  if (rc_out) CUDA_TRY(cudaMemcpyAsync(rc_out, h->w_rc, bytes, cudaMemcpyDeviceToDevice, st));
-  if (uc_out) CUDA_TRY(cudaMemcpyAsync(uc_out, h->w_uc, bytes, cudaMemcpyDeviceToDevice, st));
+  if (rc_out) CUDA_TRY(cudaMemcpyAsync(rc_out, h->w.rc, bytes, cudaMemcpyDeviceToDevice, st));
+  if (uc_out) CUDA_TRY(cudaMemcpyAsync(uc_out, h->w.uc, bytes, cudaMemcpyDeviceToDevice, st));
   return BDDC_OK;
 }
 
@@ -1231,8 +1223,8 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
   bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
                   64 << h->tune_tile_class[1], h->tune_overlap, h->tune_sym_stages[0], h->tune_sym_stages[1]};
   cudaError_t ce = cudaSuccess;
-  if ((ce = cudaMemsetAsync(h->w_rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
-      (ce = cudaMemsetAsync(h->w_yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
+  if ((ce = cudaMemsetAsync(h->w.rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
+      (ce = cudaMemsetAsync(h->w.yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return fail(BDDC_ERR_CUDA, cudaGetErrorString(ce));
@@ -1253,7 +1245,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
         h->tune_tile_class[fam] = tc;
         h->tune_sym_stages[fam] = ns;
         const float ms = timed([&] {
-          return launch_local_op(h, interior, interior ? h->w_rI : h->w_yG, interior ? h->w_tI : h->w_zG, nrhs, st);
+          return launch_local_op(h, interior, interior ? h->w.rI : h->w.yG, interior ? h->w.tI : h->w.zG, nrhs, st);
         });
         if (ms >= 0.0f && (best < 0.0f || ms < best)) {
           best = ms;
@@ -1277,12 +1269,12 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     }
   }
   if (h->n_c && !h->coarse_dense && !h->coarse_cg && nrhs >= 2) {
-    CUDA_TRY(cudaMemsetAsync(h->w_rc, 0, sizeof(double) * h->n_c * nrhs, st));
+    CUDA_TRY(cudaMemsetAsync(h->w.rc, 0, sizeof(double) * h->n_c * nrhs, st));
     const int keep = h->tune_coarse_rb_min;
     h->tune_coarse_rb_min = nrhs;   // blocked
-    const float blocked = timed([&] { return launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st); });
+    const float blocked = timed([&] { return launch_coarse_solve(h, h->w, h->w.rc, h->w.uc, nrhs, st); });
     h->tune_coarse_rb_min = 65;     // one row per unit
-    const float single = timed([&] { return launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st); });
+    const float single = timed([&] { return launch_coarse_solve(h, h->w, h->w.rc, h->w.uc, nrhs, st); });
     h->tune_coarse_rb_min = keep;
     if (blocked >= 0.0f && single >= 0.0f)
       t.coarse_rowblock_min_nrhs = blocked < single ? std::min(keep, (int)nrhs) : std::max(keep, (int)nrhs + 1);

@@ -36,10 +36,13 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 // ---------------------------------------------------------------------------
 // restriction: r_I (compact), W r_G (compact copies), zero Dirichlet outputs
 // ---------------------------------------------------------------------------
-__global__ void k_restrict(const double* __restrict__ r, int nrhs, const int32_t* __restrict__ inode,
+// ONE: a single right-hand side (nrhs = 1 at compile time: no index division).
+template <bool ONE>
+__global__ void k_restrict(const double* __restrict__ r, int nrhs_, const int32_t* __restrict__ inode,
                            int64_t nI, const int32_t* __restrict__ gnode, const double* __restrict__ gw,
                            int64_t nG, double* __restrict__ rI, double* __restrict__ yG,
                            const int32_t* __restrict__ dnode, int64_t nD, double* __restrict__ zout) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int64_t total = (nI + nG + nD) * nrhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -153,10 +156,11 @@ __global__ void __launch_bounds__(kThreads) k_bgemv(const WorkItem* __restrict__
 // One thread per (row, block of CB columns; CB = 1 measured fastest for 1 to
 // 64 columns: more threads hide more latency), the CSR loop unrolled so that
 // the loads of several nonzeros are in flight together.
-template <int CB>
-__global__ void k_iface_rhs(int64_t nG, int nrhs, const int32_t* __restrict__ ptr,
+template <int CB, bool ONE>
+__global__ void k_iface_rhs(int64_t nG, int nrhs_, const int32_t* __restrict__ ptr,
                             const int32_t* __restrict__ col, const double* __restrict__ val,
                             const double* __restrict__ tI, double* __restrict__ yG) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = nG * ncb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -183,9 +187,11 @@ __global__ void k_iface_rhs(int64_t nG, int nrhs, const int32_t* __restrict__ pt
 }
 
 // r_c[c, k] = sum over the local constraints that map to coarse dof c
-__global__ void k_coarse_gather(int64_t n_c, int nrhs, const int32_t* __restrict__ ptr,
+template <bool ONE>
+__global__ void k_coarse_gather(int64_t n_c, int nrhs_, const int32_t* __restrict__ ptr,
                                 const int32_t* __restrict__ idx, const double* __restrict__ g,
                                 double* __restrict__ rc) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int64_t total = n_c * nrhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -207,8 +213,10 @@ __global__ void k_gather_rows(int64_t n, int nrhs, const int32_t* __restrict__ p
   }
 }
 
-__global__ void k_coarse_scatter(int64_t nC, int nrhs, const int32_t* __restrict__ ccdof, const double* __restrict__ uc,
+template <bool ONE>
+__global__ void k_coarse_scatter(int64_t nC, int nrhs_, const int32_t* __restrict__ ccdof, const double* __restrict__ uc,
                                  double* __restrict__ ucl) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int64_t total = nC * nrhs;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -217,12 +225,58 @@ __global__ void k_coarse_scatter(int64_t nC, int nrhs, const int32_t* __restrict
   }
 }
 
+// e_G = Phi_G u_c per interface copy, read from the Phi_G^T array of the
+// coarse residual (n_ci rows of n_Gi entries per subdomain): one block per
+// subdomain stages the subdomain's coarse values u_c[R_ci] in shared memory,
+// thread `col` owns interface copy col and sums over the n_ci rows (loads
+// coalesced across the threads). Columns of u_c in chunks of NB.
+template <typename T, int NB>
+__global__ void __launch_bounds__(kThreads) k_phi_prolong(int n_sub, int nrhs, const T* __restrict__ pt,
+                                                         const int64_t* __restrict__ pt_off,
+                                                         const int32_t* __restrict__ pt_ld,
+                                                         const int32_t* __restrict__ goff,
+                                                         const int32_t* __restrict__ coff,
+                                                         const int32_t* __restrict__ ccdof,
+                                                         const double* __restrict__ uc, double* __restrict__ eG) {
+  using Acc = typename Elem<T>::Acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* us = reinterpret_cast<Acc*>(smem_raw);     // [n_ci][nrhs]
+  for (int s = blockIdx.x; s < n_sub; s += gridDim.x) {
+    const int g0 = goff[s], nG = goff[s + 1] - g0, c0 = coff[s], nc = coff[s + 1] - c0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * nrhs; i += blockDim.x) {
+      const int j = i / nrhs, k = i - j * nrhs;
+      us[i] = (Acc)uc[(int64_t)ccdof[c0 + j] * nrhs + k];
+    }
+    __syncthreads();
+    const T* a = pt + pt_off[s];
+    const int64_t ld = pt_ld[s];
+    for (int col = threadIdx.x; col < nG; col += blockDim.x)
+      for (int kb = 0; kb < nrhs; kb += NB) {
+        Acc acc[NB];
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk) acc[kk] = Acc(0);
+        for (int j = 0; j < nc; ++j) {
+          const Acc v = (Acc)__ldg(a + j * ld + col);
+#pragma unroll
+          for (int kk = 0; kk < NB; ++kk)
+            if (NB == 1 || kb + kk < nrhs) acc[kk] = fma(v, us[j * nrhs + kb + kk], acc[kk]);
+        }
+        double* out = eG + (int64_t)(g0 + col) * nrhs + kb;
+#pragma unroll
+        for (int kk = 0; kk < NB; ++kk)
+          if (NB == 1 || kb + kk < nrhs) out[kk] = (double)acc[kk];
+      }
+  }
+}
+
 // z[node] = sum over the copies q of the node of W_q (z_G[q] + (Phi_G u_c)[q])
-template <int CB>
-__global__ void k_prolong_gather(int64_t n_gu, int nrhs, const int32_t* __restrict__ gu_node,
+template <int CB, bool ONE>
+__global__ void k_prolong_gather(int64_t n_gu, int nrhs_, const int32_t* __restrict__ gu_node,
                                  const int32_t* __restrict__ gu_ptr, const int32_t* __restrict__ gu_copy,
                                  const double* __restrict__ gw, const double* __restrict__ zG,
                                  const double* __restrict__ eG, double* __restrict__ z) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = n_gu * ncb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -250,11 +304,12 @@ __global__ void k_prolong_gather(int64_t n_gu, int nrhs, const int32_t* __restri
 }
 
 // b_I = r_I - A_IG v_G   (rows: compact interior; cols: node ids)
-template <int CB>
-__global__ void k_interior_rhs(int64_t nI, int nrhs, const int32_t* __restrict__ ptr,
+template <int CB, bool ONE>
+__global__ void k_interior_rhs(int64_t nI, int nrhs_, const int32_t* __restrict__ ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ val,
                                const double* __restrict__ rI, const double* __restrict__ z,
                                double* __restrict__ bI) {
+  const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = nI * ncb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -473,6 +528,31 @@ cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y
 
 }  // namespace
 
+// e_G = Phi_G u_c for every interface copy (k_phi_prolong).
+cudaError_t launch_phi_prolong(bddc_handle_s* h, const ApplyWork& W, int nrhs, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(h->n_sub, 16 * 152);
+  const bool f32 = h->phi_prec == BDDC_PREC_FP32;
+  const size_t smem = (size_t)std::max(1, h->max_nc) * nrhs * (f32 ? 4 : 8);
+  cudaError_t e = cudaSuccess;
+  if (f32) {
+    auto kern = nrhs == 1 ? k_phi_prolong<float, 1> : k_phi_prolong<float, 8>;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    kern<<<blocks, kThreads, smem, st>>>(h->n_sub, nrhs, static_cast<const float*>(h->d_phit), h->d_pt_off,
+                                         h->d_pt_ld, h->d_sub_goff, h->d_sub_coff, h->d_ccdof, W.uc, W.eG);
+  } else {
+    auto kern = nrhs == 1 ? k_phi_prolong<double, 1> : k_phi_prolong<double, 8>;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    kern<<<blocks, kThreads, smem, st>>>(h->n_sub, nrhs, static_cast<const double*>(h->d_phit), h->d_pt_off,
+                                         h->d_pt_ld, h->d_sub_goff, h->d_sub_coff, h->d_ccdof, W.uc, W.eG);
+  }
+  h->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, int nrhs, cudaStream_t st) {
   return local_op(h, interior, X, Y, nullptr, nrhs, st);
 }
@@ -480,19 +560,20 @@ cudaError_t launch_local_op(bddc_handle_s* h, bool interior, const double* X, do
 cudaError_t launch_interior_correction(bddc_handle_s* h, const double* b, double* x, int nrhs,
                                        cudaStream_t st) {
   // x = 0 on interface and Dirichlet nodes, A_II^-1 b_I on interior nodes
-  k_restrict<<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(b, nrhs, h->d_inode, h->nI_tot, nullptr,
-                                                                nullptr, 0, h->w_rI, nullptr, h->d_dnode,
+  k_restrict<false><<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(b, nrhs, h->d_inode, h->nI_tot, nullptr,
+                                                                nullptr, 0, h->w.rI, nullptr, h->d_dnode,
                                                                 h->n_dir, x);
   if (h->n_gu)
     k_zero_nodes<<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(h->n_gu, nrhs, h->d_gu_node, x);
-  cudaError_t e = local_op(h, true, h->w_rI, x, h->d_inode, nrhs, st);
+  cudaError_t e = local_op(h, true, h->w.rI, x, h->d_inode, nrhs, st);
   h->launches += 1 + (h->n_gu > 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs, cudaStream_t st,
-                         cudaEvent_t* ev) {
+                         cudaEvent_t* ev, const ApplyWork* wk) {
+  const ApplyWork& W = wk ? *wk : h->w;
   cudaError_t e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(ev[i], st);
@@ -500,17 +581,17 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(0);
   // restriction + zero Dirichlet entries of z
   const int64_t tot = (h->nI_tot + h->nG_tot + h->n_dir) * nrhs;
-  k_restrict<<<blocks_for(tot), kThreads, 0, st>>>(r, nrhs, h->d_inode, h->nI_tot, h->d_gnode, h->d_gw,
-                                                   h->nG_tot, h->w_rI, h->w_yG, h->d_dnode, h->n_dir, z);
+  (nrhs == 1 ? k_restrict<true> : k_restrict<false>)<<<blocks_for(tot), kThreads, 0, st>>>(
+      r, nrhs, h->d_inode, h->nI_tot, h->d_gnode, h->d_gw, h->nG_tot, W.rI, W.yG, h->d_dnode, h->n_dir, z);
   h->launches++;
   mark(1);
   // t_I = A_II^-1 r_I
-  if ((e = local_op(h, true, h->w_rI, h->w_tI, nullptr, nrhs, st)) != cudaSuccess) return e;
+  if ((e = local_op(h, true, W.rI, W.tI, nullptr, nrhs, st)) != cudaSuccess) return e;
   mark(2);
   if (h->nG_tot) {
     // y'_G = W r_G - A_GI t_I; z_G = K_GG y'_G
-    k_iface_rhs<1><<<blocks_for(h->nG_tot * nrhs), kThreads, 0, st>>>(h->nG_tot, nrhs, h->d_agi_ptr, h->d_agi_col,
-                                                                    h->d_agi_val, h->w_tI, h->w_yG);
+    (nrhs == 1 ? k_iface_rhs<1, true> : k_iface_rhs<1, false>)<<<blocks_for(h->nG_tot * nrhs), kThreads, 0, st>>>(
+        h->nG_tot, nrhs, h->d_agi_ptr, h->d_agi_col, h->d_agi_val, W.tI, W.yG);
     h->launches++;
   }
   mark(3);
@@ -525,34 +606,34 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   if (overlap) {
     if ((e = cudaEventRecord(h->ev_fork[ax], st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->aux_stream[ax], h->ev_fork[ax], 0)) != cudaSuccess) return e;
-    if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, h->aux_stream[ax], 2)) != cudaSuccess) return e;
+    if ((e = local_op(h, false, W.yG, W.zG, nullptr, nrhs, h->aux_stream[ax], 2)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(h->ev_join[ax], h->aux_stream[ax])) != cudaSuccess) return e;
   } else if (h->nG_tot) {
-    if ((e = local_op(h, false, h->w_yG, h->w_zG, nullptr, nrhs, st)) != cudaSuccess) return e;
+    if ((e = local_op(h, false, W.yG, W.zG, nullptr, nrhs, st)) != cudaSuccess) return e;
   }
   mark(4);
   if (h->n_c) {
     // coarse residual r_c = sum R_ci^T Phi_G^T y'_G
-    if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, h->w_yG, h->w_g,
+    if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, W.yG, W.g,
                               nullptr, nrhs, h->d_err, st, 12, overlap ? 2 : 0)) != cudaSuccess)
       return e;
-    k_coarse_gather<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx,
-                                                                    h->w_g, h->w_rc);
+    (nrhs == 1 ? k_coarse_gather<true> : k_coarse_gather<false>)<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(
+        h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx, W.g, W.rc);
     h->launches += 2;
   }
   mark(5);
   if (h->n_c) {
     if (h->coarse_dense) {
       // u_c = A_c^-1 r_c: per-panel products of the explicit inverse, then their sum
-      if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, h->w_rc, h->w_cpart,
+      if ((e = launch_bgemv_tma(BDDC_PREC_FP64, h->d_wi_C, h->n_wi_C, h->ldc, h->d_acinv, W.rc, W.cpart,
                                 nullptr, nrhs, h->d_err, st)) != cudaSuccess)
         return e;
-      k_panel_sum<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c * nrhs, h->n_cpanels, h->w_cpart,
-                                                                  h->w_uc);
+      k_panel_sum<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(h->n_c * nrhs, h->n_cpanels, W.cpart,
+                                                                  W.uc);
       h->launches += 2;
     } else {
       // u_c = A_c^-1 r_c: sparse Cholesky forward and backward sweeps
-      if ((e = launch_coarse_solve(h, h->w_rc, h->w_uc, nrhs, st, overlap)) != cudaSuccess) return e;
+      if ((e = launch_coarse_solve(h, W, W.rc, W.uc, nrhs, st, overlap)) != cudaSuccess) return e;
     }
   }
   if (overlap && (e = cudaStreamWaitEvent(st, h->ev_join[ax], 0)) != cudaSuccess) return e;
@@ -561,28 +642,25 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
     // v_G = sum R^T W (z_G + Phi_G u_c)
     const double* eG = nullptr;
     if (h->n_c) {
-      k_coarse_scatter<<<blocks_for(h->nC_tot * nrhs), kThreads, 0, st>>>(h->nC_tot, nrhs, h->d_ccdof, h->w_uc,
-                                                                          h->w_ucl);
-      if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_P, h->n_wi_P, h->max_ld_P, h->d_phi, h->w_ucl, h->w_eG,
-                                nullptr, nrhs, h->d_err, st)) != cudaSuccess)
-        return e;
-      eG = h->w_eG;
-      h->launches += 2;
+      if ((e = launch_phi_prolong(h, W, nrhs, st)) != cudaSuccess) return e;
+      eG = W.eG;
     } else {
-      cudaMemsetAsync(h->w_eG, 0, sizeof(double) * h->nG_tot * nrhs, st);
-      eG = h->w_eG;
+      cudaMemsetAsync(W.eG, 0, sizeof(double) * h->nG_tot * nrhs, st);
+      eG = W.eG;
     }
-    k_prolong_gather<1><<<blocks_for(h->n_gu * nrhs), kThreads, 0, st>>>(
-        h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr, h->d_gu_copy, h->d_gw, h->w_zG, eG, z);
+    (nrhs == 1 ? k_prolong_gather<1, true> : k_prolong_gather<1, false>)<<<blocks_for(h->n_gu * nrhs), kThreads, 0,
+                                                                            st>>>(
+        h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr, h->d_gu_copy, h->d_gw, W.zG, eG, z);
     h->launches++;
   }
   mark(7);
   // z_I = A_II^-1 (r_I - A_IG v_G)
-  k_interior_rhs<1><<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(
-      h->nI_tot, nrhs, h->d_aig_ptr, h->d_aig_col, h->d_aig_val, h->w_rI, z, h->w_bI);
+  (nrhs == 1 ? k_interior_rhs<1, true> : k_interior_rhs<1, false>)<<<blocks_for(h->nI_tot * nrhs), kThreads, 0,
+                                                                      st>>>(
+      h->nI_tot, nrhs, h->d_aig_ptr, h->d_aig_col, h->d_aig_val, W.rI, z, W.bI);
   h->launches++;
   mark(8);
-  if ((e = local_op(h, true, h->w_bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
+  if ((e = local_op(h, true, W.bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
   mark(9);
   return cudaGetLastError();
 }

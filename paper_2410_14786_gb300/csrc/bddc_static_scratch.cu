@@ -54,16 +54,16 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   if (h->coarse_cg)
     return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
                                 "bddc_apply_static_scratch: the coarse CG mode is not supported; use bddc_apply");
-  // slices: rI, tI, bI (interior), yG, zG, eG (interface copies), g, ucl
-  // (local constraints), rc, uc (coarse), then the coarse solve's own
-  // temporaries, each nrhs columns wide
+  // slices: rI, tI, bI (interior), yG, zG, eG (interface copies), g (local
+  // constraints), rc, uc (coarse), then the coarse solve's own temporaries,
+  // each nrhs columns wide
   const long long R = nrhs;
   const long long nI = round_up(h->nI_tot * R), nG = round_up(h->nG_tot * R);
   const long long nC = round_up(h->nC_tot * R), nc = round_up(h->n_c * R);
   // coarse temporaries: the panel products (dense mode) or r' and y
   // (sparse mode)
   const long long ncoarse = h->coarse_dense ? round_up((long long)h->n_cpanels * h->n_c * R) : 2 * nc;
-  const long long need = 3 * nI + 3 * nG + 2 * nC + 2 * nc + ncoarse;
+  const long long need = 3 * nI + 3 * nG + nC + 2 * nc + ncoarse;
   if (need > kScratchDoubles)
     return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
                                 "bddc_apply_static_scratch: this problem needs " + std::to_string(need) +
@@ -75,33 +75,26 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   cudaError_t ae = scratch_address(h->device, &base);
   if (ae != cudaSuccess)
     return bddc::set_last_error(BDDC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ae));
-  // Point the handle's workspace at the static array for this one call.
-  // Calls on a handle are not re-entrant, and the launches below capture
-  // the pointer values when they are enqueued, so the handle's own
-  // workspace pointers are restored right after.
-  double* saved[13] = {h->w_rI, h->w_tI, h->w_bI, h->w_yG, h->w_zG, h->w_eG,
-                       h->w_g,  h->w_ucl, h->w_rc, h->w_uc, h->w_cr, h->w_cy, h->w_cpart};
+  // this call's work vectors: slices of the static array (the handle itself
+  // is not modified)
+  bddc::ApplyWork W;
   double* p = base;
-  h->w_rI = p; p += nI;
-  h->w_tI = p; p += nI;
-  h->w_bI = p; p += nI;
-  h->w_yG = p; p += nG;
-  h->w_zG = p; p += nG;
-  h->w_eG = p; p += nG;
-  h->w_g = p; p += nC;
-  h->w_ucl = p; p += nC;
-  h->w_rc = p; p += nc;
-  h->w_uc = p; p += nc;
+  W.rI = p; p += nI;
+  W.tI = p; p += nI;
+  W.bI = p; p += nI;
+  W.yG = p; p += nG;
+  W.zG = p; p += nG;
+  W.eG = p; p += nG;
+  W.g = p; p += nC;
+  W.rc = p; p += nc;
+  W.uc = p; p += nc;
   if (h->coarse_dense) {
-    h->w_cpart = p;
+    W.cpart = p;
   } else {
-    h->w_cr = p; p += nc;
-    h->w_cy = p;
+    W.cr = p; p += nc;
+    W.cy = p;
   }
-  cudaError_t e = bddc::launch_apply(h, r, z, nrhs, static_cast<cudaStream_t>(stream));
-  h->w_rI = saved[0]; h->w_tI = saved[1]; h->w_bI = saved[2]; h->w_yG = saved[3]; h->w_zG = saved[4];
-  h->w_eG = saved[5]; h->w_g = saved[6]; h->w_ucl = saved[7]; h->w_rc = saved[8]; h->w_uc = saved[9];
-  h->w_cr = saved[10]; h->w_cy = saved[11]; h->w_cpart = saved[12];
+  cudaError_t e = bddc::launch_apply(h, r, z, nrhs, static_cast<cudaStream_t>(stream), nullptr, &W);
   if (e != cudaSuccess) return bddc::set_last_error(BDDC_ERR_CUDA, cudaGetErrorString(e));
   return BDDC_OK;
 }

@@ -894,8 +894,8 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   return build_gather(h, cf, h->g_blocks > 0 ? std::min(h->g_blocks, sms) : sms);
 }
 
-cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st,
-                                bool narrow) {
+cudaError_t launch_coarse_solve(bddc_handle_s* h, const ApplyWork& W, const double* rc, double* uc, int nrhs,
+                                cudaStream_t st, bool narrow) {
   if (h->n_c == 0) return cudaSuccess;
   // row blocking pays from about 16 right-hand sides on (fewer, longer units
   // per level; measured on 10439 coarse dofs); the autotuner may move the
@@ -906,7 +906,7 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   attr[0].val.cooperative = 1;
   if (h->coarse_cg) {
     if (nrhs > kCgMaxRhs) return cudaErrorInvalidValue;
-    CgArgs g{h->d_acp, h->d_acc, h->d_acv, rc, uc, h->w_cr, h->w_cy, h->w_cq, h->d_cgpart, h->d_cgiters,
+    CgArgs g{h->d_acp, h->d_acc, h->d_acv, rc, uc, W.cr, W.cy, W.cq, h->d_cgpart, h->d_cgiters,
              h->d_cbar, h->d_err, (int)h->n_c, nrhs, h->cg_maxit, h->cg_rtol, h->cbar_extra, h->cbar_cycles};
     if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -921,7 +921,7 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   }
   if (nrhs == 1 && h->d_gC) {
     const int sh = narrow ? 1 : 0;
-    GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
+    GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, W.cr, W.cy, uc, h->d_cbar, h->d_err,
                  h->c_levels, (int)h->n_c, h->cbar_extra, h->cbar_cycles};
     if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -937,7 +937,7 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, 
   }
   const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
   CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
-               blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, h->w_cr, h->w_cy, uc, h->d_cbar, h->d_err,
+               blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, W.cr, W.cy, uc, h->d_cbar, h->d_err,
                h->c_levels, nrhs, h->cbar_extra, h->cbar_cycles};
   if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -160,6 +160,18 @@ struct HostSetup {
   int error_subdomain = -1;
 };
 
+// The work vectors of one apply (each nrhs columns wide, right-hand side
+// fastest): compact interior (rI, tI, bI), interface copies (yG, zG, eG),
+// local constraints (g), coarse (rc, uc), and the coarse solve's own: r' and y
+// of the factor's sweeps or r and p of the coarse CG (cr, cy), A_c p of the
+// coarse CG (cq), the dense coarse solve's panel products (cpart).
+struct ApplyWork {
+  double *rI = nullptr, *tI = nullptr, *bI = nullptr;
+  double *yG = nullptr, *zG = nullptr, *eG = nullptr;
+  double *g = nullptr, *rc = nullptr, *uc = nullptr;
+  double *cr = nullptr, *cy = nullptr, *cq = nullptr, *cpart = nullptr;
+};
+
 // Makes `device` current for the lifetime of the guard and restores the
 // caller's current device afterwards (every entry point of the C ABI).
 struct DeviceGuard {
@@ -223,13 +235,13 @@ struct bddc_handle_s {
   int32_t* d_agi_ptr = nullptr; int32_t* d_agi_col = nullptr; double* d_agi_val = nullptr;
   // A_IG: rows = compact interior positions, cols = node ids (interface nodes)
   int32_t* d_aig_ptr = nullptr; int32_t* d_aig_col = nullptr; double* d_aig_val = nullptr;
-  // Phi_Gamma^T [nc x nG] (coarse residual) and Phi_Gamma [nG x nc]
-  // (prolongation) per subdomain, float64, with their work lists
+  // Phi_Gamma^T [nc x nG] per subdomain (phi_prec), with the work list of the
+  // coarse residual's streamed GEMV; the prolongation reads it column-wise
   void* d_phit = nullptr;             // Phi_G^T arena (phi_prec)
-  void* d_phi = nullptr;              // Phi_G arena (phi_prec)
   int phi_prec = BDDC_PREC_FP64;      // BDDC_PREC_FP64 or BDDC_PREC_FP32
   bddc::WorkItem* d_wi_PT = nullptr; int n_wi_PT = 0; int max_ld_PT = 0;
-  bddc::WorkItem* d_wi_P = nullptr; int n_wi_P = 0; int max_ld_P = 0;
+  int64_t* d_pt_off = nullptr;        // [n_sub] element offset of each subdomain's Phi_G^T block
+  int32_t* d_pt_ld = nullptr;         // [n_sub] its leading dimension
   int32_t* d_sub_goff = nullptr;      // [n_sub + 1] interface copy offsets
   int32_t* d_sub_coff = nullptr;      // [n_sub + 1] local constraint offsets
   int32_t* d_csub = nullptr;          // [nC_tot] subdomain of each local constraint
@@ -246,7 +258,6 @@ struct bddc_handle_s {
   double* d_acinv = nullptr;
   int32_t ldc = 0, n_cpanels = 0;
   bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
-  double* w_cpart = nullptr;          // per-panel partial products
   // sparse coarse solve (coarse_solve.cu): supernode matrices, level lists
   double* d_cF = nullptr;             // forward matrices [L_PP^-1 ; M]
   double* d_cB = nullptr;             // backward matrices [L_PP^-T , -M^T]
@@ -275,7 +286,6 @@ struct bddc_handle_s {
   // inexact coarse solve by CG: A_c in CSR (glob order), work vectors, block partials
   bool coarse_cg = false;
   int32_t* d_acp = nullptr; int32_t* d_acc = nullptr; double* d_acv = nullptr;
-  double* w_cq = nullptr;
   double* d_cgpart = nullptr;          // [c_sms][2][nrhs_max]
   int32_t* d_cgiters = nullptr;        // [nrhs_max] iterations of the last coarse solve
   int cg_maxit = 2000;
@@ -306,12 +316,7 @@ struct bddc_handle_s {
   int max_cols_I = 0, max_cols_G = 0;
   int max_nc = 0;                     // most constraints of one subdomain
   // apply workspace (nrhs_max columns)
-  double *w_rI = nullptr, *w_tI = nullptr, *w_bI = nullptr;
-  double *w_yG = nullptr, *w_zG = nullptr, *w_g = nullptr, *w_rc = nullptr, *w_uc = nullptr;
-  double* w_cr = nullptr;             // r' of the coarse forward sweep (elimination order)
-  double* w_cy = nullptr;             // forward-sweep result (elimination order)
-  double* w_eG = nullptr;             // Phi_G u_c per interface copy
-  double* w_ucl = nullptr;            // u_c per local constraint
+  bddc::ApplyWork w;                  // the apply's work vectors (nrhs_max columns)
   // PCG workspace
   double *p_r = nullptr, *p_z = nullptr, *p_zold = nullptr, *p_p = nullptr, *p_q = nullptr;
   double *s_b = nullptr, *s_x = nullptr;   // staging for host-buffer solves

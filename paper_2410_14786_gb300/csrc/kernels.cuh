@@ -13,8 +13,9 @@ namespace bddc {
 
 // z = M^-1 r for nrhs columns; all phases on `st`. prof_events, if not
 // null, holds 10 events recorded between the launches.
+// W: the work vectors to use (null: the handle's own).
 cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs, cudaStream_t st,
-                         cudaEvent_t* prof_events = nullptr);
+                         cudaEvent_t* prof_events = nullptr, const ApplyWork* W = nullptr);
 
 // Batched GEMV over row tiles of many operators, streamed by bulk async
 // copies through shared memory (bddc_bgemv_tma.cu). err receives
@@ -80,8 +81,8 @@ cudaError_t build_coarse_cg_device(bddc_handle_s* h);
 // narrow: one block per SM sized to leave room on every SM for a concurrent
 // kernel (the interface operator) while the sweeps run: 256 threads (half
 // the registers) for one column, 512 threads for several.
-cudaError_t launch_coarse_solve(bddc_handle_s* h, const double* rc, double* uc, int nrhs, cudaStream_t st,
-                                bool narrow = false);
+cudaError_t launch_coarse_solve(bddc_handle_s* h, const ApplyWork& W, const double* rc, double* uc, int nrhs,
+                                cudaStream_t st, bool narrow = false);
 
 // Y = Op X over the interior (A_II^-1) or interface (K_GG) operators in the
 // compact layouts, on whichever engine the handle uses (for the autotuner).
