@@ -110,6 +110,21 @@ extern "C" {
 #define BDDC_COARSE_SPARSE  2
 #define BDDC_COARSE_CG      3
 
+/* Local solver of the interior (Dirichlet) problems with A_II (Sec. 2, Eqs.
+ * compzi and inner; Sec. 3, implementation paragraph: the paper factorises
+ * its local systems with a sparse direct solver on the GPU). DENSE: A_II^-1
+ * is formed explicitly in float64 and stored in the operator precision;
+ * every interior solve is a dense product with it. SPARSE: A_II is
+ * factorised by a supernodal Cholesky factorisation in nested-dissection
+ * order of the subdomain's elements, in float64, and every interior solve
+ * is the factor's forward and backward sweeps, level by level (float64 in
+ * every precision); the interface Schur complement comes from the same
+ * factorisation, so no dense n_I x n_I matrix is formed at any point (for
+ * subdomains of 10^4 dofs and more, as in the experiments of Sec. 3, whose
+ * dense A_II^-1 would take gigabytes each). K_GG is dense in both. */
+#define BDDC_LOCAL_DENSE    0
+#define BDDC_LOCAL_SPARSE   1
+
 /* Constraint families that become coarse (primal) dofs (Sec. 2). */
 #define BDDC_CORNERS 1u
 #define BDDC_EDGES   2u
@@ -150,6 +165,9 @@ typedef struct {
                               0 = 2000 */
     double coarse_cg_rtol; /* BDDC_COARSE_CG: relative residual at which the coarse CG
                               stops, in [0, 1); 0 = 1e-10 */
+    int32_t local_solver;  /* BDDC_LOCAL_*; 0 = DENSE */
+    int32_t local_leaf;    /* BDDC_LOCAL_SPARSE: largest vertex set of the nested dissection
+                              that is not split further (a dense front), 0..4096; 0 = 32 */
 } bddc_options_t;
 
 typedef struct {
@@ -187,6 +205,12 @@ typedef struct {
     int32_t coarse_cg_iters;            /* BDDC_COARSE_CG: most coarse CG iterations over the columns
                                            of the most recent coarse solve (bddc_query synchronises);
                                            0 otherwise */
+    int32_t local_solver;               /* BDDC_LOCAL_* */
+    int32_t interior_levels;            /* BDDC_LOCAL_SPARSE: levels of the interior elimination
+                                           forest (all subdomains' trees, merged by height); else 0 */
+    int64_t interior_factor_entries;    /* BDDC_LOCAL_SPARSE: stored entries of one sweep of the
+                                           interior factors (sum over supernodes of (p + u) p);
+                                           else 0 */
 } bddc_info_t;
 
 /* Build the preconditioner (Sec. 2: the subdomain matrices A_i of A = sum
@@ -225,7 +249,7 @@ int bddc_apply(bddc_handle_t h, const double *r, double *z, int32_t nrhs, void *
  * the dense coarse solve and 2 n_c for the sparse one
  * (sizes from bddc_query; each term rounded up to 32), must not exceed 2^20;
  * larger problems get BDDC_ERR_INVALID_ARG, and so do handles set up with
- * BDDC_COARSE_CG (its work vectors are not relocated). The driver places the array in
+ * BDDC_COARSE_CG or BDDC_LOCAL_SPARSE (their work vectors are not relocated). The driver places the array in
  * the device's memory when it loads the library's device code on that device:
  * under CUDA's default lazy module loading that happens in the first call on
  * the device (8 MiB less free memory from then on), with

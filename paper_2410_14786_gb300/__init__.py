@@ -20,6 +20,7 @@ from ._lib import (CORNERS, EDGES, FACES, PREC_BF16, PREC_FP32, PREC_FP64, PREC_
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "bf16": PREC_BF16, "tf32": PREC_TF32}
 TENSOR_CORES = {"auto": _lib.TC_AUTO, True: _lib.TC_ON, False: _lib.TC_OFF}
 COARSE = {"auto": _lib.COARSE_AUTO, "dense": _lib.COARSE_DENSE, "sparse": _lib.COARSE_SPARSE, "cg": _lib.COARSE_CG}
+LOCAL = {"dense": _lib.LOCAL_DENSE, "sparse": _lib.LOCAL_SPARSE}
 
 
 @dataclass
@@ -68,13 +69,18 @@ class BDDC:
     history: PCG iterations whose scalars (||r_k||, alpha_k, beta_k) the
     handle keeps for `pcg_history()` (0 = none); coarse="cg" solves the
     coarse system inexactly by plain CG (the paper's choice) to
-    coarse_cg_rtol (0: 1e-10) within coarse_cg_maxit iterations (0: 2000).
+    coarse_cg_rtol (0: 1e-10) within coarse_cg_maxit iterations (0: 2000);
+    local_solver="sparse" factorises every A_II (sparse Cholesky in nested-
+    dissection order, float64) and runs the interior solves as its sweeps
+    instead of forming A_II^-1 (subdomains of 10^4 dofs and more), with
+    dense fronts of up to local_leaf dofs (0: 32).
     """
 
     def __init__(self, dim, ne, elem_sigma, elem_subdomain, n_sub, precision="fp64",
                  constraints=0, nrhs_max=1, n_threads=0, device=None, coarse="auto", graph=True,
                  phi_fp64=False, tensor_cores="auto", autotune=False, tune_cache=None, coarse_blocks=0,
-                 full_operators=False, history=0, coarse_cg_rtol=0.0, coarse_cg_maxit=0):
+                 full_operators=False, history=0, coarse_cg_rtol=0.0, coarse_cg_maxit=0,
+                 local_solver="dense", local_leaf=0):
         import torch
         self._L = _lib.lib()
         self.handle = C.c_void_p()
@@ -89,7 +95,9 @@ class BDDC:
                             COARSE[coarse] if isinstance(coarse, str) else int(coarse), 0 if graph else 1,
                             1 if phi_fp64 else 0, TENSOR_CORES[tensor_cores], int(coarse_blocks),
                             1 if full_operators else 0, int(history), int(coarse_cg_maxit),
-                            float(coarse_cg_rtol))
+                            float(coarse_cg_rtol),
+                            LOCAL[local_solver] if isinstance(local_solver, str) else int(local_solver),
+                            int(local_leaf))
         _lib.check(self._L.bddc_setup(C.byref(prob), C.byref(opts), C.byref(self.handle)))
         self.dim, self.ne, self.nrhs_max = int(dim), int(ne), int(nrhs_max)
         self.n_nodes = (self.ne + 1) ** self.dim
@@ -123,6 +131,7 @@ class BDDC:
         import os
         key = "|".join([f"dim{self.dim}", f"ne{self.ne}", f"nrhs{self.nrhs_max}", f"prec{self.precision}",
                         f"tc{self.info()['tensor_cores']}", f"sym{self.info()['symmetric_operators']}",
+                        f"local{self.info()['local_solver']}",
                         hashlib.sha1(np.ascontiguousarray(part, dtype=np.int32).tobytes()).hexdigest()[:16]])
         table = {}
         if cache is not None and os.path.exists(cache):

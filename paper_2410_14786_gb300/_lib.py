@@ -25,6 +25,7 @@ PREC_FP64, PREC_FP32, PREC_BF16, PREC_TF32 = 0, 1, 2, 3
 TC_AUTO, TC_ON, TC_OFF = 0, 1, 2
 CORNERS, EDGES, FACES = 1, 2, 4
 COARSE_AUTO, COARSE_DENSE, COARSE_SPARSE, COARSE_CG = 0, 1, 2, 3
+LOCAL_DENSE, LOCAL_SPARSE = 0, 1
 
 EXPORTED = [
     "bddc_setup", "bddc_apply", "bddc_matvec", "bddc_rhs", "bddc_pcg_solve",
@@ -52,7 +53,8 @@ class Options(C.Structure):
                 ("n_threads", C.c_int32), ("device", C.c_int32), ("coarse", C.c_int32),
                 ("no_graph", C.c_int32), ("phi_fp64", C.c_int32),
                 ("tensor_cores", C.c_int32), ("coarse_blocks", C.c_int32), ("full_operators", C.c_int32),
-                ("history", C.c_int32), ("coarse_cg_maxit", C.c_int32), ("coarse_cg_rtol", C.c_double)]
+                ("history", C.c_int32), ("coarse_cg_maxit", C.c_int32), ("coarse_cg_rtol", C.c_double),
+                ("local_solver", C.c_int32), ("local_leaf", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -65,7 +67,8 @@ class Info(C.Structure):
         ("setup_seconds", C.c_double), ("precision", C.c_int32), ("error_subdomain", C.c_int32),
         ("device_error", C.c_int32), ("phi_precision", C.c_int32),
         ("tensor_cores", C.c_int32), ("solve_graph", C.c_int32), ("symmetric_operators", C.c_int32),
-        ("coarse_cg_iters", C.c_int32)]
+        ("coarse_cg_iters", C.c_int32), ("local_solver", C.c_int32), ("interior_levels", C.c_int32),
+        ("interior_factor_entries", C.c_int64)]
 
 
 class BDDCError(RuntimeError):

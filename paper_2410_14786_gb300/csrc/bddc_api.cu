@@ -232,6 +232,20 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     coarse_renumber(hs.cfac, cperm);
     for (auto& c : ccdof) c = cperm[c];
   }
+  // sparse local solver: each subdomain's compact interior positions are
+  // numbered in the elimination order of its factor (the interior sweeps
+  // then read and write contiguous runs); iperm[s][local] = position
+  std::vector<std::vector<int32_t>> iperm(hs.sparse_local ? S : 0), iinv(hs.sparse_local ? S : 0);
+  if (hs.sparse_local) {
+    for (int s = 0; s < S; ++s) {
+      coarse_renumber(hs.ifac[s], iperm[s]);
+      iinv[s].assign(iperm[s].size(), 0);
+      for (size_t l = 0; l < iperm[s].size(); ++l) {
+        iinv[s][iperm[s][l]] = (int32_t)l;
+        inode[ioff[s] + iperm[s][l]] = hs.sub_I[s][l];
+      }
+    }
+  }
   // A_GI with global compact interior columns; A_IG with node-id columns
   std::vector<int32_t> agi_ptr(h->nG_tot + 1, 0), agi_col, aig_ptr(h->nI_tot + 1, 0), aig_col;
   std::vector<double> agi_val, aig_val;
@@ -239,17 +253,19 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     const int nG = (int)hs.sub_G[s].size(), nI = (int)hs.sub_I[s].size();
     for (int r = 0; r < nG; ++r) {
       for (int j = hs.agi_ptr[s][r]; j < hs.agi_ptr[s][r + 1]; ++j) {
-        agi_col.push_back(ioff[s] + hs.agi_col[s][j]);
+        const int32_t c = hs.agi_col[s][j];
+        agi_col.push_back(ioff[s] + (hs.sparse_local ? iperm[s][c] : c));
         agi_val.push_back(hs.agi_val[s][j]);
       }
       agi_ptr[goff[s] + r + 1] = (int32_t)agi_col.size();
     }
-    for (int r = 0; r < nI; ++r) {
+    for (int q = 0; q < nI; ++q) {
+      const int r = hs.sparse_local ? iinv[s][q] : q;
       for (int j = hs.aig_ptr[s][r]; j < hs.aig_ptr[s][r + 1]; ++j) {
         aig_col.push_back(hs.sub_G[s][hs.aig_col[s][j]]);
         aig_val.push_back(hs.aig_val[s][j]);
       }
-      aig_ptr[ioff[s] + r + 1] = (int32_t)aig_col.size();
+      aig_ptr[ioff[s] + q + 1] = (int32_t)aig_col.size();
     }
   }
   // Phi_G^T (n_c x n_G per subdomain: coarse residual) and Phi_G (n_G x n_c:
@@ -287,6 +303,8 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   // ---- operator arenas ----------------------------------------------------------
   std::vector<int> dI(S), dG(S);
   for (int s = 0; s < S; ++s) { dI[s] = (int)hs.sub_I[s].size(); dG[s] = (int)hs.sub_G[s].size(); }
+  // the dense interior operators (none with the sparse local solver)
+  const std::vector<int> dIop = hs.sparse_local ? std::vector<int>(S, 0) : dI;
   std::vector<int64_t> offI, offG;
   std::vector<int32_t> ldI, ldG;
   const int prec = h->precision;
@@ -329,14 +347,14 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     };
     int rc2;
     if (prec == BDDC_PREC_BF16) {
-      if ((rc2 = up_tc(__nv_bfloat16{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I,
+      if ((rc2 = up_tc(__nv_bfloat16{}, hs.AIIinv, dIop, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I,
                        &h->n_tcs_I, &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I, &h->tc_maxg_I)) != BDDC_OK)
         return rc2;
       if ((rc2 = up_tc(__nv_bfloat16{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G,
                        &h->n_tcs_G, &h->d_tcop_G, &h->tcB_cols_G, &opbytes_G, &h->tc_maxg_G)) != BDDC_OK)
         return rc2;
     } else {
-      if ((rc2 = up_tc(float{}, hs.AIIinv, dI, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I, &h->n_tcs_I,
+      if ((rc2 = up_tc(float{}, hs.AIIinv, dIop, ioff, &h->d_aii, &h->d_tcu_I, &h->n_tcu_I, &h->d_tcs_I, &h->n_tcs_I,
                        &h->d_tcop_I, &h->tcB_cols_I, &opbytes_I, &h->tc_maxg_I)) != BDDC_OK)
         return rc2;
       if ((rc2 = up_tc(float{}, hs.Kgg, dG, goff, &h->d_kgg, &h->d_tcu_G, &h->n_tcu_G, &h->d_tcs_G, &h->n_tcs_G,
@@ -350,7 +368,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     h->d_tcB = pB;
     h->use_tma = false;
   } else if (!h->full_operators && h->nrhs_max == 1 && (prec == BDDC_PREC_FP32 || prec == BDDC_PREC_BF16) &&
-             sgemv_tma_supported(prec, std::max(dI.empty() ? 0 : *std::max_element(dI.begin(), dI.end()),
+             sgemv_tma_supported(prec, std::max(dIop.empty() ? 0 : *std::max_element(dIop.begin(), dIop.end()),
                                                 dG.empty() ? 0 : *std::max_element(dG.begin(), dG.end())))) {
     // symmetric operators, one right-hand side: lower triangles, one work
     // item per operator (largest first)
@@ -382,17 +400,17 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       *n_items = (int)it.size();
       return upload(h, items, it);
     };
-    CUDA_TRY(up_sym(hs.AIIinv, dI, ioff, reinterpret_cast<void**>(&h->d_aii), &h->d_wsy_I, &h->n_wsy_I,
+    CUDA_TRY(up_sym(hs.AIIinv, dIop, ioff, reinterpret_cast<void**>(&h->d_aii), &h->d_wsy_I, &h->n_wsy_I,
                     &h->max_n_I, &opbytes_I));
     CUDA_TRY(up_sym(hs.Kgg, dG, goff, reinterpret_cast<void**>(&h->d_kgg), &h->d_wsy_G, &h->n_wsy_G, &h->max_n_G,
                     &opbytes_G));
     h->use_sym = true;
     h->use_tma = true;
   } else {
-    CUDA_TRY(up_arena(hs.AIIinv, dI, offI, ldI, &h->d_aii));
+    CUDA_TRY(up_arena(hs.AIIinv, dIop, offI, ldI, &h->d_aii));
     CUDA_TRY(up_arena(hs.Kgg, dG, offG, ldG, &h->d_kgg));
     const int tile = 64;
-    auto itI = make_items(offI, ldI, dI, ioff, tile);
+    auto itI = make_items(offI, ldI, dIop, ioff, tile);
     auto itG = make_items(offG, ldG, dG, goff, tile);
     h->n_wi_I = (int)itI.size();
     h->n_wi_G = (int)itG.size();
@@ -405,7 +423,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     // (the autotuner picks one per operator family; 128 by default)
     for (int c = 0; c < 3; ++c) {
       const int ttile = 64 << c;
-      auto tI = make_items(offI, ldI, dI, ioff, ttile);
+      auto tI = make_items(offI, ldI, dIop, ioff, ttile);
       auto tG = make_items(offG, ldG, dG, goff, ttile);
       h->n_wtx_I[c] = (int)tI.size();
       h->n_wtx_G[c] = (int)tG.size();
@@ -415,7 +433,7 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
       CUDA_TRY(upload(h, &h->d_wtx_G[c], tG));
     }
     for (int s = 0; s < S; ++s) {
-      opbytes_I += (int64_t)dI[s] * ldI[s] * elem_bytes(prec);
+      opbytes_I += (int64_t)dIop[s] * ldI[s] * elem_bytes(prec);
       opbytes_G += (int64_t)dG[s] * ldG[s] * elem_bytes(prec);
     }
   }
@@ -474,8 +492,21 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   } else if (hs.n_c) {
     // sparse Cholesky factorisation of A_c: supernode matrices and level lists
     CUDA_TRY(build_coarse_device(h, hs.cfac));
-    in_coarse_bytes = h->c_nnz * 8 + h->g_entries * 12;
-    coarse_read_1rhs = h->g_entries * 12;
+    in_coarse_bytes = h->c_nnz * 8 + h->cs.g_entries * 12;
+    coarse_read_1rhs = h->cs.g_entries * 12;
+  }
+  // ---- sparse local solver: the interior factors as one forest ----------------------
+  h->sparse_local = hs.sparse_local;
+  int64_t ifac_entries = 0;
+  if (hs.sparse_local && h->nI_tot > 0) {
+    CoarseFactor forest;
+    merge_forest(hs.ifac, ioff, forest);
+    std::vector<CoarseFactor>().swap(hs.ifac);
+    ifac_entries = forest.nnz;
+    CUDA_TRY(build_sweeps(h, forest, h->is, h->nrhs_max > 1, 0));
+    // one interior solve at one column reads the gather form once
+    opbytes_I = h->is.g_entries * 12;
+    arena_bytes += (size_t)(h->is.g_entries * 12 + (h->is.multi ? h->is.nnz * 8 : 0));
   }
   // ---- index arrays -----------------------------------------------------------------
   std::vector<double> sigma(P->elem_sigma, P->elem_sigma + hs.n_elems);
@@ -516,6 +547,10 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(dev_alloc(h, &h->w.rI, h->nI_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w.tI, h->nI_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w.bI, h->nI_tot * R));
+  if (h->sparse_local) {
+    CUDA_TRY(dev_alloc(h, &h->w.ir, h->nI_tot * R));
+    CUDA_TRY(dev_alloc(h, &h->w.iy, h->nI_tot * R));
+  }
   CUDA_TRY(dev_alloc(h, &h->w.yG, h->nG_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w.zG, h->nG_tot * R));
   CUDA_TRY(dev_alloc(h, &h->w.eG, h->nG_tot * R));
@@ -586,13 +621,16 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   // couplings, the input r and the output z.
   int64_t ops = 0;
   in.interior_op_bytes = opbytes_I;
+  in.local_solver = h->sparse_local ? BDDC_LOCAL_SPARSE : BDDC_LOCAL_DENSE;
+  in.interior_levels = h->sparse_local ? h->is.levels : 0;
+  in.interior_factor_entries = ifac_entries;
   in.interface_op_bytes = opbytes_G;
   in.tensor_cores = h->use_tc ? 1 : 0;
   in.symmetric_operators = h->use_sym ? 1 : 0;
   in.n_interface_copies = h->nG_tot;
   in.coarse_factor_entries = h->c_nnz;
-  in.coarse_update_total = h->c_update_total;
-  in.coarse_levels = h->coarse_dense || h->coarse_cg ? 0 : h->c_levels;
+  in.coarse_update_total = h->cs.update_total;
+  in.coarse_levels = h->coarse_dense || h->coarse_cg ? 0 : h->cs.levels;
   ops = 2 * in.interior_op_bytes + in.interface_op_bytes;
   in.phi_precision = h->phi_prec;
   in.apply_bytes_1rhs = ops + 2 * (int64_t)elem_bytes(h->phi_prec) * in.sum_nG_nc + coarse_read_1rhs +
@@ -1238,6 +1276,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     for (int fam = 0; fam < 2; ++fam) {
       const bool interior = fam == 0;
       if ((interior ? h->nI_tot : h->nG_tot) == 0) continue;
+      if (interior && h->sparse_local) continue;   // the interior solves are sweeps, not a GEMV
       float best = -1.0f;
       int best_kb = h->tune_stage_kb[fam], best_tc = h->tune_tile_class[fam], best_ns = h->tune_sym_stages[fam];
       auto try_one = [&](int kb, int tc, int ns) {

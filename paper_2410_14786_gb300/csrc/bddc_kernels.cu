@@ -213,15 +213,15 @@ __global__ void k_gather_rows(int64_t n, int nrhs, const int32_t* __restrict__ p
   }
 }
 
+// z rows of the compact interior result: dst[perm[i]] = src[i]
 template <bool ONE>
-__global__ void k_coarse_scatter(int64_t nC, int nrhs_, const int32_t* __restrict__ ccdof, const double* __restrict__ uc,
-                                 double* __restrict__ ucl) {
+__global__ void k_scatter_rows(int64_t n, int nrhs_, const int32_t* __restrict__ perm, const double* __restrict__ src,
+                               double* __restrict__ dst) {
   const int nrhs = ONE ? 1 : nrhs_;
-  const int64_t total = nC * nrhs;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * nrhs;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = i / nrhs;
-    ucl[i] = uc[(int64_t)ccdof[j] * nrhs + (i - j * nrhs)];
+    const int64_t r = i / nrhs;
+    dst[(int64_t)perm[r] * nrhs + (i - r * nrhs)] = src[i];
   }
 }
 
@@ -500,11 +500,26 @@ cudaError_t bgemv(int precision, const WorkItem* items, int n_items, int max_lda
   }
 }
 
+// Interior solves with the sparse local solver: A_II^-1 X for all
+// subdomains at once by the forward and backward sweeps of the interior
+// forest (X and the result in compact interior order); with yscatter the
+// result goes through W.tI to rows yscatter of Y.
+cudaError_t interior_sweeps(bddc_handle_s* h, const ApplyWork& W, const double* X, double* Y,
+                            const int32_t* yscatter, int nrhs, cudaStream_t st) {
+  if (h->nI_tot == 0) return cudaSuccess;
+  double* out = yscatter ? W.tI : Y;
+  cudaError_t e = launch_sweeps(h, h->is, X, W.ir, W.iy, out, nrhs, st, false, false);
+  if (e != cudaSuccess || !yscatter) return e;
+  h->launches++;
+  return launch_scatter_rows(h->nI_tot, nrhs, yscatter, out, Y, st);
+}
+
 // One batched application of the interior (A_II^-1) or interface (K_GG)
 // operators of all subdomains.
 // Y = Op X over the interior or interface operators; counts its launches.
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
                      cudaStream_t st, int max_per_sm = 0) {
+  if (interior && h->sparse_local) return interior_sweeps(h, h->w, X, Y, yscatter, nrhs, st);
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
   if (h->use_sym) {
     if (nrhs != 1) return cudaErrorInvalidValue;   // nrhs_max is 1 on this path
@@ -693,6 +708,14 @@ cudaError_t launch_gather_rows(int64_t n, int nrhs, const int32_t* perm, const d
                                cudaStream_t st) {
   if (n * nrhs == 0) return cudaSuccess;
   k_gather_rows<<<blocks_for(n * nrhs), kThreads, 0, st>>>(n, nrhs, perm, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(int64_t n, int nrhs, const int32_t* perm, const double* src, double* dst,
+                                cudaStream_t st) {
+  if (n * nrhs == 0) return cudaSuccess;
+  (nrhs == 1 ? k_scatter_rows<true> : k_scatter_rows<false>)<<<blocks_for(n * nrhs), kThreads, 0, st>>>(
+      n, nrhs, perm, src, dst);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,12 @@
 //   Phi_G = G Sc^-1                            interface rows of Phi_i (Eq. saddlepoint)
 //   A_ci  = Sc^-1 - rho I                      = Phi_i^T A_i Phi_i = -Lambda_i
 //   K_GG  = Ahat^-1 - Phi_G G^T                (1,1) block of [S C^T; C 0]^-1
+// With the sparse local solver A_II^-1 is never formed: A_i is assembled in
+// CSR and factorised by the supernodal Cholesky of coarse_sparse.cpp in
+// nested-dissection order of the subdomain's elements, the interface dofs
+// eliminated last; their front, assembled but not factorised, is S (the
+// same matrix, without the dense n_I x n_I inverse), and the factor of A_II
+// is kept for the interior sweeps on the device.
 // The interior rows of Phi_i and z_i follow from the first block row,
 // x_I = A_II^-1 (y_I - A_IG x_G), and are never stored (see the apply).
 // Coarse: A_c = sum_i R_ci^T A_ci R_ci, inverted explicitly (SPD).
@@ -77,6 +83,8 @@ int validate_problem(const bddc_problem_t* P, const bddc_options_t* O, std::stri
   if (!(O->coarse_cg_rtol >= 0.0 && O->coarse_cg_rtol < 1.0)) { err = "coarse_cg_rtol must be in [0, 1)"; return BDDC_ERR_INVALID_ARG; }
   if (O->coarse_blocks < 0) { err = "coarse_blocks must be >= 0"; return BDDC_ERR_INVALID_ARG; }
   if (O->full_operators != 0 && O->full_operators != 1) { err = "full_operators must be 0 or 1"; return BDDC_ERR_INVALID_ARG; }
+  if (O->local_solver != BDDC_LOCAL_DENSE && O->local_solver != BDDC_LOCAL_SPARSE) { err = "unknown local_solver"; return BDDC_ERR_INVALID_ARG; }
+  if (O->local_leaf < 0 || O->local_leaf > 4096) { err = "local_leaf must be in [0, 4096]"; return BDDC_ERR_INVALID_ARG; }
   if (O->history < 0 || O->history > 100000) { err = "history must be in [0, 100000]"; return BDDC_ERR_INVALID_ARG; }
   const int64_t ne = P->ne;
   const int64_t n_el = P->dim == 2 ? ne * ne : ne * ne * ne;
@@ -218,6 +226,10 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
   // ---- per-subdomain numerics -----------------------------------------------
   double kd[4];
   q1_stiffness_by_distance(dim, hs.h, kd);
+  const bool sparse = O->local_solver == BDDC_LOCAL_SPARSE;
+  const int leaf = O->local_leaf > 0 ? O->local_leaf : kLocalLeaf;
+  hs.sparse_local = sparse;
+  hs.ifac.assign(sparse ? hs.n_sub : 0, {});
   hs.AIIinv.assign(hs.n_sub, {});
   hs.Kgg.assign(hs.n_sub, {});
   hs.Phi.assign(hs.n_sub, {});
@@ -247,60 +259,134 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
       if (jt != G.end() && *jt == node) return nI + (int)(jt - G.begin());
       return -1;
     };
-    std::vector<double> A((size_t)n * n, 0.0);
-    for (int64_t q = sptr[s]; q < sptr[s + 1]; ++q) {
-      int64_t e = selem[q];
-      int li[8];
-      for (int a = 0; a < nloc; ++a) {
-        int64_t nd = elem_node(e, a);
-        li[a] = hs.kappa[nd] ? local((int32_t)nd) : -1;
-      }
-      const double sg = P->elem_sigma[e];
-      for (int a = 0; a < nloc; ++a) {
-        if (li[a] < 0) continue;
-        for (int b = 0; b < nloc; ++b) {
-          if (li[b] < 0) continue;
-          A[(size_t)li[a] * n + li[b]] += sg * kd[__builtin_popcount(a ^ b)];
+    std::vector<double> S;   // Schur complement A_GG - A_GI A_II^-1 A_IG (nG x nG)
+    if (sparse) {
+      // local matrix in CSR (both triangles, exact zeros dropped), from the
+      // subdomain's elements; rows and columns in local order [I; G]
+      const int cap = dim == 2 ? 9 : 27;
+      std::vector<int32_t> rc((size_t)n * cap), cnt(n, 0);
+      std::vector<double> rv((size_t)n * cap, 0.0);
+      std::vector<std::vector<int32_t>> groups(nI);
+      const int64_t nel = sptr[s + 1] - sptr[s];
+      std::vector<double> gxyz(3 * (size_t)nel);
+      for (int64_t q = sptr[s]; q < sptr[s + 1]; ++q) {
+        const int64_t e = selem[q], lq = q - sptr[s];
+        gxyz[3 * lq] = (double)(e % ne) + 0.5;
+        gxyz[3 * lq + 1] = (double)((e / ne) % ne) + 0.5;
+        gxyz[3 * lq + 2] = dim == 3 ? (double)(e / ((int64_t)ne * ne)) + 0.5 : 0.0;
+        int li[8];
+        for (int a2 = 0; a2 < nloc; ++a2) {
+          const int64_t nd = elem_node(e, a2);
+          li[a2] = hs.kappa[nd] ? local((int32_t)nd) : -1;
+          if (li[a2] >= 0 && li[a2] < nI) groups[li[a2]].push_back((int32_t)lq);
+        }
+        const double sg = P->elem_sigma[e];
+        for (int a2 = 0; a2 < nloc; ++a2) {
+          if (li[a2] < 0) continue;
+          int32_t* cr = &rc[(size_t)li[a2] * cap];
+          double* vr = &rv[(size_t)li[a2] * cap];
+          for (int b2 = 0; b2 < nloc; ++b2) {
+            if (li[b2] < 0) continue;
+            int k = 0;
+            while (k < cnt[li[a2]] && cr[k] != li[b2]) ++k;
+            if (k == cnt[li[a2]]) { cr[k] = li[b2]; vr[k] = 0.0; cnt[li[a2]]++; }
+            vr[k] += sg * kd[__builtin_popcount(a2 ^ b2)];
+          }
         }
       }
-    }
-    // sparse couplings between interior and interface
-    auto& gp = hs.agi_ptr[s]; auto& gc = hs.agi_col[s]; auto& gv = hs.agi_val[s];
-    gp.assign(nG + 1, 0);
-    for (int r = 0; r < nG; ++r) {
-      for (int c = 0; c < nI; ++c) {
-        double v = A[(size_t)(nI + r) * n + c];
-        if (v != 0.0) { gc.push_back(c); gv.push_back(v); }
+      std::vector<int64_t> rp(n + 1, 0);
+      std::vector<int32_t> ci;
+      std::vector<double> cv;
+      std::vector<std::pair<int32_t, double>> row;
+      for (int r = 0; r < n; ++r) {
+        row.clear();
+        for (int k = 0; k < cnt[r]; ++k)
+          if (rv[(size_t)r * cap + k] != 0.0) row.emplace_back(rc[(size_t)r * cap + k], rv[(size_t)r * cap + k]);
+        std::sort(row.begin(), row.end());
+        for (auto& x : row) { ci.push_back(x.first); cv.push_back(x.second); }
+        rp[r + 1] = (int64_t)ci.size();
       }
-      gp[r + 1] = (int32_t)gc.size();
-    }
-    auto& ip = hs.aig_ptr[s]; auto& ic = hs.aig_col[s]; auto& iv = hs.aig_val[s];
-    ip.assign(nI + 1, 0);
-    for (int r = 0; r < nI; ++r) {
-      for (int c = 0; c < nG; ++c) {
-        double v = A[(size_t)r * n + nI + c];
-        if (v != 0.0) { ic.push_back(c); iv.push_back(v); }
+      std::vector<int32_t>().swap(rc);
+      std::vector<double>().swap(rv);
+      // sparse couplings between interior and interface
+      auto& gp = hs.agi_ptr[s]; auto& gc = hs.agi_col[s]; auto& gv = hs.agi_val[s];
+      gp.assign(nG + 1, 0);
+      for (int r = 0; r < nG; ++r) {
+        for (int64_t j = rp[nI + r]; j < rp[nI + r + 1]; ++j)
+          if (ci[j] < nI) { gc.push_back(ci[j]); gv.push_back(cv[j]); }
+        gp[r + 1] = (int32_t)gc.size();
       }
-      ip[r + 1] = (int32_t)ic.size();
-    }
-    // interior block: Cholesky, L^-1, A_II^-1
-    std::vector<double> L((size_t)nI * nI), X((size_t)nI * nI);
-    for (int r = 0; r < nI; ++r) std::memcpy(&L[(size_t)r * nI], &A[(size_t)r * n], sizeof(double) * nI);
-    if (nI > 0) {
-      if (dense::potrf(nI, L.data(), nI) >= 0) { bad_sub = s; return; }
-      dense::trtri_lower(nI, L.data(), nI, X.data(), nI);
-      hs.AIIinv[s].assign((size_t)nI * nI, 0.0);
-      dense::lower_gram(nI, X.data(), nI, hs.AIIinv[s].data(), nI);
-    }
-    if (nG == 0) return;
-    // Schur complement S = A_GG - Y^T Y with Y = L^-1 A_IG
-    std::vector<double> S((size_t)nG * nG);
-    for (int r = 0; r < nG; ++r)
-      std::memcpy(&S[(size_t)r * nG], &A[(size_t)(nI + r) * n + nI], sizeof(double) * nG);
-    if (nI > 0) {
-      std::vector<double> Y((size_t)nI * nG, 0.0);
-      dense::gemm_nn(nI, nG, nI, 1.0, X.data(), nI, &A[nI], n, Y.data(), nG);
-      dense::gemm(dense::GemmArgs{nG, nG, nI, -1.0, Y.data(), nG, true, Y.data(), nG, false, S.data(), nG});
+      auto& ip = hs.aig_ptr[s]; auto& ic = hs.aig_col[s]; auto& iv = hs.aig_val[s];
+      ip.assign(nI + 1, 0);
+      for (int r = 0; r < nI; ++r) {
+        for (int64_t j = rp[r]; j < rp[r + 1]; ++j)
+          if (ci[j] >= nI) { ic.push_back(ci[j] - nI); iv.push_back(cv[j]); }
+        ip[r + 1] = (int32_t)ic.size();
+      }
+      // A_II factorised in nested-dissection order of the elements, the
+      // interface eliminated last: its front is S
+      std::string ferr;
+      if (sparse_factor(n, rp, ci, cv, groups, gxyz, nG, leaf, hs.ifac[s], &S, ferr) != BDDC_OK) {
+        bad_sub = s;
+        return;
+      }
+      if (nG == 0) return;
+    } else {
+      std::vector<double> A((size_t)n * n, 0.0);
+      for (int64_t q = sptr[s]; q < sptr[s + 1]; ++q) {
+        int64_t e = selem[q];
+        int li[8];
+        for (int a = 0; a < nloc; ++a) {
+          int64_t nd = elem_node(e, a);
+          li[a] = hs.kappa[nd] ? local((int32_t)nd) : -1;
+        }
+        const double sg = P->elem_sigma[e];
+        for (int a = 0; a < nloc; ++a) {
+          if (li[a] < 0) continue;
+          for (int b = 0; b < nloc; ++b) {
+            if (li[b] < 0) continue;
+            A[(size_t)li[a] * n + li[b]] += sg * kd[__builtin_popcount(a ^ b)];
+          }
+        }
+      }
+      // sparse couplings between interior and interface
+      auto& gp = hs.agi_ptr[s]; auto& gc = hs.agi_col[s]; auto& gv = hs.agi_val[s];
+      gp.assign(nG + 1, 0);
+      for (int r = 0; r < nG; ++r) {
+        for (int c = 0; c < nI; ++c) {
+          double v = A[(size_t)(nI + r) * n + c];
+          if (v != 0.0) { gc.push_back(c); gv.push_back(v); }
+        }
+        gp[r + 1] = (int32_t)gc.size();
+      }
+      auto& ip = hs.aig_ptr[s]; auto& ic = hs.aig_col[s]; auto& iv = hs.aig_val[s];
+      ip.assign(nI + 1, 0);
+      for (int r = 0; r < nI; ++r) {
+        for (int c = 0; c < nG; ++c) {
+          double v = A[(size_t)r * n + nI + c];
+          if (v != 0.0) { ic.push_back(c); iv.push_back(v); }
+        }
+        ip[r + 1] = (int32_t)ic.size();
+      }
+      // interior block: Cholesky, L^-1, A_II^-1
+      std::vector<double> L((size_t)nI * nI), X((size_t)nI * nI);
+      for (int r = 0; r < nI; ++r) std::memcpy(&L[(size_t)r * nI], &A[(size_t)r * n], sizeof(double) * nI);
+      if (nI > 0) {
+        if (dense::potrf(nI, L.data(), nI) >= 0) { bad_sub = s; return; }
+        dense::trtri_lower(nI, L.data(), nI, X.data(), nI);
+        hs.AIIinv[s].assign((size_t)nI * nI, 0.0);
+        dense::lower_gram(nI, X.data(), nI, hs.AIIinv[s].data(), nI);
+      }
+      if (nG == 0) return;
+      // Schur complement S = A_GG - Y^T Y with Y = L^-1 A_IG
+      S.assign((size_t)nG * nG, 0.0);
+      for (int r = 0; r < nG; ++r)
+        std::memcpy(&S[(size_t)r * nG], &A[(size_t)(nI + r) * n + nI], sizeof(double) * nG);
+      if (nI > 0) {
+        std::vector<double> Y((size_t)nI * nG, 0.0);
+        dense::gemm_nn(nI, nG, nI, 1.0, X.data(), nI, &A[nI], n, Y.data(), nG);
+        dense::gemm(dense::GemmArgs{nG, nG, nI, -1.0, Y.data(), nG, true, Y.data(), nG, false, S.data(), nG});
+      }
     }
     // constraints on the interface (rows: globs of this subdomain)
     std::vector<double> C((size_t)nc * nG, 0.0);

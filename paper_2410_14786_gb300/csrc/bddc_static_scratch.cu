@@ -54,6 +54,9 @@ extern "C" int bddc_apply_static_scratch(bddc_handle_t h, const double* r, doubl
   if (h->coarse_cg)
     return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
                                 "bddc_apply_static_scratch: the coarse CG mode is not supported; use bddc_apply");
+  if (h->sparse_local)
+    return bddc::set_last_error(BDDC_ERR_INVALID_ARG,
+                                "bddc_apply_static_scratch: the sparse local solver is not supported; use bddc_apply");
   // slices: rI, tI, bI (interior), yG, zG, eG (interface copies), g (local
   // constraints), rc, uc (coarse), then the coarse solve's own temporaries,
   // each nrhs columns wide

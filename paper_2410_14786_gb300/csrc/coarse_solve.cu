@@ -731,18 +731,18 @@ cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
 
 namespace {
 
-cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, int blocks) {
+cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, int blocks) {
   GatherLayout g;
   const int nb[2] = {blocks, blocks}, wpb[2] = {kGThreadsWide / 32, kGThreadsNarrow / 32};
   gather_layout(cf, 2, nb, wpb, g);
-  h->g_entries = (int64_t)g.C.size();
-  h->g_blocks = blocks;
+  S.g_entries = (int64_t)g.C.size();
+  S.g_blocks = blocks;
   cudaError_t e;
-  if ((e = up(h, &h->d_gC, g.C)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_gI, g.I)) != cudaSuccess) return e;
+  if ((e = up(h, &S.gC, g.C)) != cudaSuccess) return e;
+  if ((e = up(h, &S.gI, g.I)) != cudaSuccess) return e;
   for (int sh = 0; sh < 2; ++sh) {
-    if ((e = up(h, &h->d_gU[sh], g.units[sh])) != cudaSuccess) return e;
-    if ((e = up(h, &h->d_gwo[sh], g.wo[sh])) != cudaSuccess) return e;
+    if ((e = up(h, &S.gU[sh], g.units[sh])) != cudaSuccess) return e;
+    if ((e = up(h, &S.gwo[sh], g.wo[sh])) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -763,9 +763,11 @@ cudaError_t build_coarse_cg_device(bddc_handle_s* h) {
   return cudaSuccess;
 }
 
-cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
+cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req) {
   const int L = cf.n_levels;
-  h->c_levels = L;
+  S.levels = L;
+  S.n = cf.n;
+  S.multi = multi;
   if (cf.n == 0) return cudaSuccess;
   const int nn = (int)cf.nodes.size();
   std::vector<CNodeDev> nodes(nn);
@@ -786,10 +788,30 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
     bcur = (bcur + 31) / 32 * 32;
     d.boff = bcur;
     bcur += (int64_t)T.p * d.bld;
-    upd.insert(upd.end(), T.upd.begin(), T.upd.end());
+    if (multi) upd.insert(upd.end(), T.upd.begin(), T.upd.end());
     ucur += T.u;
     nodes[t] = d;
   }
+  S.nnz = fcur + bcur;
+  S.update_total = ucur;
+  cudaError_t e;
+  if (S.bar == nullptr && (e = up(h, &S.bar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return cudaErrorNotSupported;
+  // cooperative grids: every block resident at once, in every shape
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsWide>, kGThreadsWide,
+                                                         0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorNotSupported;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsNarrow>,
+                                                         kGThreadsNarrow, 0)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorNotSupported;
+  if ((e = build_gather(h, cf, S, blocks_req > 0 ? std::min(blocks_req, sms) : sms)) != cudaSuccess) return e;
+  if (!multi) return cudaSuccess;
   std::vector<double> F((size_t)std::max<int64_t>(fcur, 1), 0.0), B((size_t)std::max<int64_t>(bcur, 1), 0.0);
   for (int t = 0; t < nn; ++t) {
     const CoarseNode& T = cf.nodes[t];
@@ -853,53 +875,45 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   std::vector<int32_t> lvl, lvl4;
   make_units(1, units, lvl, true);
   make_units(kRB, units4, lvl4, false);
-  h->c_nnz = fcur + bcur;
-  h->c_update_total = ucur;
-  cudaError_t e;
-  if ((e = up(h, &h->d_cF, F)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cB, B)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cnodes, nodes)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cunits, units)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cunits4, units4)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_clvl4, lvl4)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_clist, list)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cupd, upd)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_corder, cf.order)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_clvl, lvl)) != cudaSuccess) return e;
-  if ((e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
-  // cooperative grid: every block resident at once
-  int dev = 0, sms = 0, coop = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return cudaErrorNotSupported;
+  if ((e = up(h, &S.F, F)) != cudaSuccess) return e;
+  std::vector<double>().swap(F);
+  if ((e = up(h, &S.B, B)) != cudaSuccess) return e;
+  std::vector<double>().swap(B);
+  if ((e = up(h, &S.nodes, nodes)) != cudaSuccess) return e;
+  if ((e = up(h, &S.units, units)) != cudaSuccess) return e;
+  if ((e = up(h, &S.units4, units4)) != cudaSuccess) return e;
+  if ((e = up(h, &S.lvl4, lvl4)) != cudaSuccess) return e;
+  if ((e = up(h, &S.list, list)) != cudaSuccess) return e;
+  if ((e = up(h, &S.upd, upd)) != cudaSuccess) return e;
+  if ((e = up(h, &S.order, cf.order)) != cudaSuccess) return e;
+  if ((e = up(h, &S.lvl, lvl)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve<1>, kThreads, 0)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
-  h->c_grid = sms * std::min(per_sm, 2);
-  h->c_sms = sms;
+  S.grid = sms * std::min(per_sm, 2);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_solve<kRB>, kThreads / 2, 0)) !=
       cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
-  h->c_grid4 = sms * std::min(per_sm, 2);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsWide>, kGThreadsWide,
-                                                         0)) != cudaSuccess)
-    return e;
-  if (per_sm < 1) return cudaErrorNotSupported;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_sweeps<kGThreadsNarrow>,
-                                                         kGThreadsNarrow, 0)) != cudaSuccess)
-    return e;
-  if (per_sm < 1) return cudaErrorNotSupported;
-  return build_gather(h, cf, h->g_blocks > 0 ? std::min(h->g_blocks, sms) : sms);
+  S.grid4 = sms * std::min(per_sm, 2);
+  return cudaSuccess;
+}
+
+cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
+  int dev = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&h->c_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (h->d_cbar == nullptr && (e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
+  h->cs.bar = h->d_cbar;
+  if ((e = build_sweeps(h, cf, h->cs, true, h->g_blocks)) != cudaSuccess) return e;
+  h->c_nnz = h->cs.nnz;
+  return cudaSuccess;
 }
 
 cudaError_t launch_coarse_solve(bddc_handle_s* h, const ApplyWork& W, const double* rc, double* uc, int nrhs,
                                 cudaStream_t st, bool narrow) {
   if (h->n_c == 0) return cudaSuccess;
-  // row blocking pays from about 16 right-hand sides on (fewer, longer units
-  // per level; measured on 10439 coarse dofs); the autotuner may move the
-  // threshold
   cudaError_t e;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -919,13 +933,25 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const ApplyWork& W, const doub
     h->launches++;
     return e;
   }
-  if (nrhs == 1 && h->d_gC) {
+  return launch_sweeps(h, h->cs, rc, W.cr, W.cy, uc, nrhs, st, narrow, true);
+}
+
+cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, double* rp, double* y, double* u,
+                          int nrhs, cudaStream_t st, bool narrow, bool inject) {
+  if (S.n == 0) return cudaSuccess;
+  if (nrhs > 1 && !S.multi) return cudaErrorInvalidValue;
+  cudaError_t e;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  const unsigned int extra = inject ? h->cbar_extra : 0u;
+  const long long cycles = inject ? h->cbar_cycles : kBarrierWaitCycles;
+  if ((e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  if (nrhs == 1 && S.gC) {
     const int sh = narrow ? 1 : 0;
-    GatherArgs g{h->d_gU[sh], h->d_gwo[sh], h->d_gC, h->d_gI, rc, W.cr, W.cy, uc, h->d_cbar, h->d_err,
-                 h->c_levels, (int)h->n_c, h->cbar_extra, h->cbar_cycles};
-    if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+    GatherArgs g{S.gU[sh], S.gwo[sh], S.gC, S.gI, r, rp, y, u, S.bar, h->d_err, S.levels, (int)S.n, extra, cycles};
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->g_blocks);
+    cfg.gridDim = dim3(S.g_blocks);
     cfg.blockDim = dim3(narrow ? kGThreadsNarrow : kGThreadsWide);
     cfg.stream = st;
     cfg.attrs = attr;
@@ -935,13 +961,14 @@ cudaError_t launch_coarse_solve(bddc_handle_s* h, const ApplyWork& W, const doub
     h->launches++;
     return e;
   }
+  // row blocking pays from about 16 right-hand sides on (fewer, longer units
+  // per level; measured on 10439 coarse dofs); the autotuner may move the
+  // threshold
   const bool blocked = nrhs > 1 && nrhs >= h->tune_coarse_rb_min;
-  CoarseArgs a{h->d_cnodes, blocked ? h->d_cunits4 : h->d_cunits, h->d_clist, h->d_cupd, h->d_corder,
-               blocked ? h->d_clvl4 : h->d_clvl, h->d_cF, h->d_cB, rc, W.cr, W.cy, uc, h->d_cbar, h->d_err,
-               h->c_levels, nrhs, h->cbar_extra, h->cbar_cycles};
-  if ((e = cudaMemsetAsync(h->d_cbar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  CoarseArgs a{S.nodes, blocked ? S.units4 : S.units, S.list, S.upd, S.order, blocked ? S.lvl4 : S.lvl,
+               S.F, S.B, r, rp, y, u, S.bar, h->d_err, S.levels, nrhs, extra, cycles};
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(narrow ? h->c_sms : blocked ? h->c_grid4 : h->c_grid);
+  cfg.gridDim = dim3(narrow ? h->c_sms : blocked ? S.grid4 : S.grid);
   cfg.blockDim = dim3((narrow || blocked) ? kThreads / 2 : kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;

@@ -39,27 +39,29 @@ namespace bddc {
 
 namespace {
 
-constexpr int kLeaf = 384;  // vertex sets up to this size are not split
+constexpr int kLeaf = 384;  // coarse problem: vertex sets up to this size are not split
 
 struct Dissection {
-  const std::vector<std::vector<int32_t>>& subs;   // per dof: its subdomains
-  const std::vector<double>& sxyz;                 // per subdomain: centroid
-  std::vector<int8_t> side;                        // per subdomain: 1 or 2 during a split
+  const std::vector<std::vector<int32_t>>& subs;   // per dof: its groups (subdomains or elements)
+  const std::vector<double>& sxyz;                 // per group: centroid
+  std::vector<int8_t> side;                        // per group: 1 or 2 during a split
   CoarseFactor& cf;
+  int leaf;                                        // vertex sets up to this size are not split
   std::vector<int32_t> order;                      // position -> dof
 
-  Dissection(const std::vector<std::vector<int32_t>>& s, const std::vector<double>& x, int n_sub, CoarseFactor& f)
-      : subs(s), sxyz(x), side(n_sub, 0), cf(f) {}
+  Dissection(const std::vector<std::vector<int32_t>>& s, const std::vector<double>& x, int n_sub, CoarseFactor& f,
+             int leaf_size)
+      : subs(s), sxyz(x), side(n_sub, 0), cf(f), leaf(leaf_size) {}
 
   // V: the dofs all of whose subdomains are in G. Returns the index of the
   // new tree node (children first).
   int build(std::vector<int32_t> V, std::vector<int32_t> G, int depth) {
     std::vector<int32_t> sep, h1, h2, g1, g2;
-    bool leaf = (int)V.size() <= kLeaf || G.size() < 2 || depth > 60;
-    if (!leaf) leaf = !split(V, G, sep, h1, h2, g1, g2);
+    bool is_leaf = (int)V.size() <= leaf || G.size() < 2 || depth > 60;
+    if (!is_leaf) is_leaf = !split(V, G, sep, h1, h2, g1, g2);
     CoarseNode node;
     std::vector<int> kids;
-    if (leaf) {
+    if (is_leaf) {
       node.piv = V;
     } else {
       if (!h1.empty()) kids.push_back(build(std::move(h1), std::move(g1), depth + 1));
@@ -292,24 +294,40 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
   }
 }
 
-int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
-                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {
+int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_groups,
+                  const std::vector<double>& group_xyz, int64_t n_keep, int leaf, CoarseFactor& cf,
+                  std::vector<double>* schur, std::string& err) {
   cf = CoarseFactor();
   cf.n = n;
+  const int64_t nf = n - n_keep;        // dofs eliminated
   if (n == 0) return BDDC_OK;
   // ---- ordering and tree ----------------------------------------------------------
-  const int n_sub = (int)(sub_xyz.size() / 3);
-  Dissection nd(dof_subs, sub_xyz, n_sub, cf);
-  std::vector<int32_t> all(n), groups(n_sub);
-  std::iota(all.begin(), all.end(), 0);
-  std::iota(groups.begin(), groups.end(), 0);
-  nd.build(std::move(all), std::move(groups), 0);
+  // the dissection orders the dofs [0, nf); the kept dofs [nf, n) form one
+  // last front above it (its root), assembled but not factorised
+  const int n_groups = (int)(group_xyz.size() / 3);
+  Dissection nd(dof_groups, group_xyz, n_groups, cf, std::max(1, leaf));
+  int top = -1;
+  if (nf > 0) {
+    std::vector<int32_t> all(nf), groups(n_groups);
+    std::iota(all.begin(), all.end(), 0);
+    std::iota(groups.begin(), groups.end(), 0);
+    top = nd.build(std::move(all), std::move(groups), 0);
+  }
+  if (n_keep > 0) {
+    CoarseNode root;
+    for (int64_t v = nf; v < n; ++v) root.piv.push_back((int32_t)v);
+    if (top >= 0) root.children.push_back(top);
+    root.first = top >= 0 ? cf.nodes[top].first : 0;
+    for (int32_t v : root.piv) nd.order.push_back(v);
+    root.last = (int)n - 1;
+    cf.nodes.push_back(std::move(root));
+    if (top >= 0) cf.nodes[top].parent = (int)cf.nodes.size() - 1;
+  }
   std::vector<int32_t> pos(n);
   for (int64_t i = 0; i < n; ++i) pos[nd.order[i]] = (int32_t)i;
   cf.order = nd.order;
   const int nn = (int)cf.nodes.size();   // nodes are in post-order (children before parents)
-
   // ---- symbolic: update sets --------------------------------------------------------
   std::vector<int32_t> mark(n, -1);
   for (int t = 0; t < nn; ++t) {
@@ -368,6 +386,11 @@ int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
     }
     for (int i = 0; i < p; ++i) loc[T.piv[i]] = -1;
     for (int i = 0; i < u; ++i) loc[T.upd[i]] = -1;
+    if (n_keep > 0 && t == nn - 1) {
+      // the kept dofs' front is their Schur complement (pivots ascending, u = 0)
+      if (schur) *schur = std::move(F);
+      break;
+    }
     T.Fm.assign((size_t)f * p, 0.0);
     T.Bm.assign((size_t)p * f, 0.0);
     if (p > 0) {
@@ -375,7 +398,8 @@ int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
       std::vector<double> L((size_t)p * p), Li((size_t)p * p), Ai((size_t)p * p);
       for (int i = 0; i < p; ++i) std::memcpy(&L[(size_t)i * p], &F[(size_t)i * f], sizeof(double) * p);
       if (dense::potrf(p, L.data(), p) >= 0) {
-        err = "coarse matrix A_c is not positive definite";
+        err = n_keep > 0 ? "a local interior matrix A_II is not positive definite"
+                         : "coarse matrix A_c is not positive definite";
         return BDDC_ERR_SINGULAR;
       }
       dense::trtri_lower(p, L.data(), p, Li.data(), p);
@@ -412,7 +436,65 @@ int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
     }
     cf.nnz += (int64_t)f * p;
   }
+  if (n_keep > 0) {
+    // drop the kept front and the kept dofs from every update set (a suffix:
+    // update sets are in elimination order and the kept dofs come last), with
+    // their rows of Fm and columns of Bm: what remains factorises A_FF alone
+    cf.nodes.pop_back();
+    if (top >= 0) cf.nodes[top].parent = -1;
+    cf.n = nf;
+    cf.order.resize(nf);
+    cf.nnz = 0;
+    cf.n_levels = 0;
+    for (CoarseNode& T : cf.nodes) {
+      int u2 = 0;
+      while (u2 < T.u && T.upd[u2] < nf) ++u2;
+      if (u2 < T.u) {
+        const int p = T.p, f = p + T.u, f2 = p + u2;
+        T.Fm.resize((size_t)f2 * p);
+        std::vector<double> B2((size_t)p * f2);
+        for (int i = 0; i < p; ++i) std::memcpy(&B2[(size_t)i * f2], &T.Bm[(size_t)i * f], sizeof(double) * f2);
+        T.Bm.swap(B2);
+        T.upd.resize(u2);
+        T.u = u2;
+      }
+      cf.nnz += (int64_t)(T.p + T.u) * T.p;
+      cf.n_levels = std::max(cf.n_levels, T.height + 1);
+    }
+  }
   return BDDC_OK;
+}
+
+int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
+                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {
+  return sparse_factor(n, rp, ci, val, dof_subs, sub_xyz, 0, kLeaf, cf, nullptr, err);
+}
+
+void merge_forest(const std::vector<CoarseFactor>& parts, const std::vector<int32_t>& off, CoarseFactor& out) {
+  out = CoarseFactor();
+  int64_t n = 0;
+  for (size_t s = 0; s < parts.size(); ++s) n = std::max<int64_t>(n, off[s] + parts[s].n);
+  out.n = n;
+  out.order.assign(n, 0);
+  for (size_t s = 0; s < parts.size(); ++s) {
+    const CoarseFactor& P = parts[s];
+    const int32_t o = off[s];
+    const int t0 = (int)out.nodes.size();
+    for (int64_t i = 0; i < P.n; ++i) out.order[o + i] = o + P.order[i];
+    for (const CoarseNode& T : P.nodes) {
+      CoarseNode N = T;
+      for (int32_t& v : N.piv) v += o;
+      for (int32_t& w : N.upd) w += o;
+      for (int& k : N.children) k += t0;
+      if (N.parent >= 0) N.parent += t0;
+      N.first += o;
+      N.last += o;
+      out.nodes.push_back(std::move(N));
+    }
+    out.n_levels = std::max(out.n_levels, P.n_levels);
+    out.nnz += P.nnz;
+  }
 }
 
 }  // namespace bddc

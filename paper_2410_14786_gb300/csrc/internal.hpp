@@ -47,6 +47,7 @@ struct CGUnit {
 // in that order. Phases 0 .. L-1 are the forward levels (height = phase),
 // phases L .. 2L-1 the backward levels (height = 2L-1-phase).
 struct CoarseFactor;
+constexpr int kLocalLeaf = 32;      // default leaf size of the interior factorisations
 constexpr int kGatherBatch = 256;   // coefficients a warp reads per step of a unit (cost unit of the assignment)
 constexpr long long kBarrierWaitCycles = 4000000000LL;   // grid-barrier wait limit: about 2 s at 2 GHz
 struct GatherLayout {
@@ -63,6 +64,35 @@ struct CContrib {
   int32_t x_off;    // elimination position of the node's first pivot
   int32_t len;      // p of the node
   int64_t pad;
+};
+// Device form of one supernodal factorisation and of its sweeps
+// (coarse_solve.cu): the coarse factor of A_c, or the forest of the
+// interior factors of all subdomains (sparse local solver). F, B: node
+// matrices (several right-hand sides); gC, gI, gU, gwo: the gather form (one
+// right-hand side) for launch shapes [0] blocks of 512 threads and [1] of
+// 256; bar: the persistent kernel's grid-barrier counter.
+struct SweepSet {
+  double* F = nullptr;          // forward matrices [L_PP^-1 ; M]
+  double* B = nullptr;          // backward matrices [L_PP^-T , -M^T]
+  CNodeDev* nodes = nullptr;
+  CUnit* units = nullptr;       // warp units, forward levels then backward levels
+  CUnit* units4 = nullptr;      // the same with kinds 0 and 2 blocked by 4 rows
+  CContrib* list = nullptr;     // contributions of the receiving units
+  int32_t* upd = nullptr;       // update-set dofs of every node
+  int32_t* order = nullptr;     // elimination position -> dof
+  int32_t* lvl = nullptr;       // unit offsets: [L+1 forward][L+1 backward], then n
+  int32_t* lvl4 = nullptr;
+  double* gC = nullptr;
+  int32_t* gI = nullptr;
+  CGUnit* gU[2] = {nullptr, nullptr};
+  int32_t* gwo[2] = {nullptr, nullptr};   // [2 L][warps + 1]
+  unsigned int* bar = nullptr;
+  int64_t n = 0;                // dofs
+  int levels = 0, grid = 0, grid4 = 0, g_blocks = 0;
+  int64_t nnz = 0;              // stored entries of F and B
+  int64_t g_entries = 0;        // stored entries of the gather form
+  int64_t update_total = 0;     // sum of the update-set sizes
+  bool multi = false;           // F, B and the unit lists built (several right-hand sides)
 };
 
 // Tensor-core batched GEMM (bddc_tc_gemm.cu). A dense n x n operator is
@@ -124,6 +154,23 @@ void coarse_renumber(CoarseFactor& cf, std::vector<int32_t>& perm);
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
                   const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err);
+// The same factorisation in general form (coarse_factor is the case n_keep
+// = 0, leaf 384): the dofs [0, n - n_keep) are ordered by nested dissection
+// of their groups (dof_groups: the groups holding each of them; group_xyz: 3
+// coordinates per group) with vertex sets up to `leaf` dofs not split, and
+// factorised; the kept dofs [n - n_keep, n) are eliminated last as one front
+// that is assembled but not factorised: it is their Schur complement,
+// returned in *schur (n_keep x n_keep, row-major). The factor holds the
+// eliminated dofs alone (n = n - n_keep; the kept dofs are dropped from the
+// update sets).
+int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                  const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_groups,
+                  const std::vector<double>& group_xyz, int64_t n_keep, int leaf, CoarseFactor& cf,
+                  std::vector<double>* schur, std::string& err);
+// One factorisation of the block-diagonal matrix diag(parts): part s holds
+// dofs and positions [off[s], off[s] + parts[s].n) (a forest of elimination
+// trees whose levels are merged by height).
+void merge_forest(const std::vector<CoarseFactor>& parts, const std::vector<int32_t>& off, CoarseFactor& out);
 
 // Host-side results of the topology and numeric setup (float64).
 struct HostSetup {
@@ -157,6 +204,10 @@ struct HostSetup {
   std::vector<int32_t> Ac_col;
   std::vector<double> Ac_val;
   CoarseFactor cfac;                         // its sparse Cholesky factorisation
+  // sparse local solver: per subdomain, the factorisation of A_II (dofs in
+  // local interior order)
+  bool sparse_local = false;
+  std::vector<CoarseFactor> ifac;
   int error_subdomain = -1;
 };
 
@@ -164,12 +215,14 @@ struct HostSetup {
 // fastest): compact interior (rI, tI, bI), interface copies (yG, zG, eG),
 // local constraints (g), coarse (rc, uc), and the coarse solve's own: r' and y
 // of the factor's sweeps or r and p of the coarse CG (cr, cy), A_c p of the
-// coarse CG (cq), the dense coarse solve's panel products (cpart).
+// coarse CG (cq), the dense coarse solve's panel products (cpart), and r'
+// and y of the interior factors' sweeps (ir, iy).
 struct ApplyWork {
   double *rI = nullptr, *tI = nullptr, *bI = nullptr;
   double *yG = nullptr, *zG = nullptr, *eG = nullptr;
   double *g = nullptr, *rc = nullptr, *uc = nullptr;
   double *cr = nullptr, *cy = nullptr, *cq = nullptr, *cpart = nullptr;
+  double *ir = nullptr, *iy = nullptr;   // r' and y of the interior sweeps (sparse local solver)
 };
 
 // Makes `device` current for the lifetime of the guard and restores the
@@ -258,31 +311,17 @@ struct bddc_handle_s {
   double* d_acinv = nullptr;
   int32_t ldc = 0, n_cpanels = 0;
   bddc::WorkItem* d_wi_C = nullptr; int n_wi_C = 0;
-  // sparse coarse solve (coarse_solve.cu): supernode matrices, level lists
-  double* d_cF = nullptr;             // forward matrices [L_PP^-1 ; M]
-  double* d_cB = nullptr;             // backward matrices [L_PP^-T , -M^T]
-  bddc::CNodeDev* d_cnodes = nullptr;
-  bddc::CUnit* d_cunits = nullptr;    // warp units, forward levels then backward levels
-  bddc::CContrib* d_clist = nullptr;  // contributions of the receiving units
-  int32_t* d_cupd = nullptr;          // update-set dofs of every node
-  int32_t* d_corder = nullptr;        // elimination position -> coarse dof
+  // sparse coarse solve (coarse_solve.cu): the coarse factor's sweeps
+  bddc::SweepSet cs;
   int32_t* d_cperm = nullptr;         // glob -> device coarse dof (sparse coarse: elimination order)
-  int32_t* d_clvl = nullptr;          // unit offsets: [L+1 forward][L+1 backward], then n_c
-  unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernel
-  bddc::CUnit* d_cunits4 = nullptr;   // the same with kinds 0 and 2 blocked by 4 rows
-  int32_t* d_clvl4 = nullptr;
-  // gather form of the sweeps (one right-hand side): coefficients and operand
-  // indices in warp order, unit descriptors, per-phase per-warp offsets
-  // [0]: blocks of 512 threads (the sweeps alone), [1]: blocks of 256
-  // threads (half an SM's registers: beside the interface operator)
-  double* d_gC = nullptr;
-  int32_t* d_gI = nullptr;
-  bddc::CGUnit* d_gU[2] = {nullptr, nullptr};
-  int32_t* d_gwo[2] = {nullptr, nullptr};   // [2 L][warps + 1]
-  int g_blocks = 0;                   // grid the warp assignment was made for (requested: 0 = SMs)
-  int64_t g_entries = 0;
-  int c_levels = 0, c_grid = 0, c_grid4 = 0, c_block = 0, c_sms = 0;
-  int64_t c_nnz = 0, c_update_total = 0;
+  unsigned int* d_cbar = nullptr;     // grid barrier of the persistent coarse kernels
+  int g_blocks = 0;                   // requested grid of the one-column coarse sweeps (0 = SMs)
+  int c_sms = 0;
+  int64_t c_nnz = 0;                  // stored entries of the coarse operator
+  // sparse local solver: the interior factors of all subdomains as one forest
+  // (dofs = compact interior positions, numbered in elimination order)
+  bool sparse_local = false;
+  bddc::SweepSet is;
   // inexact coarse solve by CG: A_c in CSR (glob order), work vectors, block partials
   bool coarse_cg = false;
   int32_t* d_acp = nullptr; int32_t* d_acc = nullptr; double* d_acv = nullptr;

@@ -72,8 +72,23 @@ cudaError_t launch_tc_gemm(bddc_handle_s* h, bool interior, const double* X, dou
 cudaError_t launch_gather_rows(int64_t n, int nrhs, const int32_t* perm, const double* src, double* dst,
                                cudaStream_t st);
 
-// Sparse coarse solve (coarse_solve.cu): upload of the factorisation and
-// u_c = A_c^-1 r_c by level-scheduled forward and backward sweeps.
+// dst[perm[i], k] = src[i, k] for i < n, k < nrhs (row scatter).
+cudaError_t launch_scatter_rows(int64_t n, int nrhs, const int32_t* perm, const double* src, double* dst,
+                                cudaStream_t st);
+
+// Sweeps of a supernodal factorisation (coarse_solve.cu). build_sweeps
+// uploads cf (dofs numbered in elimination order or not) into S: the gather
+// form for one right-hand side on a grid of blocks_req blocks (0 = one per
+// SM), and with `multi` also the node matrices and unit lists for several.
+cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req);
+// u = A^-1 r by the forward and backward sweeps of S, level by level, in one
+// cooperative launch (r and u: S.n x nrhs in dof order; rp and y: work
+// vectors of the same size). inject: the barriers take the handle's test
+// settings (bddc_test_coarse_stall); otherwise the normal limit.
+cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, double* rp, double* y, double* u,
+                          int nrhs, cudaStream_t st, bool narrow, bool inject);
+// Sparse coarse solve: upload of the factorisation of A_c into the handle's
+// coarse sweep set; u_c = A_c^-1 r_c by its sweeps.
 cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf);
 // Inexact coarse solve by plain CG (A_c uploaded by the caller): barrier
 // counter and launch checks.

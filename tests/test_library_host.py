@@ -36,19 +36,21 @@ def test_exports_every_declared_symbol(L):
     assert sorted(_lib.EXPORTED) == names
 
 
-def _structs(p, precision=0, constraints=0, nrhs_max=1):
+def _structs(p, precision=0, constraints=0, nrhs_max=1, local_solver=0, local_leaf=0):
     from paper_2410_14786_gb300 import _lib
     sig = np.ascontiguousarray(p.elem_sigma, dtype=np.float64)
     part = np.ascontiguousarray(p.elem_subdomain, dtype=np.int32)
     prob = _lib.Problem(p.dim, p.ne, sig.ctypes.data_as(C.POINTER(C.c_double)),
                         part.ctypes.data_as(C.POINTER(C.c_int32)), p.n_sub)
     opts = _lib.Options(precision, constraints, nrhs_max, 4, 0, 0, 0)
+    opts.local_solver = local_solver
+    opts.local_leaf = local_leaf
     return prob, opts, (sig, part)
 
 
-def _inspect(L, p, constraints=0):
+def _inspect(L, p, constraints=0, local_solver=0, local_leaf=0):
     from paper_2410_14786_gb300 import _lib
-    prob, opts, keep = _structs(p, constraints=constraints)
+    prob, opts, keep = _structs(p, constraints=constraints, local_solver=local_solver, local_leaf=local_leaf)
     info = _lib.Info()
     rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 1, C.byref(info), None, 0)
     assert rc == 0, L.bddc_last_error()
@@ -76,10 +78,17 @@ def _small_voronoi():
     return synth.Problem(3, 10, s, sub, n, f, "voronoi_10_6")
 
 
+@pytest.mark.parametrize("local", ["dense", "sparse", "sparse_leaf2"])
 @pytest.mark.parametrize("name,make,mask", CASES, ids=[c[0] for c in CASES])
-def test_coarse_matrix_matches_oracle(L, name, make, mask):
+def test_coarse_matrix_matches_oracle(L, name, make, mask, local):
+    """A_c = sum R_ci^T Phi_i^T A_i Phi_i R_ci (Sec. 2, Eq. coarsegrid) from
+    the library's host setup against the oracle's, with the dense local
+    solver and with the sparse one (Schur complement from the partial
+    factorisation; leaf 2: deep dissection trees even on these small
+    subdomains)."""
     p = make()
-    info, Ac = _inspect(L, p, mask)
+    info, Ac = _inspect(L, p, mask, local_solver=0 if local == "dense" else 1,
+                        local_leaf=2 if local == "sparse_leaf2" else 0)
     o = Oracle(p.dim, p.ne, p.elem_sigma, p.elem_subdomain, p.n_sub,
                constraints=mask or (CORNER | EDGE | FACE))
     assert info.n_c == o.n_c
@@ -208,6 +217,17 @@ def test_coarse_blocks_and_full_operators_options_validated(L):
     assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == _lib.ERR_INVALID_ARG
     opts.full_operators = 1
     assert L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 0, C.byref(info), None, 0) == 0
+
+
+def test_local_solver_options_validated(L):
+    from paper_2410_14786_gb300 import _lib
+    prob, opts, keep = _structs(synth.config(1))
+    info = _lib.Info()
+    for ls, leaf, ok in ((2, 0, False), (-1, 0, False), (1, -1, False), (1, 4097, False), (1, 4096, True),
+                         (1, 1, True), (0, 0, True)):
+        opts.local_solver, opts.local_leaf = ls, leaf
+        rc = L.bddc_setup_inspect(C.byref(prob), C.byref(opts), 1, C.byref(info), None, 0)
+        assert rc == (0 if ok else _lib.ERR_INVALID_ARG), (ls, leaf, rc)
 
 
 def test_struct_mirrors_match_the_header():
