@@ -13,6 +13,9 @@ interior operators with float32 accumulation inside flexible PCG; everything
 else float64). The FP64, FP32 and TF32 (tensor-core) forms are timed beside it.
 `forms_cfg5` times the 192^3 workload (24^3 subdomains, 8 right-hand sides,
 whole solve as one CUDA graph) in FP64 and in the mixed BF16 tensor-core form.
+`forms_sparse_local` times the sparse local solver (A_II factorised, interior
+solves as its sweeps) on the paper's 2D Poisson workloads: 10^4 dofs per
+subdomain, and 6.35 million dofs in 9 x 9 subdomains.
 
 `cpu_baseline` and `--impl reference` time the CPU oracle (the plain
 NumPy/SciPy definitions of the paper's Sec. 2) on this same workload: its
@@ -383,6 +386,10 @@ def run_gb300(args):
     if args.config == 2 and not args.no_cfg5:
         cfg5 = run_cfg5(args, barrier, peak, peak_kind)
 
+    sparse_local = None
+    if args.config == 2 and not args.no_sparse_local:
+        sparse_local = run_sparse_local(args, barrier, peak, peak_kind)
+
     cpu = collect_oracle_worker(oracle_proc, timeout_s=1200.0) if oracle_proc is not None else None
 
     ms = head["ms_per_solve"]
@@ -405,6 +412,7 @@ def run_gb300(args):
         "time_to_rtol_ms": {k: v["ms_per_solve"] for k, v in forms.items()},
         "applies_per_s": {k: v["applies_per_s"] for k, v in forms.items()},
         "forms_cfg5": cfg5,
+        "forms_sparse_local": sparse_local,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -469,6 +477,96 @@ def run_cfg5(args, barrier, peak, peak_kind) -> dict:
     if g64 is not None:
         g64.close()
     out["mixed_speedup_vs_fp64"] = out["forms"]["fp64"]["ms_per_solve_block"] / out["forms"]["bf16"]["ms_per_solve_block"]
+    return out
+
+
+SPARSE_LOCAL_WORKLOADS = [
+    # the paper's 2D Poisson workloads (Sec. 3, Fig. 1): 10^4 dofs per
+    # subdomain (the local size of its BDDC vs CG comparison), and its
+    # strong-scaling problem of 6.35 million dofs split into 9 x 9
+    # subdomains of 280^2 elements (78,000 dofs each)
+    ("paper_2d_800sq_8x8_subdomains_10k_dofs_each", 800, 8),
+    ("paper_2d_2520sq_9x9_subdomains_6.35M_dofs", 2520, 9),
+]
+
+
+def run_sparse_local(args, barrier, peak, peak_kind) -> dict:
+    """The sparse local solver on the paper's own 2D workloads (sigma = 1,
+    corner and edge constraints, one right-hand side), where a dense A_II^-1
+    does not fit (80 MB to 48 GB per subdomain in float64): FP64 and the
+    mixed form (BF16 K_GG, float64 interior sweeps) to rtol 1e-8, with
+    setup time, iterations, true residual, the apply's phases and the
+    interior sweeps' bytes per solve against the HBM peak."""
+    import torch
+
+    import synth
+    from paper_2410_14786_gb300 import BDDC
+    out = {}
+    for wi, (name, ne, nsub) in enumerate(SPARSE_LOCAL_WORKLOADS):
+        if args.sparse_local_workload >= 0 and wi != args.sparse_local_workload:
+            continue
+        p = synth.make_problem(2, ne, nsub, "one", 1, k=6, name=name)
+        f = torch.from_numpy(np.ascontiguousarray(p.f)).cuda()
+        w = {"elements": f"{ne}^2", "subdomains": p.n_sub, "nrhs": 1, "rtol": RTOL, "constraints": "corners+edges",
+             "steps": min(args.steps, 5), "warmup": 1, "forms": {}}
+        x64 = None
+        g64 = None
+        for prec in ("fp64", "bf16"):
+            g = BDDC.from_problem(p, precision=prec, constraints=3, local_solver="sparse")
+            inf = g.info()
+            fm = {"setup_s": inf["setup_seconds"], "interior_levels": inf["interior_levels"],
+                  "interior_factor_entries": inf["interior_factor_entries"],
+                  "interior_bytes_per_solve": inf["interior_op_bytes"], "device_gb": inf["device_bytes"] / 1e9}
+            w["n_free"], w["n_c"], w["max_ni"] = inf["n_free"], inf["n_c"], inf["max_ni"]
+            b = g.rhs(f[:, 0])
+            if prec == "fp64":
+                # the interior sweeps split at every height (gather form below
+                # it, block form from it on): one interior solve's time each
+                scan = {}
+                rr = torch.rand_like(b)
+                for k in range(inf["interior_levels"] + 1):
+                    t = g.get_tuning()
+                    t["interior_block_height"] = k
+                    g.set_tuning(t)
+                    scan[k] = g.profile_apply(rr, reps=3)["interior_op"]
+                w["interior_split_scan_ms"] = scan
+            fm["tuning"] = g.autotune(1)
+            fm["interior_bytes_per_solve"] = g.info()["interior_op_bytes"]
+            x = torch.empty_like(b)
+            g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(w["steps"]):
+                _, res = g.pcg_solve(b, x, rtol=RTOL, maxit=500)
+            e1.record()
+            barrier()
+            fm["ms_per_solve"] = e0.elapsed_time(e1) / w["steps"]
+            fm["iters"] = int(res.iters[0])
+            gm = g64 if g64 is not None else g
+            fm["true_relres"] = float(((b - gm.matvec(x)).norm() / b.norm()).item())
+            prof = g.profile_apply(torch.rand_like(b), reps=5)
+            fm["apply_launch_ms"] = prof
+            sweep_ms = prof["interior_op"] + prof["interior_op_final"]
+            # two interior solves per apply: the gather form read once each,
+            # plus the compact vectors (operand, two work vectors, result)
+            sweep_bytes = 2 * (inf["interior_op_bytes"] + 8 * 4 * inf["n_interior"])
+            ach = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+            fm["sweeps_roofline"] = {"bound": "hbm", "kernel": "k_coarse_sweeps on the interior forest (2 per apply)",
+                                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                     "peak_kind": peak_kind, "bytes_per_apply": sweep_bytes, "traffic": None}
+            if prec == "fp64":
+                x64, g64 = x.clone(), g
+            else:
+                fm["rel_diff_vs_fp64"] = float(((x - x64).norm() / x64.norm()).item())
+                g.close()
+            w["forms"][prec] = fm
+        if g64 is not None:
+            g64.close()
+        w["mixed_speedup_vs_fp64"] = w["forms"]["fp64"]["ms_per_solve"] / w["forms"]["bf16"]["ms_per_solve"]
+        out[name] = w
+        del f
+        torch.cuda.empty_cache()
     return out
 
 
@@ -600,6 +698,12 @@ def main():
     ap.add_argument("--apply-only", type=int, default=0,
                     help="profiling aid: set up the headline form, run this many applies and one solve, exit")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 192^3 workload (forms_cfg5)")
+    ap.add_argument("--no-sparse-local", action="store_true",
+                    help="skip the sparse local solver on the paper's 2D workloads (forms_sparse_local)")
+    ap.add_argument("--sparse-local-only", action="store_true",
+                    help="run only the sparse local solver on the paper's 2D workloads and print that section")
+    ap.add_argument("--sparse-local-workload", type=int, default=-1,
+                    help="with --sparse-local-only: run only this one of its workloads (0 or 1)")
     ap.add_argument("--coarse", default="auto", choices=["auto", "sparse", "dense", "cg"],
                     help="development aid: coarse solve (auto = sparse factorisation; cg = inexact, by plain CG)")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
@@ -614,6 +718,12 @@ def main():
         return run_apply_only(args)
     if args.config == 4:
         return run_adjoint(args)
+    if args.sparse_local_only:
+        import torch
+        torch.cuda.init()
+        peak, peak_kind = _peaks()
+        print(json.dumps({"forms_sparse_local": run_sparse_local(args, torch.cuda.synchronize, peak, peak_kind)}))
+        return 0
     return run_gb300(args)
 
 

@@ -294,18 +294,25 @@ typedef struct {
     int32_t sym_stages_interior;      /* shared-memory stages of the symmetric (lower-triangle) GEMV,
                                          3 or 4 (default 4) */
     int32_t sym_stages_interface;
+    int32_t interior_block_height;    /* BDDC_LOCAL_SPARSE, one column: the levels of the interior
+                                         elimination forest below this height run as per-level gather
+                                         sweeps (one warp group per factor row), the levels from it on
+                                         supernode by supernode with the node matrices streamed;
+                                         0..64, clamped to the forest's levels (default: all levels
+                                         in the gather form) */
 } bddc_tuning_t;
 
 /* Time the candidate launch parameters for blocks of nrhs columns (row
  * tiles of 64, 128 and 256 rows and stage sizes of 6, 12, 24 and 48 KB of
  * the streamed GEMV of each operator family when the handle uses it, or for
  * the symmetric GEMV 3 or 4 stages of 10 to 24 KB;
- * one-row against four-row coarse sweep units when nrhs >= 2; whole applies
- * with and without the coarse overlap), apply the fastest and return them in
- * *out (may be NULL).
+ * one-row against four-row coarse sweep units when nrhs >= 2; every split
+ * height of the sparse local solver's interior sweeps at one column; whole
+ * applies with and without the coarse overlap), apply the fastest and return
+ * them in *out (may be NULL).
  * Uses the handle's work vectors (their contents are overwritten) and CUDA
- * events; synchronises `stream`. Results do not change (the candidates
- * differ only in scheduling, up to the order of the coarse sums). */
+ * events; synchronises `stream`. Results do not change beyond rounding (the
+ * candidates differ in scheduling and in the order of some sums). */
 int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t *out, void *stream);
 int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t *out);
 /* Returns INVALID_ARG (and changes nothing) if a field is out of range. */

@@ -503,10 +503,10 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     merge_forest(hs.ifac, ioff, forest);
     std::vector<CoarseFactor>().swap(hs.ifac);
     ifac_entries = forest.nnz;
-    CUDA_TRY(build_sweeps(h, forest, h->is, h->nrhs_max > 1, 0));
-    // one interior solve at one column reads the gather form once
-    opbytes_I = h->is.g_entries * 12;
-    arena_bytes += (size_t)(h->is.g_entries * 12 + (h->is.multi ? h->is.nnz * 8 : 0));
+    CUDA_TRY(build_sweeps(h, forest, h->is, h->nrhs_max > 1, 0, kSweepBlock));
+    // one interior solve at one column reads its coefficients once
+    opbytes_I = sweep_read_1col(h->is);
+    arena_bytes += (size_t)(h->is.g_entries * 12 + ((h->is.multi || h->is.block_form) ? h->is.nnz * 8 : 0));
   }
   // ---- index arrays -----------------------------------------------------------------
   std::vector<double> sigma(P->elem_sigma, P->elem_sigma + hs.n_elems);
@@ -1204,7 +1204,7 @@ int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
   if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
   *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min,
                        64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1], h->tune_overlap,
-                       h->tune_sym_stages[0], h->tune_sym_stages[1]};
+                       h->tune_sym_stages[0], h->tune_sym_stages[1], h->is.block_min_height};
   return BDDC_OK;
 }
 
@@ -1223,6 +1223,8 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   if (in->sym_stages_interior < 3 || in->sym_stages_interior > 4 || in->sym_stages_interface < 3 ||
       in->sym_stages_interface > 4)
     return fail(BDDC_ERR_INVALID_ARG, "symmetric GEMV stages must be 3 or 4");
+  if (in->interior_block_height < 0 || in->interior_block_height > 64)
+    return fail(BDDC_ERR_INVALID_ARG, "interior_block_height must be 0..64");
   h->tune_tile_class[0] = tile_class(in->gemv_rows_interior);
   h->tune_tile_class[1] = tile_class(in->gemv_rows_interface);
   h->tune_overlap = in->coarse_overlap;
@@ -1231,6 +1233,14 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   h->tune_sym_stages[0] = in->sym_stages_interior;
   h->tune_sym_stages[1] = in->sym_stages_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
+  if (h->is.block_form) {
+    // the interior sweeps' bytes per solve follow the split
+    const int64_t before = sweep_read_1col(h->is);
+    h->is.block_min_height = std::min(in->interior_block_height, h->is.levels);
+    const int64_t after = sweep_read_1col(h->is);
+    h->info.interior_op_bytes = after;
+    h->info.apply_bytes_1rhs += 2 * (after - before);
+  }
   drop_graphs(h);   // captured graphs hold the old launch parameters
   return BDDC_OK;
 }
@@ -1259,7 +1269,8 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     return best[1];
   };
   bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
-                  64 << h->tune_tile_class[1], h->tune_overlap, h->tune_sym_stages[0], h->tune_sym_stages[1]};
+                  64 << h->tune_tile_class[1], h->tune_overlap, h->tune_sym_stages[0], h->tune_sym_stages[1],
+                  h->is.block_min_height};
   cudaError_t ce = cudaSuccess;
   if ((ce = cudaMemsetAsync(h->w.rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
       (ce = cudaMemsetAsync(h->w.yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
@@ -1306,6 +1317,22 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
       (interior ? t.gemv_rows_interior : t.gemv_rows_interface) = 64 << best_tc;
       (interior ? t.sym_stages_interior : t.sym_stages_interface) = best_ns;
     }
+  }
+  if (h->is.block_form && nrhs == 1 && h->nI_tot) {
+    // every split height of the interior sweeps (one interior solve each)
+    const int keep = h->is.block_min_height;
+    float best = -1.0f;
+    int best_k = keep;
+    for (int k = 0; k <= h->is.levels; ++k) {
+      h->is.block_min_height = k;
+      const float ms = timed([&] { return launch_local_op(h, true, h->w.rI, h->w.tI, 1, st); });
+      if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+        best = ms;
+        best_k = k;
+      }
+    }
+    h->is.block_min_height = keep;
+    t.interior_block_height = best_k;
   }
   if (h->n_c && !h->coarse_dense && !h->coarse_cg && nrhs >= 2) {
     CUDA_TRY(cudaMemsetAsync(h->w.rc, 0, sizeof(double) * h->n_c * nrhs, st));

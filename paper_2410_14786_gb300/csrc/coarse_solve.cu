@@ -565,6 +565,252 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
 }
 
 
+// ---- per-level form (one right-hand side, large factors) --------------------------------
+// One launch per phase of the gather form (the launch boundary replaces the
+// grid barrier, and the grid is not limited to one resident block per SM).
+// A phase's units, longest first, are split into classes by length; a unit
+// of class c is processed by a group of G = 32, 16, 8, 4, 2 or 1 lanes, so
+// the many short rows of the lower levels keep every lane busy: each lane
+// strides over the unit's coefficients four at a time (their operand loads
+// in flight together), the group's partial sums are combined by shuffles
+// within the group, and its first lane stores the result. Values of other
+// phases are read with plain loads (written by earlier launches);
+// coefficients and indices through the read-only path.
+struct LevelArgs {
+  const CGUnit* units;       // the phase's descriptors
+  const double* C;
+  const int32_t* I;
+  const double* xa;          // operand vector for indices < n (forward: r', backward: y)
+  const double* xb;          // operand vector for indices n + i (forward: r, backward: u by position)
+  double* rp;                // r' (forward, receiving units) / u by position (backward)
+  double* y;                 // y (forward rows)
+  double* u;                 // u by dof (backward)
+  int n, fwd;
+  int32_t cb[kLevelClasses + 1], bb[kLevelClasses + 1];
+};
+
+template <int G, int c>
+__device__ __forceinline__ void level_group(const LevelArgs& a, int b) {
+  const int grp = (int)threadIdx.x / G, gl = (int)threadIdx.x % G;
+  const int k = a.cb[c] + (b - a.bb[c]) * (kLevelThreads / G) + grp;
+  const bool valid = k < a.cb[c + 1];
+  CGUnit d{0, 0, 0, -1, 0};
+  if (valid) d = a.units[k];
+  const double* C = a.C + d.off;
+  const int32_t* I = a.I + d.off;
+  auto X = [&](int ix) { return ix < a.n ? a.xa[ix] : a.xb[ix - a.n]; };
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = gl; j < d.len; j += 4 * G) {
+    const bool b1 = j + G < d.len, b2 = j + 2 * G < d.len, b3 = j + 3 * G < d.len;
+    const double c0 = __ldg(C + j);
+    const double c1 = b1 ? __ldg(C + j + G) : 0.0;
+    const double c2 = b2 ? __ldg(C + j + 2 * G) : 0.0;
+    const double c3 = b3 ? __ldg(C + j + 3 * G) : 0.0;
+    const int i0 = __ldg(I + j);
+    const int i1 = b1 ? __ldg(I + j + G) : i0;
+    const int i2 = b2 ? __ldg(I + j + 2 * G) : i0;
+    const int i3 = b3 ? __ldg(I + j + 3 * G) : i0;
+    const double x0 = X(i0), x1 = X(i1), x2 = X(i2), x3 = X(i3);
+    s0 = fma(c0, x0, s0);
+    s1 = fma(c1, x1, s1);
+    s2 = fma(c2, x2, s2);
+    s3 = fma(c3, x3, s3);
+  }
+  double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (!valid || gl != 0) return;
+  if (!a.fwd) {
+    a.rp[d.dst] = s;
+    a.u[d.aux] = s;
+  } else if (d.aux < 0) {
+    a.y[d.dst] = s;
+  } else {
+    a.rp[d.dst] = X(d.aux) - s;
+  }
+}
+
+__global__ void __launch_bounds__(kLevelThreads) k_level_sweep(LevelArgs a) {
+  const int b = blockIdx.x;
+  int c = 0;   // the block's class (the block ranges ascend with the class)
+#pragma unroll
+  for (int q = 1; q < kLevelClasses; ++q) c += b >= a.bb[q];
+  switch (c) {
+    case 0: level_group<32, 0>(a, b); break;
+    case 1: level_group<16, 1>(a, b); break;
+    case 2: level_group<8, 2>(a, b); break;
+    case 3: level_group<4, 3>(a, b); break;
+    case 4: level_group<2, 4>(a, b); break;
+    default: level_group<1, 5>(a, b); break;
+  }
+}
+
+// ---- block form (one right-hand side, large factors) --------------------------------------
+// One launch per phase; one block per work item (a chunk of rows of one
+// supernode). The block assembles the node's front vector in shared memory
+// (forward: r at the pivots plus the children's contribution vectors,
+// children one after another so the sums have a fixed order; backward: y at
+// the pivots and u at the update set's positions), then groups of G lanes
+// take one row each: the row's coefficients are read contiguously (four per
+// lane in flight), multiplied with the front from shared memory and summed
+// by shuffles within the group.
+constexpr int kBlockThreads = 256;
+
+struct BlockArgs {
+  const SNode* nodes;
+  const int32_t* kids;
+  const int32_t* cmap;
+  const int32_t* upd;
+  const BlockItem* items;    // this phase's items
+  const double* F;
+  const double* B;
+  const double* r;           // right-hand side at the pivots (positions): r, or r' after gather-form levels
+  double* y;                 // forward result (positions)
+  double* u;                 // solution (positions)
+  double* cbuf;              // contribution vectors
+  int kmin;                  // children below this height ran the gather form (their contributions are in r')
+};
+
+// sum over j in [j0, j1) of m[j] v[j] by a group of G lanes (lane gl), the
+// total on every lane of the group
+template <int G>
+__device__ __forceinline__ double group_dot(const double* __restrict__ m, const double* v, int j0, int j1, int gl) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = j0 + gl; j < j1; j += 4 * G) {
+    const bool b1 = j + G < j1, b2 = j + 2 * G < j1, b3 = j + 3 * G < j1;
+    const double m0 = __ldg(m + j);
+    const double m1 = b1 ? __ldg(m + j + G) : 0.0;
+    const double m2 = b2 ? __ldg(m + j + 2 * G) : 0.0;
+    const double m3 = b3 ? __ldg(m + j + 3 * G) : 0.0;
+    s0 = fma(m0, v[j], s0);
+    s1 = fma(m1, b1 ? v[j + G] : 0.0, s1);
+    s2 = fma(m2, b2 ? v[j + 2 * G] : 0.0, s2);
+    s3 = fma(m3, b3 ? v[j + 3 * G] : 0.0, s3);
+  }
+  double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Rows [row0, row0 + nrows) of node d by groups of G lanes: thread t of the
+// cooperating threads (T of them: a block, or a warp for a small node) is
+// lane t % G of group t / G.
+template <int G, int T>
+__device__ __forceinline__ void block_fwd_rows(const BlockArgs& a, int row0, int nrows, const SNode& d,
+                                               const double* f, int t) {
+  const int grp = t / G, gl = t % G;
+  const int end = row0 + nrows;
+  for (int base = row0; base < end; base += T / G) {
+    const int row = base + grp;
+    const bool valid = row < end;
+    const int len = !valid ? 0 : row < d.p ? row + 1 : d.p;
+    const double s = group_dot<G>(a.F + d.foff + (int64_t)(valid ? row : 0) * d.fld, f, 0, len, gl);
+    if (valid && gl == 0) {
+      if (row < d.p)
+        a.y[d.pos0 + row] = s;
+      else
+        a.cbuf[d.cbase + row - d.p] = f[row] - s;
+    }
+  }
+}
+
+template <int G, int T>
+__device__ __forceinline__ void block_bwd_rows(const BlockArgs& a, int row0, int nrows, const SNode& d,
+                                               const double* v, int t) {
+  const int grp = t / G, gl = t % G;
+  const int end = row0 + nrows, f = d.p + d.u;
+  for (int base = row0; base < end; base += T / G) {
+    const int row = base + grp;
+    const bool valid = row < end;
+    const double s = group_dot<G>(a.B + d.boff + (int64_t)(valid ? row : 0) * d.bld, v, valid ? row : f, f, gl);
+    if (valid && gl == 0) a.u[d.pos0 + row] = s;
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void fwd_rows(const BlockArgs& a, const BlockItem& it, const SNode& d, const double* f,
+                                         int t) {
+  switch (it.g) {
+    case 32: block_fwd_rows<32, T>(a, it.row0, it.nrows, d, f, t); break;
+    case 16: block_fwd_rows<16, T>(a, it.row0, it.nrows, d, f, t); break;
+    case 8: block_fwd_rows<8, T>(a, it.row0, it.nrows, d, f, t); break;
+    default: block_fwd_rows<4, T>(a, it.row0, it.nrows, d, f, t); break;
+  }
+}
+template <int T>
+__device__ __forceinline__ void bwd_rows(const BlockArgs& a, const BlockItem& it, const SNode& d, const double* v,
+                                         int t) {
+  switch (it.g) {
+    case 32: block_bwd_rows<32, T>(a, it.row0, it.nrows, d, v, t); break;
+    case 16: block_bwd_rows<16, T>(a, it.row0, it.nrows, d, v, t); break;
+    case 8: block_bwd_rows<8, T>(a, it.row0, it.nrows, d, v, t); break;
+    default: block_bwd_rows<4, T>(a, it.row0, it.nrows, d, v, t); break;
+  }
+}
+
+// Blocks [0, nbig): one chunk of a large node each (the front assembled by
+// the whole block); the later blocks: kBlockThreads / 32 small nodes each,
+// one per warp (its front in the warp's slice of kSmallFront values).
+__global__ void __launch_bounds__(kBlockThreads) k_block_fwd(BlockArgs a, int nbig, int nitems) {
+  extern __shared__ double smem[];
+  if ((int)blockIdx.x < nbig) {
+    const BlockItem it = a.items[blockIdx.x];
+    const SNode d = a.nodes[it.node];
+    const int f = d.p + d.u;
+    for (int i = threadIdx.x; i < f; i += kBlockThreads) smem[i] = i < d.p ? a.r[d.pos0 + i] : 0.0;
+    __syncthreads();
+    for (int q = 0; q < d.nkid; ++q) {
+      const SNode k = a.nodes[a.kids[d.kid0 + q]];
+      if (k.height < a.kmin) continue;   // uniform across the block
+      for (int i = threadIdx.x; i < k.u; i += kBlockThreads) smem[a.cmap[k.cmap0 + i]] += a.cbuf[k.cbase + i];
+      __syncthreads();
+    }
+    fwd_rows<kBlockThreads>(a, it, d, smem, threadIdx.x);
+    return;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = nbig + ((int)blockIdx.x - nbig) * (kBlockThreads / 32) + w;
+  if (k >= nitems) return;   // the whole warp (no block-wide barrier below)
+  double* f = smem + w * kSmallFront;
+  const BlockItem it = a.items[k];
+  const SNode d = a.nodes[it.node];
+  const int fs = d.p + d.u;
+  for (int i = lane; i < fs; i += 32) f[i] = i < d.p ? a.r[d.pos0 + i] : 0.0;
+  __syncwarp();
+  for (int q = 0; q < d.nkid; ++q) {
+    const SNode kd = a.nodes[a.kids[d.kid0 + q]];
+    if (kd.height < a.kmin) continue;
+    for (int i = lane; i < kd.u; i += 32) f[a.cmap[kd.cmap0 + i]] += a.cbuf[kd.cbase + i];
+    __syncwarp();
+  }
+  fwd_rows<32>(a, it, d, f, lane);
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_block_bwd(BlockArgs a, int nbig, int nitems) {
+  extern __shared__ double smem[];
+  if ((int)blockIdx.x < nbig) {
+    const BlockItem it = a.items[blockIdx.x];
+    const SNode d = a.nodes[it.node];
+    const int f = d.p + d.u;
+    for (int i = threadIdx.x; i < f; i += kBlockThreads)
+      smem[i] = i < d.p ? a.y[d.pos0 + i] : a.u[a.upd[d.upd_off + i - d.p]];
+    __syncthreads();
+    bwd_rows<kBlockThreads>(a, it, d, smem, threadIdx.x);
+    return;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = nbig + ((int)blockIdx.x - nbig) * (kBlockThreads / 32) + w;
+  if (k >= nitems) return;
+  double* v = smem + w * kSmallFront;
+  const BlockItem it = a.items[k];
+  const SNode d = a.nodes[it.node];
+  const int fs = d.p + d.u;
+  for (int i = lane; i < fs; i += 32) v[i] = i < d.p ? a.y[d.pos0 + i] : a.u[a.upd[d.upd_off + i - d.p]];
+  __syncwarp();
+  bwd_rows<32>(a, it, d, v, lane);
+}
+
 // ---- inexact coarse solve: plain CG on A_c (all columns in lockstep) ---------------------
 //
 // One cooperative persistent launch per coarse solve. Rows of A_c (CSR, glob
@@ -731,15 +977,29 @@ cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
 
 namespace {
 
-cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, int blocks) {
+cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, int blocks, bool level_form) {
   GatherLayout g;
   const int nb[2] = {blocks, blocks}, wpb[2] = {kGThreadsWide / 32, kGThreadsNarrow / 32};
-  gather_layout(cf, 2, nb, wpb, g);
+  gather_layout(cf, level_form ? 0 : 2, nb, wpb, g);
   S.g_entries = (int64_t)g.C.size();
   S.g_blocks = blocks;
+  const int L = cf.n_levels;
+  S.gbytes_h.assign(L, 0);
+  if (level_form)
+    for (int ph = 0; ph < 2 * L; ++ph) {
+      int64_t len = 0;
+      for (int64_t k = g.seq_off[ph]; k < g.seq_off[ph + 1]; ++k) len += g.seq[k].len;
+      S.gbytes_h[ph < L ? ph : 2 * L - 1 - ph] += 12 * len;
+    }
   cudaError_t e;
   if ((e = up(h, &S.gC, g.C)) != cudaSuccess) return e;
+  std::vector<double>().swap(g.C);
   if ((e = up(h, &S.gI, g.I)) != cudaSuccess) return e;
+  std::vector<int32_t>().swap(g.I);
+  if (level_form) {
+    level_phases(g, S.lv);
+    return up(h, &S.seq, g.seq);
+  }
   for (int sh = 0; sh < 2; ++sh) {
     if ((e = up(h, &S.gU[sh], g.units[sh])) != cudaSuccess) return e;
     if ((e = up(h, &S.gwo[sh], g.wo[sh])) != cudaSuccess) return e;
@@ -763,7 +1023,8 @@ cudaError_t build_coarse_cg_device(bddc_handle_s* h) {
   return cudaSuccess;
 }
 
-cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req) {
+cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req,
+                         int form) {
   const int L = cf.n_levels;
   S.levels = L;
   S.n = cf.n;
@@ -810,16 +1071,78 @@ cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
                                                          kGThreadsNarrow, 0)) != cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorNotSupported;
-  if ((e = build_gather(h, cf, S, blocks_req > 0 ? std::min(blocks_req, sms) : sms)) != cudaSuccess) return e;
-  if (!multi) return cudaSuccess;
-  std::vector<double> F((size_t)std::max<int64_t>(fcur, 1), 0.0), B((size_t)std::max<int64_t>(bcur, 1), 0.0);
-  for (int t = 0; t < nn; ++t) {
-    const CoarseNode& T = cf.nodes[t];
-    const int f = T.p + T.u;
-    for (int r = 0; r < f; ++r)
-      std::memcpy(&F[nodes[t].foff + (int64_t)r * nodes[t].fld], &T.Fm[(size_t)r * T.p], sizeof(double) * T.p);
-    for (int r = 0; r < T.p; ++r)
-      std::memcpy(&B[nodes[t].boff + (int64_t)r * nodes[t].bld], &T.Bm[(size_t)r * f], sizeof(double) * f);
+  // one-column form: the block form where every front fits in shared
+  // memory, else the per-level gather form
+  BlockLayout bl;
+  bool block = form == kSweepBlock;
+  if (block) {
+    block_layout(cf, kBlockTarget, bl);
+    block = bl.max_front <= kBlockMaxFront;
+    for (int t = 0; t < nn && block; ++t)
+      if (bl.nodes[t].foff != nodes[t].foff || bl.nodes[t].boff != nodes[t].boff) return cudaErrorInvalidValue;
+  }
+  // the gather form (the block form keeps its per-level launches for the
+  // low levels, whose nodes are too small for a block of their own)
+  if ((e = build_gather(h, cf, S, blocks_req > 0 ? std::min(blocks_req, sms) : sms, form != kSweepCoop)) !=
+      cudaSuccess)
+    return e;
+  S.read_1col = S.g_entries * 12;
+  if (block) {
+    S.block_form = true;
+    S.bitem_off = bl.item_off;
+    S.bn_big = bl.n_big;
+    S.bphase_front.assign(bl.item_off.size() - 1, 0);
+    int64_t entries = 0;
+    for (size_t ph = 0; ph + 1 < bl.item_off.size(); ++ph)
+      for (int64_t k = bl.item_off[ph]; k < bl.item_off[ph + 1]; ++k) {
+        const SNode& d = bl.nodes[bl.items[k].node];
+        if (k < bl.item_off[ph] + bl.n_big[ph]) S.bphase_front[ph] = std::max(S.bphase_front[ph], d.p + d.u);
+      }
+    // default split: every level in the gather form (measured fastest on the
+    // 2D workloads of 10^4 and 7.8 10^4 dofs per subdomain, each level
+    // against the block form); the autotuner tries every split
+    S.block_min_height = L;
+    // bytes of one one-column solve per height: the block form reads the
+    // lower part of F and the upper part of B once each, the gather form its
+    // coefficients and indices
+    S.bbytes_h.assign(L, 0);
+    for (const SNode& d : bl.nodes) {
+      const int64_t ent = (int64_t)d.p * (d.p + 1) / 2 + (int64_t)d.u * d.p;
+      S.bbytes_h[d.height] += 2 * 8 * ent;
+      entries += ent;
+    }
+    if ((e = up(h, &S.bnodes, bl.nodes)) != cudaSuccess) return e;
+    if ((e = up(h, &S.bkids, bl.kids)) != cudaSuccess) return e;
+    if ((e = up(h, &S.bcmap, bl.cmap)) != cudaSuccess) return e;
+    if ((e = up(h, &S.bupd, bl.upd)) != cudaSuccess) return e;
+    if ((e = up(h, &S.bitems, bl.items)) != cudaSuccess) return e;
+    if ((e = up(h, &S.cbuf, std::vector<double>((size_t)std::max<int64_t>(bl.cbuf, 1), 0.0))) != cudaSuccess)
+      return e;
+    const int smem = bl.max_front * (int)sizeof(double);
+    if (smem > 48 * 1024) {
+      if ((e = cudaFuncSetAttribute(k_block_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(k_block_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+        return e;
+    }
+  }
+  if (!multi && !block) return cudaSuccess;
+  std::vector<double> F, B;
+  if (block) {
+    // the block layout's node matrices: the same offsets (same order and alignment)
+    F.swap(bl.F);
+    B.swap(bl.B);
+  } else {
+    F.assign((size_t)std::max<int64_t>(fcur, 1), 0.0);
+    B.assign((size_t)std::max<int64_t>(bcur, 1), 0.0);
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      const int f = T.p + T.u;
+      for (int r = 0; r < f; ++r)
+        std::memcpy(&F[nodes[t].foff + (int64_t)r * nodes[t].fld], &T.Fm[(size_t)r * T.p], sizeof(double) * T.p);
+      for (int r = 0; r < T.p; ++r)
+        std::memcpy(&B[nodes[t].boff + (int64_t)r * nodes[t].bld], &T.Bm[(size_t)r * f], sizeof(double) * f);
+    }
   }
   std::vector<int32_t> pos(cf.n);
   for (int64_t i = 0; i < cf.n; ++i) pos[cf.order[i]] = (int32_t)i;
@@ -879,6 +1202,7 @@ cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
   std::vector<double>().swap(F);
   if ((e = up(h, &S.B, B)) != cudaSuccess) return e;
   std::vector<double>().swap(B);
+  if (!multi) return cudaSuccess;
   if ((e = up(h, &S.nodes, nodes)) != cudaSuccess) return e;
   if ((e = up(h, &S.units, units)) != cudaSuccess) return e;
   if ((e = up(h, &S.units4, units4)) != cudaSuccess) return e;
@@ -906,7 +1230,7 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   cudaDeviceGetAttribute(&h->c_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->d_cbar == nullptr && (e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
   h->cs.bar = h->d_cbar;
-  if ((e = build_sweeps(h, cf, h->cs, true, h->g_blocks)) != cudaSuccess) return e;
+  if ((e = build_sweeps(h, cf, h->cs, true, h->g_blocks, kSweepCoop)) != cudaSuccess) return e;
   h->c_nnz = h->cs.nnz;
   return cudaSuccess;
 }
@@ -946,6 +1270,58 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
   attr[0].val.cooperative = 1;
   const unsigned int extra = inject ? h->cbar_extra : 0u;
   const long long cycles = inject ? h->cbar_cycles : kBarrierWaitCycles;
+  if (nrhs == 1 && S.block_form) {
+    // heights below kmin: the per-level gather form (r' starts as a copy of
+    // r, the backward sweeps read u by position); heights from kmin on: the
+    // block form (fronts from r' and the block-form children)
+    const int L = S.levels, kmin = std::max(0, std::min(S.block_min_height, L));
+    auto level_phase = [&](int ph, bool fwd) {
+      const SweepSet::LevelPhase& P = S.lv[ph];
+      const int nblk = P.bb[kLevelClasses];
+      if (nblk == 0) return;
+      LevelArgs la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : u, rp, y, u, (int)S.n, fwd ? 1 : 0, {}, {}};
+      std::memcpy(la.cb, P.cb, sizeof(la.cb));
+      std::memcpy(la.bb, P.bb, sizeof(la.bb));
+      k_level_sweep<<<nblk, kLevelThreads, 0, st>>>(la);
+      h->launches++;
+    };
+    if (kmin > 0 &&
+        (e = cudaMemcpyAsync(rp, r, sizeof(double) * S.n, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return e;
+    for (int ph = 0; ph < kmin; ++ph) level_phase(ph, true);
+    for (int ph = kmin; ph < 2 * L - kmin; ++ph) {
+      const int64_t k0 = S.bitem_off[ph], nblk = S.bitem_off[ph + 1] - k0;
+      if (nblk == 0) continue;
+      BlockArgs ba{S.bnodes, S.bkids, S.bcmap, S.bupd, S.bitems + k0, S.F, S.B, kmin > 0 ? rp : r, y, u, S.cbuf,
+                   kmin};
+      const int nbig = (int)S.bn_big[ph], nsmall = (int)nblk - nbig;
+      const int grid = nbig + (nsmall + kBlockThreads / 32 - 1) / (kBlockThreads / 32);
+      const size_t smem = (size_t)std::max(S.bphase_front[ph], nsmall > 0 ? (kBlockThreads / 32) * kSmallFront : 0) *
+                          sizeof(double);
+      if ((int)ph < S.levels)
+        k_block_fwd<<<grid, kBlockThreads, smem, st>>>(ba, nbig, (int)nblk);
+      else
+        k_block_bwd<<<grid, kBlockThreads, smem, st>>>(ba, nbig, (int)nblk);
+      h->launches++;
+    }
+    for (int ph = 2 * L - kmin; ph < 2 * L; ++ph) level_phase(ph, false);
+    return cudaGetLastError();
+  }
+  if (nrhs == 1 && !S.lv.empty()) {
+    // per-level form: one launch per phase, forward levels then backward
+    for (size_t ph = 0; ph < S.lv.size(); ++ph) {
+      const SweepSet::LevelPhase& P = S.lv[ph];
+      const int nblk = P.bb[kLevelClasses];
+      if (nblk == 0) continue;
+      const bool fwd = (int)ph < S.levels;
+      LevelArgs la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n, fwd ? 1 : 0, {}, {}};
+      std::memcpy(la.cb, P.cb, sizeof(la.cb));
+      std::memcpy(la.bb, P.bb, sizeof(la.bb));
+      k_level_sweep<<<nblk, kLevelThreads, 0, st>>>(la);
+      h->launches++;
+    }
+    return cudaGetLastError();
+  }
   if ((e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   if (nrhs == 1 && S.gC) {
     const int sh = narrow ? 1 : 0;

@@ -179,6 +179,8 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
   std::vector<int32_t>& gI = g.I;
   gC.clear();
   gI.clear();
+  g.seq.clear();
+  g.seq_off.assign(1, 0);
   g.units.assign(nshapes, {});
   g.wo.assign(nshapes, {});
   for (int sh = 0; sh < nshapes; ++sh)
@@ -261,6 +263,7 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
         d.aux = cf.order[pos0 + x.i];
       }
       desc[k] = d;
+      g.seq.push_back(d);
     }
     // per launch shape: longest first to the least-loaded warp (cost: batches
     // of kGatherBatch, and a quarter batch per unit for its reduction and store);
@@ -288,6 +291,7 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
       }
       wrow[nw] = (int32_t)gu.size();
     }
+    g.seq_off.push_back((int64_t)g.seq.size());
     if (fwd)
       for (const GU& x : us)
         if (x.kind == 1) has[x.a] = 1;
@@ -463,6 +467,129 @@ int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
     }
   }
   return BDDC_OK;
+}
+
+void level_phases(const GatherLayout& g, std::vector<SweepSet::LevelPhase>& out) {
+  out.clear();
+  for (size_t ph = 0; ph + 1 < g.seq_off.size(); ++ph) {
+    SweepSet::LevelPhase P{};
+    P.u0 = g.seq_off[ph];
+    const int32_t m = (int32_t)(g.seq_off[ph + 1] - g.seq_off[ph]);
+    int32_t k = 0;
+    for (int c = 0; c < kLevelClasses; ++c) {
+      P.cb[c] = k;
+      while (k < m && level_class(g.seq[P.u0 + k].len) <= c) ++k;
+    }
+    P.cb[kLevelClasses] = m;
+    P.bb[0] = 0;
+    for (int c = 0; c < kLevelClasses; ++c) {
+      const int per = kLevelThreads / kLevelGroup[c];
+      P.bb[c + 1] = P.bb[c] + (P.cb[c + 1] - P.cb[c] + per - 1) / per;
+    }
+    out.push_back(P);
+  }
+}
+
+void block_layout(const CoarseFactor& cf, int64_t target, BlockLayout& out) {
+  out = BlockLayout();
+  const int nn = (int)cf.nodes.size(), L = cf.n_levels;
+  out.nodes.resize(nn);
+  int64_t fcur = 0, bcur = 0, ccur = 0;
+  for (int t = 0; t < nn; ++t) {
+    const CoarseNode& T = cf.nodes[t];
+    SNode& d = out.nodes[t];
+    d.p = T.p;
+    d.u = T.u;
+    d.pos0 = T.last - T.p + 1;
+    d.fld = std::max(T.p, 1);
+    d.bld = std::max(T.p + T.u, 1);
+    fcur = (fcur + 31) / 32 * 32;   // the layout of the several-column node matrices
+    d.foff = fcur;
+    fcur += (int64_t)(T.p + T.u) * d.fld;
+    bcur = (bcur + 31) / 32 * 32;
+    d.boff = bcur;
+    bcur += (int64_t)T.p * d.bld;
+    d.cbase = (int32_t)ccur;
+    ccur += T.u;
+    d.cmap0 = 0;
+    d.upd_off = (int32_t)out.upd.size();
+    out.upd.insert(out.upd.end(), T.upd.begin(), T.upd.end());
+    d.kid0 = (int32_t)out.kids.size();
+    d.nkid = (int32_t)T.children.size();
+    d.height = T.height;
+    out.kids.insert(out.kids.end(), T.children.begin(), T.children.end());
+    out.max_front = std::max(out.max_front, T.p + T.u);
+  }
+  out.cbuf = ccur;
+  // each child's update set as indices into its parent's front: the
+  // parent's pivots (contiguous positions), then its update set
+  std::vector<int32_t> where(cf.n, -1);
+  for (int q = 0; q < nn; ++q) {
+    const CoarseNode& Q = cf.nodes[q];
+    if (Q.children.empty()) continue;
+    const SNode& dq = out.nodes[q];
+    for (int i = 0; i < Q.p; ++i) where[dq.pos0 + i] = i;
+    for (int b = 0; b < Q.u; ++b) where[Q.upd[b]] = Q.p + b;
+    for (int k : Q.children) {
+      out.nodes[k].cmap0 = (int32_t)out.cmap.size();
+      for (int32_t w : cf.nodes[k].upd) out.cmap.push_back(where[w]);
+    }
+    for (int i = 0; i < Q.p; ++i) where[dq.pos0 + i] = -1;
+    for (int b = 0; b < Q.u; ++b) where[Q.upd[b]] = -1;
+  }
+  out.F.assign((size_t)std::max<int64_t>(fcur, 1), 0.0);
+  out.B.assign((size_t)std::max<int64_t>(bcur, 1), 0.0);
+  for (int t = 0; t < nn; ++t) {
+    const CoarseNode& T = cf.nodes[t];
+    const SNode& d = out.nodes[t];
+    const int f = T.p + T.u;
+    for (int r = 0; r < f && T.p > 0; ++r)
+      std::memcpy(&out.F[d.foff + (int64_t)r * d.fld], &T.Fm[(size_t)r * T.p], sizeof(double) * T.p);
+    for (int r = 0; r < T.p; ++r)
+      std::memcpy(&out.B[d.boff + (int64_t)r * d.bld], &T.Bm[(size_t)r * f], sizeof(double) * f);
+  }
+  // work items: chunks of rows, largest chunks of a phase first
+  out.item_off.assign(1, 0);
+  std::vector<BlockItem> small;
+  auto chunks = [&](int t, int rows, int len) {
+    const SNode& d = out.nodes[t];
+    if (d.p + d.u <= kSmallFront) {
+      small.push_back(BlockItem{t, 0, rows, block_group(len)});
+      return;
+    }
+    const int64_t per = std::max<int64_t>(1, target / std::max(len, 1));
+    const int R = (int)std::min<int64_t>(rows, std::max<int64_t>(8, per));
+    for (int r0 = 0; r0 < rows; r0 += R)
+      out.items.push_back(BlockItem{t, r0, std::min(R, rows - r0), block_group(len)});
+  };
+  auto close_phase = [&](bool fwd) {
+    auto work = [&](const BlockItem& x) {
+      const SNode& a = out.nodes[x.node];
+      return (int64_t)x.nrows * (fwd ? a.p : a.p + a.u);
+    };
+    auto heavier = [&](const BlockItem& x, const BlockItem& y) { return work(x) > work(y); };
+    const int64_t b = out.item_off.back();
+    std::stable_sort(out.items.begin() + b, out.items.end(), heavier);
+    out.n_big.push_back((int64_t)out.items.size() - b);
+    std::stable_sort(small.begin(), small.end(), heavier);
+    out.items.insert(out.items.end(), small.begin(), small.end());
+    small.clear();
+    out.item_off.push_back((int64_t)out.items.size());
+  };
+  for (int lv = 0; lv < L; ++lv) {
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      if (T.height == lv && T.p + T.u > 0) chunks(t, T.p + T.u, T.p);
+    }
+    close_phase(true);
+  }
+  for (int lv = L - 1; lv >= 0; --lv) {
+    for (int t = 0; t < nn; ++t) {
+      const CoarseNode& T = cf.nodes[t];
+      if (T.height == lv && T.p > 0) chunks(t, T.p, T.p + T.u);
+    }
+    close_phase(false);
+  }
 }
 
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,

@@ -55,6 +55,10 @@ struct GatherLayout {
   std::vector<int32_t> I;
   std::vector<std::vector<CGUnit>> units;
   std::vector<std::vector<int32_t>> wo;
+  // every phase's descriptors in storage order (longest unit first), phase
+  // ph at [seq_off[ph], seq_off[ph + 1]): the per-level launches
+  std::vector<CGUnit> seq;
+  std::vector<int64_t> seq_off;
 };
 void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const int* warps_per_block,
                    GatherLayout& g);
@@ -64,6 +68,21 @@ struct CContrib {
   int32_t x_off;    // elimination position of the node's first pivot
   int32_t len;      // p of the node
   int64_t pad;
+};
+// Block form of the one-column sweeps: one supernode and one chunk of its
+// rows (see BlockLayout below).
+struct SNode {
+  int64_t foff, boff;     // F: (p + u) x fld, B: p x bld (row-major)
+  int32_t p, u, pos0;
+  int32_t fld, bld;
+  int32_t cbase;          // this node's contribution vector c (u values) in the contribution buffer
+  int32_t cmap0;          // its map into the parent's front (u indices)
+  int32_t kid0, nkid;     // children: kids[kid0 .. kid0 + nkid)
+  int32_t upd_off;        // positions of the update set: upd[upd_off .. upd_off + u)
+  int32_t height;         // height in the elimination tree (leaves 0)
+};
+struct BlockItem {
+  int32_t node, row0, nrows, g;
 };
 // Device form of one supernodal factorisation and of its sweeps
 // (coarse_solve.cu): the coarse factor of A_c, or the forest of the
@@ -93,7 +112,91 @@ struct SweepSet {
   int64_t g_entries = 0;        // stored entries of the gather form
   int64_t update_total = 0;     // sum of the update-set sizes
   bool multi = false;           // F, B and the unit lists built (several right-hand sides)
+  // per-level form (one right-hand side, large factors): one launch per
+  // phase; a phase's units are in classes of decreasing length, class c
+  // processed by groups of kLevelGroup[c] lanes: units [cb[c], cb[c+1]) of
+  // the phase's descriptors (seq + u0), blocks [bb[c], bb[c+1]) of its grid
+  struct LevelPhase {
+    int64_t u0;
+    int32_t cb[7], bb[7];
+  };
+  CGUnit* seq = nullptr;
+  std::vector<LevelPhase> lv;
+  // block form (one right-hand side, large factors; see BlockLayout): node
+  // records, children, maps into the parents' fronts, update positions,
+  // work items per phase, the contribution buffer; F and B above
+  bool block_form = false;
+  SNode* bnodes = nullptr;
+  int32_t* bkids = nullptr;
+  int32_t* bcmap = nullptr;
+  int32_t* bupd = nullptr;
+  BlockItem* bitems = nullptr;
+  double* cbuf = nullptr;
+  std::vector<int64_t> bitem_off;
+  int block_min_height = 0;        // levels below this height run the per-level gather form
+  std::vector<int64_t> bn_big;     // per phase: items that are chunks of large nodes (listed first)
+  std::vector<int> bphase_front;   // largest front of each phase's large nodes
+  int64_t read_1col = 0;           // bytes of coefficients and indices one one-column solve of the gather form reads
+  std::vector<int64_t> gbytes_h, bbytes_h;   // the same per height: gather form, block form
 };
+// Bytes of coefficients (and indices) one one-column solve reads in the
+// form the set runs (the block form's split included).
+inline int64_t sweep_read_1col(const SweepSet& S) {
+  if (!S.block_form) return S.read_1col;
+  const int k = S.block_min_height < 0 ? 0 : S.block_min_height > S.levels ? S.levels : S.block_min_height;
+  int64_t b = 0;
+  for (int lv = 0; lv < S.levels; ++lv) b += lv < k ? S.gbytes_h[lv] : S.bbytes_h[lv];
+  return b;
+}
+// forms of the one-column sweeps (build_sweeps)
+constexpr int kSweepCoop = 0;       // gather form, one cooperative launch (small factors)
+constexpr int kSweepLevel = 1;      // gather form, one launch per phase
+constexpr int kSweepBlock = 2;      // block form, one launch per phase (large factors)
+constexpr int64_t kBlockTarget = 8192;   // matrix entries per work item of the block form
+constexpr int kSmallFront = 128;         // fronts up to this size: one warp per node (8 per block)
+constexpr int kBlockMaxFront = 16384;    // largest front of the block form (shared memory)
+constexpr int kLevelThreads = 256;
+constexpr int kLevelClasses = 6;
+constexpr int kLevelGroup[kLevelClasses] = {32, 16, 8, 4, 2, 1};
+// The class of a unit of len coefficients: the narrowest group that still
+// reads about four coefficients per lane.
+inline int level_class(int len) {
+  if (len >= 128) return 0;
+  if (len >= 48) return 1;
+  if (len >= 20) return 2;
+  if (len >= 8) return 3;
+  if (len >= 3) return 4;
+  return 5;
+}
+// The per-level form of a gather layout (seq, seq_off): every phase's class
+// ranges and block counts (kLevelThreads / G units per block of class G).
+void level_phases(const GatherLayout& g, std::vector<SweepSet::LevelPhase>& out);
+
+// Block form of the one-column sweeps (large factors; dofs numbered in
+// elimination order): supernode by supernode, with the node's dense
+// matrices streamed row by row. Forward, node t: its front f (p + u values)
+// = r at its pivots plus its children's contribution vectors (each child's
+// update set mapped into t's front, children in order); y_P = L_PP^-1 f_P
+// and the contribution c_t = f_U - M f_P (rows of F). Backward: u_P = [L_PP^-T,
+// -M^T] [y_P; u_U] (rows of B), u_U read at the update set's positions.
+// A work item is a chunk of rows of one node, processed by one block with
+// `g` lanes per row.
+struct BlockLayout {
+  std::vector<SNode> nodes;
+  std::vector<int32_t> kids, cmap, upd;
+  std::vector<BlockItem> items;       // forward levels (height 0 first), then backward levels
+  std::vector<int64_t> item_off;      // 2 L + 1 phase offsets into items
+  std::vector<int64_t> n_big;         // per phase: its first n_big items are chunks of large nodes
+                                      // (one block each); the rest are whole small nodes (one warp each)
+  std::vector<double> F, B;
+  int64_t cbuf = 0;                   // contribution buffer size (sum of u)
+  int max_front = 0;                  // largest p + u
+};
+// Builds the block form of cf (which must be renumbered: order = identity):
+// nodes whose front has more than kSmallFront values in chunks of about
+// target_entries matrix entries, the others whole.
+void block_layout(const CoarseFactor& cf, int64_t target_entries, BlockLayout& out);
+inline int block_group(int len) { return len >= 128 ? 32 : len >= 48 ? 16 : len >= 20 ? 8 : 4; }
 
 // Tensor-core batched GEMM (bddc_tc_gemm.cu). A dense n x n operator is
 // stored as chunks of up to 128 rows x kTcChunkK(precision) columns in the

@@ -80,7 +80,13 @@ cudaError_t launch_scatter_rows(int64_t n, int nrhs, const int32_t* perm, const 
 // uploads cf (dofs numbered in elimination order or not) into S: the gather
 // form for one right-hand side on a grid of blocks_req blocks (0 = one per
 // SM), and with `multi` also the node matrices and unit lists for several.
-cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req);
+// form: kSweepCoop (one cooperative launch of the gather form: small
+// factors), kSweepLevel (gather form, one launch per phase, sub-warp groups
+// sized to the rows) or kSweepBlock (supernode by supernode with the dense
+// node matrices streamed, one launch per phase; the level form where a front
+// does not fit in shared memory).
+cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req,
+                         int form);
 // u = A^-1 r by the forward and backward sweeps of S, level by level, in one
 // cooperative launch (r and u: S.n x nrhs in dof order; rp and y: work
 // vectors of the same size). inject: the barriers take the handle's test

@@ -17,7 +17,12 @@
 // from the partial factorisation against the dense one); then merges the
 // interior factors into one forest as the device does (each renumbered by
 // elimination order), emulates its gather-form sweeps as above, and checks
-// the result against the dense A_II^-1 r of every subdomain to 1e-10.
+// the result against the dense A_II^-1 r of every subdomain to 1e-10; and
+// checks the per-level form (class ranges and block counts of every phase;
+// the sweeps with each phase's units in storage order give bitwise the same
+// result) and the block form (supernode by supernode: fronts from the
+// children's contribution vectors, chunks of rows; every row covered once,
+// nothing read before the phase that writes it) against the dense solves.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -105,6 +110,124 @@ int emulate(const CoarseFactor& cf, const GatherLayout& gl, int sh, int nw, cons
   printf("%s shape %d warps: n %d levels %d races %d nan-reads %d write-count %d\n", what, nw, n, L, races,
          nanreads, once);
   return bad + races + nanreads + once;
+}
+
+// Emulates the one-column sweeps as the block form runs them with split
+// height kmin: heights below kmin as per-level gather phases (gl.seq; r'
+// starts as a copy of r; backward operands u by position), heights from kmin
+// on supernode by supernode (fronts from r' and the children from kmin on);
+// each phase's writes applied at its end, as the next launch sees them. r in
+// positions; u receives the result. Returns the number of failed checks
+// (indices out of range, rows not covered exactly once, reads of values not
+// yet written).
+int emulate_block(const CoarseFactor& cf, const BlockLayout& bl, const GatherLayout& gl, int kmin,
+                  const std::vector<double>& r, std::vector<double>& u) {
+  const int n = (int)cf.n, L = cf.n_levels;
+  const double nan = std::nan("");
+  std::vector<double> y(n, nan), cb(bl.cbuf, nan), rp(n, nan);
+  if (kmin > 0) rp = r;
+  u.assign(n, nan);
+  int bad = 0, nanreads = 0;
+  std::vector<int> fcover(bl.nodes.size(), 0), bcover(bl.nodes.size(), 0);
+  if (bl.item_off.size() != (size_t)2 * L + 1 || bl.item_off.back() != (int64_t)bl.items.size() ||
+      bl.n_big.size() != (size_t)2 * L || gl.seq_off.size() != (size_t)2 * L + 1)
+    ++bad;
+  // a phase's first n_big items are chunks of nodes with fronts above
+  // kSmallFront, the rest whole nodes with fronts up to it
+  for (int ph = 0; ph < 2 * L && !bad; ++ph)
+    for (int64_t k = bl.item_off[ph]; k < bl.item_off[ph + 1]; ++k) {
+      const SNode& d = bl.nodes[bl.items[k].node];
+      const bool big = k < bl.item_off[ph] + bl.n_big[ph];
+      if (big != (d.p + d.u > kSmallFront)) ++bad;
+      if (!big && (bl.items[k].row0 != 0 || bl.items[k].nrows != (ph < L ? d.p + d.u : d.p))) ++bad;
+      if (d.height != (ph < L ? ph : 2 * L - 1 - ph)) ++bad;
+    }
+  for (int ph = 0; ph < 2 * L && !bad; ++ph) {
+    const bool fwd = ph < L;
+    const int height = fwd ? ph : 2 * L - 1 - ph;
+    std::vector<std::pair<int64_t, double>> wy, wc, wu, wrp;
+    if (height < kmin) {
+      // gather phase
+      for (int64_t k = gl.seq_off[ph]; k < gl.seq_off[ph + 1]; ++k) {
+        const CGUnit& d = gl.seq[k];
+        auto X = [&](int ix) {
+          const double v = fwd ? (ix < n ? rp[ix] : r[ix - n]) : (ix < n ? y[ix] : u[ix - n]);
+          if (std::isnan(v)) ++nanreads;
+          return v;
+        };
+        double sum = 0;
+        for (int j = 0; j < d.len; ++j) sum += gl.C[d.off + j] * X(gl.I[d.off + j]);
+        if (!fwd) {
+          wrp.push_back({d.dst, sum});
+          wu.push_back({d.aux, sum});
+        } else if (d.aux < 0) {
+          wy.push_back({d.dst, sum});
+        } else {
+          wrp.push_back({d.dst, X(d.aux) - sum});
+        }
+      }
+    } else {
+      for (int64_t k = bl.item_off[ph]; k < bl.item_off[ph + 1]; ++k) {
+        const BlockItem& it = bl.items[k];
+        const SNode& d = bl.nodes[it.node];
+        const int f = d.p + d.u;
+        if (it.g != 4 && it.g != 8 && it.g != 16 && it.g != 32) ++bad;
+        if (it.row0 < 0 || it.nrows < 1 || it.row0 + it.nrows > (fwd ? f : d.p)) { ++bad; continue; }
+        (fwd ? fcover : bcover)[it.node] += it.nrows;
+        std::vector<double> v(f, 0.0);
+        if (fwd) {
+          for (int i = 0; i < d.p; ++i) {
+            v[i] = kmin > 0 ? rp[d.pos0 + i] : r[d.pos0 + i];
+            if (std::isnan(v[i])) ++nanreads;
+          }
+          for (int q = 0; q < d.nkid; ++q) {
+            const SNode& kd = bl.nodes[bl.kids[d.kid0 + q]];
+            if (kd.height < kmin) continue;
+            for (int a = 0; a < kd.u; ++a) {
+              const int32_t w = bl.cmap[kd.cmap0 + a];
+              const double c = cb[kd.cbase + a];
+              if (w < 0 || w >= f) { ++bad; continue; }
+              if (std::isnan(c)) ++nanreads;
+              v[w] += c;
+            }
+          }
+          for (int row = it.row0; row < it.row0 + it.nrows; ++row) {
+            const int len = row < d.p ? row + 1 : d.p;
+            double sum = 0;
+            for (int j = 0; j < len; ++j) sum += bl.F[d.foff + (int64_t)row * d.fld + j] * v[j];
+            if (row < d.p) wy.push_back({d.pos0 + row, sum});
+            else wc.push_back({d.cbase + row - d.p, v[row] - sum});
+          }
+        } else {
+          for (int i = 0; i < d.p; ++i) {
+            v[i] = y[d.pos0 + i];
+            if (std::isnan(v[i])) ++nanreads;
+          }
+          for (int b2 = 0; b2 < d.u; ++b2) {
+            const int32_t w = bl.upd[d.upd_off + b2];
+            if (w < 0 || w >= n) { ++bad; continue; }
+            v[d.p + b2] = u[w];
+            if (std::isnan(v[d.p + b2])) ++nanreads;
+          }
+          for (int row = it.row0; row < it.row0 + it.nrows; ++row) {
+            double sum = 0;
+            for (int j = row; j < f; ++j) sum += bl.B[d.boff + (int64_t)row * d.bld + j] * v[j];
+            wu.push_back({d.pos0 + row, sum});
+          }
+        }
+      }
+    }
+    for (auto& q : wy) y[q.first] = q.second;
+    for (auto& q : wc) cb[q.first] = q.second;
+    for (auto& q : wu) u[q.first] = q.second;
+    for (auto& q : wrp) rp[q.first] = q.second;
+  }
+  for (size_t t = 0; t < bl.nodes.size(); ++t)
+    if (bl.nodes[t].height >= kmin && (fcover[t] != bl.nodes[t].p + bl.nodes[t].u || bcover[t] != bl.nodes[t].p))
+      ++bad;
+  printf("block form, split %d: %zu items, largest front %d, bad %d, nan-reads %d\n", kmin, bl.items.size(),
+         bl.max_front, bad, nanreads);
+  return bad + nanreads;
 }
 
 void parse_shapes(int argc, char** argv, int a0, std::vector<int>& nb, std::vector<int>& wpb) {
@@ -273,6 +396,68 @@ static int local_mode(int argc, char** argv) {
     printf("  sweeps against the dense A_II^-1 r: largest relative difference %.2e\n", err2);
     if (!(err2 < 1e-10)) ++bad;
     us.push_back(u);
+  }
+  // the per-level form: class ranges and block counts of every phase, and
+  // the sweeps with each phase's units in storage order (one launch per
+  // phase) give bitwise the result of the shapes above
+  {
+    std::vector<SweepSet::LevelPhase> lv;
+    level_phases(gl, lv);
+    int lbad = 0;
+    if ((int)lv.size() != 2 * forest.n_levels || gl.seq_off.back() != (int64_t)gl.seq.size()) ++lbad;
+    for (size_t ph = 0; ph < lv.size(); ++ph) {
+      const SweepSet::LevelPhase& P = lv[ph];
+      const int64_t m = gl.seq_off[ph + 1] - gl.seq_off[ph];
+      if (P.u0 != gl.seq_off[ph] || P.cb[0] != 0 || P.cb[kLevelClasses] != m || P.bb[0] != 0) ++lbad;
+      for (int c = 0; c < kLevelClasses; ++c) {
+        const int per = kLevelThreads / kLevelGroup[c];
+        const int cnt = P.cb[c + 1] - P.cb[c];
+        if (cnt < 0 || P.bb[c + 1] - P.bb[c] != (cnt + per - 1) / per) ++lbad;
+        for (int k = P.cb[c]; k < P.cb[c + 1]; ++k)
+          if (level_class(gl.seq[P.u0 + k].len) != c) ++lbad;
+      }
+    }
+    GatherLayout one = gl;
+    one.units.assign(1, gl.seq);
+    one.wo.assign(1, std::vector<int32_t>());
+    for (size_t ph = 0; ph < lv.size(); ++ph) {
+      one.wo[0].push_back((int32_t)gl.seq_off[ph]);
+      one.wo[0].push_back((int32_t)gl.seq_off[ph + 1]);
+    }
+    std::vector<double> u;
+    lbad += emulate(forest, one, 0, 1, r, u, "per-level form");
+    for (int i = 0; i < n && !us.empty(); ++i)
+      if (u[i] != us[0][i]) {
+        ++lbad;
+        break;
+      }
+    printf("  per-level form: %zu phases, %s\n", lv.size(), lbad ? "FAILED" : "ok");
+    bad += lbad;
+  }
+  // the block form, with chunks small enough that big nodes span several,
+  // pure and split at every height
+  GatherLayout gseq;
+  gather_layout(forest, 0, nullptr, nullptr, gseq);
+  for (int64_t target : {64, 4096})
+  for (int kmin = 0; kmin <= forest.n_levels; kmin += (target == 64 ? 1 : forest.n_levels)) {
+    BlockLayout bl;
+    block_layout(forest, target, bl);
+    std::vector<double> u;
+    int bbad = emulate_block(forest, bl, gseq, kmin, r, u);
+    double err2 = 0;
+    for (int s = 0; s < S; ++s) {
+      const int nI = ioff[s + 1] - ioff[s];
+      std::vector<double> xd(nI, 0.0), xs(nI);
+      for (int l = 0; l < nI; ++l) {
+        for (int m = 0; m < nI; ++m) xd[l] += hd.AIIinv[s][(size_t)l * nI + m] * r[ioff[s] + iperm[s][m]];
+        xs[l] = u[ioff[s] + iperm[s][l]];
+      }
+      err2 = std::max(err2, rel_diff(xs, xd));
+    }
+    printf("  block form (chunks of %lld entries, split %d) against the dense A_II^-1 r: %.2e\n", (long long)target,
+           kmin, err2);
+    if (!(err2 < 1e-10)) ++bbad;
+    bad += bbad;
   }
   for (size_t sh = 1; sh < us.size(); ++sh)
     for (int i = 0; i < n; ++i)

@@ -43,13 +43,14 @@ def test_gather_layout_emulates_the_exact_coarse_solve(checker, ne, nsub, jitter
 
 # The sparse local solver (host side): the Schur complement from the partial
 # factorisation gives the dense path's K_GG, Phi_G and A_ci to 1e-10, and the
-# gather-form sweeps of the merged interior forest, emulated as the kernel
-# runs them, give the dense A_II^-1 r of every subdomain to 1e-10. Cases: 2D
-# and 3D cubes, a jittered partition (uneven subdomains), leaf size 1 (every
-# dissection down to single dofs), the default leaf 32 on 32^2-element
-# subdomains.
+# sweeps of the merged interior forest (gather form in every launch shape,
+# per-level form, block form), emulated as the kernels run them, give the
+# dense A_II^-1 r of every subdomain to 1e-10. Cases: 2D and 3D cubes, a
+# jittered partition (uneven subdomains), leaf size 1 (every dissection down
+# to single dofs), the default leaf 32 on 32^2-element subdomains, and 12^3-
+# element cubes whose fronts exceed one warp's share (large nodes in chunks).
 @pytest.mark.parametrize("dim,ne,nsub,jitter,leaf", [(2, 32, 2, 0, 16), (3, 24, 3, 1, 16), (3, 16, 2, 0, 1),
-                                                     (2, 64, 2, 0, 32)])
+                                                     (2, 64, 2, 0, 32), (3, 24, 2, 0, 32)])
 def test_interior_forest_emulates_the_dense_interior_solves(checker, dim, ne, nsub, jitter, leaf):
     r = subprocess.run([checker, "local", str(dim), str(ne), str(nsub), str(jitter), str(leaf), "1:16", "3:16",
                         "152:16", "152:8"], capture_output=True, text=True, timeout=300)

@@ -114,6 +114,29 @@ def test_leaf_sizes_give_the_same_preconditioner(leaf):
     g.close()
 
 
+@pytest.mark.parametrize("name", ["2d_96_2x2", "3d_voronoi_large_cells"])
+def test_every_split_height_gives_the_same_preconditioner(name):
+    """The one-column interior sweeps split at every height (gather form
+    below, block form from it on: all gather, all block, and each mix) give
+    M^-1 r to the float64 bound; the autotuner's choice is one of them."""
+    p, mask, tol, o = _case(name)
+    R = _residuals(o, 1, 86)
+    Z = o.apply_nodes(R)[:, 0]
+    g = _bddc(p, mask, precision="fp64")
+    L = g.info()["interior_levels"]
+    r = _cuda(R[:, 0])
+    for k in range(L + 1):
+        t = g.get_tuning()
+        t["interior_block_height"] = k
+        g.set_tuning(t)
+        assert g.get_tuning()["interior_block_height"] == k
+        assert _rel(g.apply(r).cpu().numpy(), Z) < tol, k
+    t = g.autotune(1)
+    assert 0 <= t["interior_block_height"] <= L
+    assert _rel(g.apply(r).cpu().numpy(), Z) < tol
+    g.close()
+
+
 def test_sparse_and_dense_local_solvers_agree():
     p, mask, tol, o = _case("3d_voronoi_large_cells")
     R = _residuals(o, 8, 84)
