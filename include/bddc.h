@@ -300,13 +300,17 @@ typedef struct {
                                          supernode by supernode with the node matrices streamed;
                                          0..64, clamped to the forest's levels (default: all levels
                                          in the gather form) */
+    int32_t coarse_level_launches;    /* sparse coarse solve, one column: 1 = one launch per level of
+                                         the gather form (sub-warp groups per factor row), 0 = one
+                                         cooperative launch with grid barriers (default) */
 } bddc_tuning_t;
 
 /* Time the candidate launch parameters for blocks of nrhs columns (row
  * tiles of 64, 128 and 256 rows and stage sizes of 6, 12, 24 and 48 KB of
  * the streamed GEMV of each operator family when the handle uses it, or for
  * the symmetric GEMV 3 or 4 stages of 10 to 24 KB;
- * one-row against four-row coarse sweep units when nrhs >= 2; every split
+ * one-row against four-row coarse sweep units when nrhs >= 2; one launch
+ * against one launch per level of the one-column coarse sweeps; every split
  * height of the sparse local solver's interior sweeps at one column; whole
  * applies with and without the coarse overlap), apply the fastest and return
  * them in *out (may be NULL).

@@ -41,7 +41,7 @@ class Tuning(C.Structure):
                 ("coarse_rowblock_min_nrhs", C.c_int32), ("gemv_rows_interior", C.c_int32),
                 ("gemv_rows_interface", C.c_int32), ("coarse_overlap", C.c_int32),
                 ("sym_stages_interior", C.c_int32), ("sym_stages_interface", C.c_int32),
-                ("interior_block_height", C.c_int32)]
+                ("interior_block_height", C.c_int32), ("coarse_level_launches", C.c_int32)]
 
 
 class Problem(C.Structure):

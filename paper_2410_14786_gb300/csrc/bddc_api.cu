@@ -1204,7 +1204,8 @@ int bddc_get_tuning(bddc_handle_t h, bddc_tuning_t* out) {
   if (!h || !out) return fail(BDDC_ERR_INVALID_ARG, "null handle or output");
   *out = bddc_tuning_t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min,
                        64 << h->tune_tile_class[0], 64 << h->tune_tile_class[1], h->tune_overlap,
-                       h->tune_sym_stages[0], h->tune_sym_stages[1], h->is.block_min_height};
+                       h->tune_sym_stages[0], h->tune_sym_stages[1], h->is.block_min_height,
+                       h->cs.use_level ? 1 : 0};
   return BDDC_OK;
 }
 
@@ -1225,6 +1226,8 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
     return fail(BDDC_ERR_INVALID_ARG, "symmetric GEMV stages must be 3 or 4");
   if (in->interior_block_height < 0 || in->interior_block_height > 64)
     return fail(BDDC_ERR_INVALID_ARG, "interior_block_height must be 0..64");
+  if (in->coarse_level_launches != 0 && in->coarse_level_launches != 1)
+    return fail(BDDC_ERR_INVALID_ARG, "coarse_level_launches must be 0 or 1");
   h->tune_tile_class[0] = tile_class(in->gemv_rows_interior);
   h->tune_tile_class[1] = tile_class(in->gemv_rows_interface);
   h->tune_overlap = in->coarse_overlap;
@@ -1233,6 +1236,7 @@ int bddc_set_tuning(bddc_handle_t h, const bddc_tuning_t* in) {
   h->tune_sym_stages[0] = in->sym_stages_interior;
   h->tune_sym_stages[1] = in->sym_stages_interface;
   h->tune_coarse_rb_min = in->coarse_rowblock_min_nrhs;
+  h->cs.use_level = in->coarse_level_launches == 1 && !h->cs.lv.empty();
   if (h->is.block_form) {
     // the interior sweeps' bytes per solve follow the split
     const int64_t before = sweep_read_1col(h->is);
@@ -1270,7 +1274,7 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
   };
   bddc_tuning_t t{h->tune_stage_kb[0], h->tune_stage_kb[1], h->tune_coarse_rb_min, 64 << h->tune_tile_class[0],
                   64 << h->tune_tile_class[1], h->tune_overlap, h->tune_sym_stages[0], h->tune_sym_stages[1],
-                  h->is.block_min_height};
+                  h->is.block_min_height, h->cs.use_level ? 1 : 0};
   cudaError_t ce = cudaSuccess;
   if ((ce = cudaMemsetAsync(h->w.rI, 0, sizeof(double) * std::max<int64_t>(h->nI_tot, 1) * nrhs, st)) ||
       (ce = cudaMemsetAsync(h->w.yG, 0, sizeof(double) * std::max<int64_t>(h->nG_tot, 1) * nrhs, st))) {
@@ -1334,6 +1338,17 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     h->is.block_min_height = keep;
     t.interior_block_height = best_k;
   }
+  if (h->n_c && !h->coarse_dense && !h->coarse_cg && nrhs == 1 && !h->cs.lv.empty()) {
+    // one cooperative launch against one launch per level
+    CUDA_TRY(cudaMemsetAsync(h->w.rc, 0, sizeof(double) * h->n_c, st));
+    const bool keep = h->cs.use_level;
+    h->cs.use_level = false;
+    const float coop = timed([&] { return launch_coarse_solve(h, h->w, h->w.rc, h->w.uc, 1, st); });
+    h->cs.use_level = true;
+    const float lev = timed([&] { return launch_coarse_solve(h, h->w, h->w.rc, h->w.uc, 1, st); });
+    h->cs.use_level = keep;
+    if (coop >= 0.0f && lev >= 0.0f) t.coarse_level_launches = lev < coop ? 1 : 0;
+  }
   if (h->n_c && !h->coarse_dense && !h->coarse_cg && nrhs >= 2) {
     CUDA_TRY(cudaMemsetAsync(h->w.rc, 0, sizeof(double) * h->n_c * nrhs, st));
     const int keep = h->tune_coarse_rb_min;
@@ -1350,6 +1365,8 @@ int bddc_autotune(bddc_handle_t h, int32_t nrhs, bddc_tuning_t* out, void* strea
     h->tune_stage_kb[0] = t.gemv_stage_kb_interior;
     h->tune_stage_kb[1] = t.gemv_stage_kb_interface;
     h->tune_coarse_rb_min = t.coarse_rowblock_min_nrhs;
+    h->cs.use_level = t.coarse_level_launches == 1 && !h->cs.lv.empty();
+    h->is.block_min_height = std::min(t.interior_block_height, h->is.levels);
     double* rz = nullptr;
     const size_t nv = (size_t)h->n_nodes * nrhs;
     if (cudaMalloc(&rz, 2 * nv * sizeof(double)) == cudaSuccess) {

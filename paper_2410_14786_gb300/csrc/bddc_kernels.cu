@@ -156,10 +156,12 @@ __global__ void __launch_bounds__(kThreads) k_bgemv(const WorkItem* __restrict__
 // One thread per (row, block of CB columns; CB = 1 measured fastest for 1 to
 // 64 columns: more threads hide more latency), the CSR loop unrolled so that
 // the loads of several nonzeros are in flight together.
+// y'_G = W r_G - A_GI t_I (rows: interface copies; cols: compact interior).
 template <int CB, bool ONE>
 __global__ void k_iface_rhs(int64_t nG, int nrhs_, const int32_t* __restrict__ ptr,
                             const int32_t* __restrict__ col, const double* __restrict__ val,
-                            const double* __restrict__ tI, double* __restrict__ yG) {
+                            const double* __restrict__ tI, const int32_t* __restrict__ gnode,
+                            const double* __restrict__ gw, const double* __restrict__ r, double* __restrict__ yG) {
   const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = nG * ncb;
@@ -180,9 +182,11 @@ __global__ void k_iface_rhs(int64_t nG, int nrhs_, const int32_t* __restrict__ p
         if (kb + c < nrhs) s[c] = fma(v, tp[c], s[c]);
     }
     double* yp = yG + q * nrhs + kb;
+    const double* rp = r + (int64_t)gnode[q] * nrhs + kb;
+    const double w = gw[q];
 #pragma unroll
     for (int c = 0; c < CB; ++c)
-      if (kb + c < nrhs) yp[c] -= s[c];
+      if (kb + c < nrhs) yp[c] = w * rp[c] - s[c];
   }
 }
 
@@ -271,14 +275,21 @@ __global__ void __launch_bounds__(kThreads) k_phi_prolong(int n_sub, int nrhs, c
 }
 
 // z[node] = sum over the copies q of the node of W_q (z_G[q] + (Phi_G u_c)[q])
+// (and z = 0 at the Dirichlet nodes dnode[0 .. nD))
 template <int CB, bool ONE>
 __global__ void k_prolong_gather(int64_t n_gu, int nrhs_, const int32_t* __restrict__ gu_node,
                                  const int32_t* __restrict__ gu_ptr, const int32_t* __restrict__ gu_copy,
                                  const double* __restrict__ gw, const double* __restrict__ zG,
-                                 const double* __restrict__ eG, double* __restrict__ z) {
+                                 const double* __restrict__ eG, double* __restrict__ z,
+                                 const int32_t* __restrict__ dnode, int64_t nD) {
   const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = n_gu * ncb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nD * nrhs;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / nrhs;
+    z[(int64_t)dnode[e] * nrhs + (i - e * nrhs)] = 0.0;
+  }
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = t / ncb;
@@ -307,8 +318,8 @@ __global__ void k_prolong_gather(int64_t n_gu, int nrhs_, const int32_t* __restr
 template <int CB, bool ONE>
 __global__ void k_interior_rhs(int64_t nI, int nrhs_, const int32_t* __restrict__ ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ val,
-                               const double* __restrict__ rI, const double* __restrict__ z,
-                               double* __restrict__ bI) {
+                               const int32_t* __restrict__ inode, const double* __restrict__ r,
+                               const double* __restrict__ z, double* __restrict__ bI) {
   const int nrhs = ONE ? 1 : nrhs_;
   const int ncb = (nrhs + CB - 1) / CB;
   const int64_t total = nI * ncb;
@@ -316,7 +327,7 @@ __global__ void k_interior_rhs(int64_t nI, int nrhs_, const int32_t* __restrict_
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = t / ncb;
     const int kb = (int)(t - p * ncb) * CB;
-    const double* rp = rI + p * nrhs + kb;
+    const double* rp = r + (int64_t)inode[p] * nrhs + kb;
     double s[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) s[c] = kb + c < nrhs ? rp[c] : 0.0;
@@ -517,15 +528,18 @@ cudaError_t interior_sweeps(bddc_handle_s* h, const ApplyWork& W, const double* 
 // One batched application of the interior (A_II^-1) or interface (K_GG)
 // operators of all subdomains.
 // Y = Op X over the interior or interface operators; counts its launches.
+// xgather (symmetric GEMV only): the operand is read through it (see
+// launch_sgemv_tma).
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
-                     cudaStream_t st, int max_per_sm = 0) {
+                     cudaStream_t st, int max_per_sm = 0, const int32_t* xgather = nullptr) {
   if (interior && h->sparse_local) return interior_sweeps(h, h->w, X, Y, yscatter, nrhs, st);
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
   if (h->use_sym) {
     if (nrhs != 1) return cudaErrorInvalidValue;   // nrhs_max is 1 on this path
     h->launches += (interior ? h->n_wsy_I : h->n_wsy_G) > 0;
     return interior ? launch_sgemv_tma(h->precision, h->d_wsy_I, h->n_wsy_I, h->max_n_I, h->d_aii, X, Y, yscatter,
-                                       h->d_err, st, h->tune_stage_kb[0], h->tune_sym_stages[0], max_per_sm)
+                                       h->d_err, st, h->tune_stage_kb[0], h->tune_sym_stages[0], max_per_sm,
+                                       xgather)
                     : launch_sgemv_tma(h->precision, h->d_wsy_G, h->n_wsy_G, h->max_n_G, h->d_kgg, X, Y, yscatter,
                                        h->d_err, st, h->tune_stage_kb[1], h->tune_sym_stages[1], max_per_sm);
   }
@@ -594,19 +608,25 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
     if (ev) cudaEventRecord(ev[i], st);
   };
   mark(0);
-  // restriction + zero Dirichlet entries of z
-  const int64_t tot = (h->nI_tot + h->nG_tot + h->n_dir) * nrhs;
-  (nrhs == 1 ? k_restrict<true> : k_restrict<false>)<<<blocks_for(tot), kThreads, 0, st>>>(
-      r, nrhs, h->d_inode, h->nI_tot, h->d_gnode, h->d_gw, h->nG_tot, W.rI, W.yG, h->d_dnode, h->n_dir, z);
-  h->launches++;
+  // t_I = A_II^-1 r_I: the symmetric GEMV gathers r_I from r itself; the
+  // other engines read the compact r_I of the restriction
+  const bool gather_rI = h->use_sym && !h->sparse_local && nrhs == 1;
+  if (!gather_rI && h->nI_tot) {
+    (nrhs == 1 ? k_restrict<true> : k_restrict<false>)<<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(
+        r, nrhs, h->d_inode, h->nI_tot, nullptr, nullptr, 0, W.rI, nullptr, nullptr, 0, nullptr);
+    h->launches++;
+  }
   mark(1);
-  // t_I = A_II^-1 r_I
-  if ((e = local_op(h, true, W.rI, W.tI, nullptr, nrhs, st)) != cudaSuccess) return e;
+  if (gather_rI) {
+    if ((e = local_op(h, true, r, W.tI, nullptr, nrhs, st, 0, h->d_inode)) != cudaSuccess) return e;
+  } else {
+    if ((e = local_op(h, true, W.rI, W.tI, nullptr, nrhs, st)) != cudaSuccess) return e;
+  }
   mark(2);
   if (h->nG_tot) {
     // y'_G = W r_G - A_GI t_I; z_G = K_GG y'_G
     (nrhs == 1 ? k_iface_rhs<1, true> : k_iface_rhs<1, false>)<<<blocks_for(h->nG_tot * nrhs), kThreads, 0, st>>>(
-        h->nG_tot, nrhs, h->d_agi_ptr, h->d_agi_col, h->d_agi_val, W.tI, W.yG);
+        h->nG_tot, nrhs, h->d_agi_ptr, h->d_agi_col, h->d_agi_val, W.tI, h->d_gnode, h->d_gw, r, W.yG);
     h->launches++;
   }
   mark(3);
@@ -663,17 +683,22 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
       cudaMemsetAsync(W.eG, 0, sizeof(double) * h->nG_tot * nrhs, st);
       eG = W.eG;
     }
-    (nrhs == 1 ? k_prolong_gather<1, true> : k_prolong_gather<1, false>)<<<blocks_for(h->n_gu * nrhs), kThreads, 0,
-                                                                            st>>>(
-        h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr, h->d_gu_copy, h->d_gw, W.zG, eG, z);
+    (nrhs == 1 ? k_prolong_gather<1, true> : k_prolong_gather<1, false>)<<<
+        blocks_for(std::max(h->n_gu, h->n_dir) * nrhs), kThreads, 0, st>>>(
+        h->n_gu, nrhs, h->d_gu_node, h->d_gu_ptr, h->d_gu_copy, h->d_gw, W.zG, eG, z, h->d_dnode, h->n_dir);
+    h->launches++;
+  } else if (h->n_dir) {
+    k_zero_nodes<<<blocks_for(h->n_dir * nrhs), kThreads, 0, st>>>(h->n_dir, nrhs, h->d_dnode, z);
     h->launches++;
   }
   mark(7);
   // z_I = A_II^-1 (r_I - A_IG v_G)
-  (nrhs == 1 ? k_interior_rhs<1, true> : k_interior_rhs<1, false>)<<<blocks_for(h->nI_tot * nrhs), kThreads, 0,
-                                                                      st>>>(
-      h->nI_tot, nrhs, h->d_aig_ptr, h->d_aig_col, h->d_aig_val, W.rI, z, W.bI);
-  h->launches++;
+  if (h->nI_tot) {
+    (nrhs == 1 ? k_interior_rhs<1, true> : k_interior_rhs<1, false>)<<<blocks_for(h->nI_tot * nrhs), kThreads, 0,
+                                                                        st>>>(
+        h->nI_tot, nrhs, h->d_aig_ptr, h->d_aig_col, h->d_aig_val, h->d_inode, r, z, W.bI);
+    h->launches++;
+  }
   mark(8);
   if ((e = local_op(h, true, W.bI, z, h->d_inode, nrhs, st)) != cudaSuccess) return e;
   mark(9);

@@ -497,7 +497,8 @@ int host_setup(const bddc_problem_t* P, const bddc_options_t* O, HostSetup& hs, 
       }
       for (int32_t q = 0; q < P->n_sub; ++q)
         for (int d = 0; d < 3; ++d) sxyz[3 * q + d] /= (double)std::max<int64_t>(cnt[q], 1);
-      const int rc = coarse_factor(nC, hs.Ac_ptr, hs.Ac_col, hs.Ac_val, hs.glob_subs, sxyz, hs.cfac, err);
+      const int rc = coarse_factor(nC, hs.Ac_ptr, hs.Ac_col, hs.Ac_val, hs.glob_subs, sxyz, hs.cfac, err,
+                                   kCoarseDenseTop);
       if (rc != BDDC_OK) return rc;
     }
   }

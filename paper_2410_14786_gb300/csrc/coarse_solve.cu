@@ -438,9 +438,10 @@ struct GatherArgs {
   double* u;                 // u_c (dof order)
   unsigned int* bar;
   int32_t* err;
-  int levels, n_c;
+  int levels, n_c;           // levels: forward-type phases (forward levels, then a dense top's product)
   unsigned int bar_extra;
   long long bar_cycles;
+  int phases;                // all phases
 };
 
 // Coefficients and operand indices of one batch: elements base + lane + 32 i
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * (NT / 32);
   const int gw = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
-  const int P = 2 * a.levels;
+  const int P = a.phases;
   unsigned int epoch = 0;
   int beg = a.wo[gw], cnt = a.wo[gw + 1] - beg;
   CGUnit dl = gather_desc(a, beg, cnt, 0, lane);
@@ -983,9 +984,11 @@ cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
   gather_layout(cf, level_form ? 0 : 2, nb, wpb, g);
   S.g_entries = (int64_t)g.C.size();
   S.g_blocks = blocks;
+  S.g_fwd = g.fwd_phases;
+  S.g_phases = g.phases;
   const int L = cf.n_levels;
   S.gbytes_h.assign(L, 0);
-  if (level_form)
+  if (level_form && g.phases == 2 * L)
     for (int ph = 0; ph < 2 * L; ++ph) {
       int64_t len = 0;
       for (int64_t k = g.seq_off[ph]; k < g.seq_off[ph + 1]; ++k) len += g.seq[k].len;
@@ -996,10 +999,12 @@ cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
   std::vector<double>().swap(g.C);
   if ((e = up(h, &S.gI, g.I)) != cudaSuccess) return e;
   std::vector<int32_t>().swap(g.I);
-  if (level_form) {
-    level_phases(g, S.lv);
-    return up(h, &S.seq, g.seq);
-  }
+  // the per-level form always (for the cooperative form it is the
+  // alternative the autotuner measures)
+  level_phases(g, S.lv);
+  if ((e = up(h, &S.seq, g.seq)) != cudaSuccess) return e;
+  S.use_level = level_form;
+  if (level_form) return cudaSuccess;
   for (int sh = 0; sh < 2; ++sh) {
     if ((e = up(h, &S.gU[sh], g.units[sh])) != cudaSuccess) return e;
     if ((e = up(h, &S.gwo[sh], g.wo[sh])) != cudaSuccess) return e;
@@ -1307,13 +1312,13 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
     for (int ph = 2 * L - kmin; ph < 2 * L; ++ph) level_phase(ph, false);
     return cudaGetLastError();
   }
-  if (nrhs == 1 && !S.lv.empty()) {
+  if (nrhs == 1 && S.use_level && !S.lv.empty()) {
     // per-level form: one launch per phase, forward levels then backward
     for (size_t ph = 0; ph < S.lv.size(); ++ph) {
       const SweepSet::LevelPhase& P = S.lv[ph];
       const int nblk = P.bb[kLevelClasses];
       if (nblk == 0) continue;
-      const bool fwd = (int)ph < S.levels;
+      const bool fwd = (int)ph < S.g_fwd;
       LevelArgs la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n, fwd ? 1 : 0, {}, {}};
       std::memcpy(la.cb, P.cb, sizeof(la.cb));
       std::memcpy(la.bb, P.bb, sizeof(la.bb));
@@ -1325,7 +1330,8 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
   if ((e = cudaMemsetAsync(S.bar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return e;
   if (nrhs == 1 && S.gC) {
     const int sh = narrow ? 1 : 0;
-    GatherArgs g{S.gU[sh], S.gwo[sh], S.gC, S.gI, r, rp, y, u, S.bar, h->d_err, S.levels, (int)S.n, extra, cycles};
+    GatherArgs g{S.gU[sh], S.gwo[sh], S.gC, S.gI, r, rp, y, u, S.bar, h->d_err, S.g_fwd, (int)S.n, extra, cycles,
+                 S.g_phases};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S.g_blocks);
     cfg.blockDim = dim3(narrow ? kGThreadsNarrow : kGThreadsWide);

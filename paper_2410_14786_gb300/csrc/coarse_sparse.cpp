@@ -30,6 +30,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "dense.hpp"
@@ -165,7 +166,9 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
   for (int32_t i = 0; i < n; ++i) pos[cf.order[i]] = i;
   for (int t = 0; t < nn; ++t) first[t] = cf.nodes[t].last - cf.nodes[t].p + 1;
   // kind 0: row i of node a (forward); kind 1: receiving position a with
-  // contributions [cb, ce) of rlist; kind 2: row i of node a (backward)
+  // contributions [cb, ce) of rlist; kind 2: row i of node a (backward);
+  // kind 3: row a of the dense top's inverse; kind 4: copy of y to u at the
+  // dense top's dof a
   struct GU {
     int32_t kind, a, i, len, cb, ce;
   };
@@ -181,22 +184,38 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
   gI.clear();
   g.seq.clear();
   g.seq_off.assign(1, 0);
+  // dense top: the levels from height Ht on are one forward-type phase
+  // (kind 3: y_T = S_TT^-1 r'_T, row by row); the backward levels below read
+  // u_T from y, and the first of them also copies y_T to u (kind 4)
+  const int nT = (int)cf.top_pos.size();
+  const bool dtop = cf.top_levels > 0 && nT > 0 && (int64_t)cf.top_inv.size() == (int64_t)nT * nT;
+  const int Ht = dtop ? L - cf.top_levels : L;
+  const int nph = dtop ? 2 * Ht + 1 : 2 * L, nfwd = dtop ? Ht + 1 : L;
+  std::vector<int8_t> intop(n, 0);
+  if (dtop)
+    for (int32_t q : cf.top_pos) intop[q] = 1;
+  g.fwd_phases = nfwd;
+  g.phases = nph;
   g.units.assign(nshapes, {});
   g.wo.assign(nshapes, {});
   for (int sh = 0; sh < nshapes; ++sh)
-    g.wo[sh].assign((size_t)2 * L * (blocks[sh] * warps_per_block[sh] + 1), 0);
-  int64_t total = 0;
+    g.wo[sh].assign((size_t)nph * (blocks[sh] * warps_per_block[sh] + 1), 0);
+  int64_t total = dtop ? (int64_t)nT * (nT + 1) : 0;
   for (const CoarseNode& T : cf.nodes) total += 2 * (int64_t)T.p * (T.p + T.u);
   gC.reserve((size_t)total);
   gI.reserve((size_t)total);
   std::vector<std::vector<int32_t>> per;
-  for (int ph = 0; ph < 2 * L; ++ph) {
-    const bool fwd = ph < L;
-    const int lv = fwd ? ph : 2 * L - 1 - ph;
+  for (int ph = 0; ph < nph; ++ph) {
+    const bool fwd = ph < nfwd;
+    const int lv = fwd ? ph : nph - 1 - ph;
     us.clear();
     rlist.clear();
     touched.clear();
-    for (int t = 0; t < nn; ++t) {
+    if (dtop && ph == Ht)
+      for (int i = 0; i < nT; ++i) us.push_back(GU{3, i, 0, nT, 0, 0});
+    if (dtop && !fwd && lv == Ht - 1)
+      for (int i = 0; i < nT; ++i) us.push_back(GU{4, i, 0, 1, 0, 0});
+    for (int t = 0; t < nn && !(dtop && ph == Ht); ++t) {
       const CoarseNode& T = cf.nodes[t];
       if (T.height != lv || T.p == 0) continue;
       for (int i = 0; i < T.p; ++i) us.push_back(GU{fwd ? 0 : 2, t, i, fwd ? i + 1 : T.p - i + T.u, 0, 0});
@@ -247,7 +266,7 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
         }
         d.dst = x.a;
         d.aux = xf(x.a);
-      } else {
+      } else if (x.kind == 2) {
         const CoarseNode& T = cf.nodes[x.a];
         const int32_t pos0 = first[x.a];
         const size_t f = (size_t)T.p + T.u;
@@ -256,11 +275,23 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
           gI.push_back(pos0 + j);
         }
         for (int b = 0; b < T.u; ++b) {
+          const int32_t q = pos[T.upd[b]];
           gC.push_back(T.Bm[(size_t)x.i * f + T.p + b]);
-          gI.push_back(n + pos[T.upd[b]]);
+          gI.push_back(intop[q] ? q : n + q);   // u_T is y_T
         }
         d.dst = pos0 + x.i;
         d.aux = cf.order[pos0 + x.i];
+      } else if (x.kind == 3) {
+        for (int j = 0; j < nT; ++j) {
+          gC.push_back(cf.top_inv[(size_t)x.a * nT + j]);
+          gI.push_back(xf(cf.top_pos[j]));
+        }
+        d.dst = cf.top_pos[x.a];
+      } else {
+        gC.push_back(1.0);
+        gI.push_back(cf.top_pos[x.a]);
+        d.dst = cf.top_pos[x.a];
+        d.aux = cf.order[cf.top_pos[x.a]];
       }
       desc[k] = d;
       g.seq.push_back(d);
@@ -301,7 +332,7 @@ void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const
 int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_groups,
                   const std::vector<double>& group_xyz, int64_t n_keep, int leaf, CoarseFactor& cf,
-                  std::vector<double>* schur, std::string& err) {
+                  std::vector<double>* schur, std::string& err, int64_t top_max) {
   cf = CoarseFactor();
   cf.n = n;
   const int64_t nf = n - n_keep;        // dofs eliminated
@@ -354,6 +385,35 @@ int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
     cf.n_levels = std::max(cf.n_levels, hgt + 1);
   }
 
+  // ---- dense top: the most top levels with at most top_max dofs --------------------
+  // (T: the pivots of the nodes of height >= Ht; its Schur complement S
+  // collects A_TT and the update matrices of the nodes below T whose
+  // parents are in T)
+  int Ht = -1, nT = 0;
+  std::vector<int32_t> tidx;
+  std::vector<double> S;
+  if (top_max > 0 && n_keep == 0 && cf.n_levels >= 2) {
+    std::vector<int64_t> ph(cf.n_levels, 0);
+    for (const CoarseNode& T : cf.nodes) ph[T.height] += T.p;
+    int64_t cum = 0;
+    for (int h = cf.n_levels - 1; h >= 1; --h) {
+      if (cum + ph[h] > top_max) break;
+      cum += ph[h];
+      Ht = h;
+    }
+  }
+  if (Ht >= 1) {
+    for (const CoarseNode& T : cf.nodes)
+      if (T.height >= Ht)
+        for (int32_t v : T.piv) cf.top_pos.push_back(pos[v]);
+    std::sort(cf.top_pos.begin(), cf.top_pos.end());
+    nT = (int)cf.top_pos.size();
+    tidx.assign(n, -1);
+    for (int i = 0; i < nT; ++i) tidx[cf.order[cf.top_pos[i]]] = i;
+    S.assign((size_t)nT * nT, 0.0);
+    cf.top_levels = cf.n_levels - Ht;
+  }
+
   // ---- numeric: multifrontal ------------------------------------------------------------
   std::vector<int32_t> loc(n, -1);
   std::vector<std::vector<double>> upd_mat(nn);
@@ -386,6 +446,11 @@ int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
         const int la = loc[K.upd[a]];
         for (int b = 0; b < K.u; ++b) F[(size_t)la * f + loc[K.upd[b]]] += Uk[(size_t)a * K.u + b];
       }
+      if (Ht >= 1 && T.height >= Ht && K.height < Ht)
+        for (int a = 0; a < K.u; ++a) {
+          const size_t ra = (size_t)tidx[K.upd[a]] * nT;
+          for (int b = 0; b < K.u; ++b) S[ra + tidx[K.upd[b]]] += Uk[(size_t)a * K.u + b];
+        }
       std::vector<double>().swap(upd_mat[k]);
     }
     for (int i = 0; i < p; ++i) loc[T.piv[i]] = -1;
@@ -439,6 +504,25 @@ int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
         std::memcpy(&upd_mat[t][(size_t)a * u], &F[(size_t)a * f], sizeof(double) * u);
     }
     cf.nnz += (int64_t)f * p;
+  }
+  if (Ht >= 1) {
+    // S_TT = A_TT + (the update matrices gathered above); its inverse is (A^-1)_TT
+    for (int i = 0; i < nT; ++i) {
+      const int32_t v = cf.order[cf.top_pos[i]];
+      for (int64_t j = rp[v]; j < rp[v + 1]; ++j)
+        if (tidx[ci[j]] >= 0) S[(size_t)i * nT + tidx[ci[j]]] += val[j];
+    }
+    for (int i = 0; i < nT; ++i)
+      for (int j = i + 1; j < nT; ++j) {
+        const double m = 0.5 * (S[(size_t)i * nT + j] + S[(size_t)j * nT + i]);
+        S[(size_t)i * nT + j] = S[(size_t)j * nT + i] = m;
+      }
+    const int threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    if (dense::spd_inverse(nT, S.data(), nT, threads) >= 0) {
+      err = "the Schur complement of the coarse factor's top levels is not positive definite";
+      return BDDC_ERR_SINGULAR;
+    }
+    cf.top_inv = std::move(S);
   }
   if (n_keep > 0) {
     // drop the kept front and the kept dofs from every update set (a suffix:
@@ -594,8 +678,8 @@ void block_layout(const CoarseFactor& cf, int64_t target, BlockLayout& out) {
 
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
-                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err) {
-  return sparse_factor(n, rp, ci, val, dof_subs, sub_xyz, 0, kLeaf, cf, nullptr, err);
+                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err, int64_t top_max) {
+  return sparse_factor(n, rp, ci, val, dof_subs, sub_xyz, 0, kLeaf, cf, nullptr, err, top_max);
 }
 
 void merge_forest(const std::vector<CoarseFactor>& parts, const std::vector<int32_t>& off, CoarseFactor& out) {

@@ -45,7 +45,9 @@ struct CGUnit {
 // b * warps_per_block[s] + w) the descriptors of warp w in phase ph are
 // units[s][wo[s][ph (warps+1) + w] .. wo[s][ph (warps+1) + w + 1]), processed
 // in that order. Phases 0 .. L-1 are the forward levels (height = phase),
-// phases L .. 2L-1 the backward levels (height = 2L-1-phase).
+// phases L .. 2L-1 the backward levels (height = 2L-1-phase); with a dense
+// top of k levels, phases 0 .. L-k-1 are the forward levels below it, phase
+// L-k the dense product, then the backward levels from height L-k-1 down.
 struct CoarseFactor;
 constexpr int kLocalLeaf = 32;      // default leaf size of the interior factorisations
 constexpr int kGatherBatch = 256;   // coefficients a warp reads per step of a unit (cost unit of the assignment)
@@ -59,6 +61,9 @@ struct GatherLayout {
   // ph at [seq_off[ph], seq_off[ph + 1]): the per-level launches
   std::vector<CGUnit> seq;
   std::vector<int64_t> seq_off;
+  // phases: fwd_phases forward-type phases (the forward levels, then the
+  // dense top's product if the factor has one), then the backward levels
+  int fwd_phases = 0, phases = 0;
 };
 void gather_layout(const CoarseFactor& cf, int nshapes, const int* blocks, const int* warps_per_block,
                    GatherLayout& g);
@@ -104,10 +109,11 @@ struct SweepSet {
   double* gC = nullptr;
   int32_t* gI = nullptr;
   CGUnit* gU[2] = {nullptr, nullptr};
-  int32_t* gwo[2] = {nullptr, nullptr};   // [2 L][warps + 1]
+  int32_t* gwo[2] = {nullptr, nullptr};   // [phases][warps + 1]
   unsigned int* bar = nullptr;
   int64_t n = 0;                // dofs
   int levels = 0, grid = 0, grid4 = 0, g_blocks = 0;
+  int g_fwd = 0, g_phases = 0;  // gather form: forward-type phases, all phases
   int64_t nnz = 0;              // stored entries of F and B
   int64_t g_entries = 0;        // stored entries of the gather form
   int64_t update_total = 0;     // sum of the update-set sizes
@@ -122,6 +128,7 @@ struct SweepSet {
   };
   CGUnit* seq = nullptr;
   std::vector<LevelPhase> lv;
+  bool use_level = false;       // one column: the per-level form (else the cooperative launch)
   // block form (one right-hand side, large factors; see BlockLayout): node
   // records, children, maps into the parents' fronts, update positions,
   // work items per phase, the contribution buffer; F and B above
@@ -245,7 +252,16 @@ struct CoarseFactor {
   std::vector<int32_t> order;    // elimination position -> coarse dof
   int n_levels = 0;              // 1 + largest node height (leaves have height 0)
   int64_t nnz = 0;               // stored entries of one sweep's matrices
+  // dense top (optional): the dofs of the nodes of the top `top_levels`
+  // levels (T, closed under ancestors; elimination positions, ascending) and
+  // the inverse of their Schur complement S_TT = A_TT - A_TB A_BB^-1 A_BT,
+  // which equals (A^-1)_TT: one dense product replaces the sweeps of those
+  // levels
+  int top_levels = 0;
+  std::vector<int32_t> top_pos;
+  std::vector<double> top_inv;   // |T| x |T|, row-major
 };
+constexpr int64_t kCoarseDenseTop = 2048;   // largest dense top of the coarse factor
 // Nested-dissection supernodal Cholesky of the SPD matrix (rp, ci, val)
 // (CSR, both triangles); xyz: 3 coordinates per dof for the dissection.
 // dof_subs: the subdomains of every coarse dof (glob); sub_xyz: centroid of
@@ -254,9 +270,11 @@ struct CoarseFactor {
 // position (pivot and update-set lists; the order becomes the identity);
 // perm[old dof] = new dof.
 void coarse_renumber(CoarseFactor& cf, std::vector<int32_t>& perm);
+// top_max > 0: the most top levels (at least one level left below) whose
+// dofs number at most top_max become a dense top (see CoarseFactor).
 int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_subs,
-                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err);
+                  const std::vector<double>& sub_xyz, CoarseFactor& cf, std::string& err, int64_t top_max = 0);
 // The same factorisation in general form (coarse_factor is the case n_keep
 // = 0, leaf 384): the dofs [0, n - n_keep) are ordered by nested dissection
 // of their groups (dof_groups: the groups holding each of them; group_xyz: 3
@@ -269,7 +287,7 @@ int coarse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
 int sparse_factor(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                   const std::vector<double>& val, const std::vector<std::vector<int32_t>>& dof_groups,
                   const std::vector<double>& group_xyz, int64_t n_keep, int leaf, CoarseFactor& cf,
-                  std::vector<double>* schur, std::string& err);
+                  std::vector<double>* schur, std::string& err, int64_t top_max = 0);
 // One factorisation of the block-diagonal matrix diag(parts): part s holds
 // dofs and positions [off[s], off[s] + parts[s].n) (a forest of elimination
 // trees whose levels are merged by height).

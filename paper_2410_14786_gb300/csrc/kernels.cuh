@@ -28,9 +28,10 @@ bool bgemv_tma_supported(int precision, int max_lda);
 // ncols = n, xoff, yoff).
 int64_t sym_packed_elems(int precision, int n);
 bool sgemv_tma_supported(int precision, int max_n);
+// xgather: the operand entry i of an item is X[xgather[xoff + i]] (else X[xoff + i]).
 cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
-                             int stage_kb, int n_stages, int max_per_sm = 0);
+                             int stage_kb, int n_stages, int max_per_sm = 0, const int32_t* xgather = nullptr);
 // stage_kb: target bytes of one shared-memory stage, in KB (1..64; 12 by default,
 // the autotuner may choose another per operator family); max_per_sm > 0 caps
 // the blocks per SM (to leave room for a concurrent kernel).

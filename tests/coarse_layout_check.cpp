@@ -43,13 +43,16 @@ namespace {
 // number of failed structural checks.
 int emulate(const CoarseFactor& cf, const GatherLayout& gl, int sh, int nw, const std::vector<double>& r,
             std::vector<double>& u, const char* what) {
-  const int n = (int)cf.n, L = cf.n_levels;
+  const int n = (int)cf.n, NF = gl.fwd_phases, NP = gl.phases;
   int bad = 0;
+  if (NP != (cf.top_levels ? 2 * (cf.n_levels - cf.top_levels) + 1 : 2 * cf.n_levels) ||
+      NF != (cf.top_levels ? cf.n_levels - cf.top_levels + 1 : cf.n_levels))
+    ++bad;
   for (int32_t ix : gl.I)
     if (ix < 0 || ix >= 2 * n) ++bad;
   const std::vector<CGUnit>& U = gl.units[sh];
   const std::vector<int32_t>& wo = gl.wo[sh];
-  if (wo.size() != (size_t)2 * L * (nw + 1) || wo.front() != 0 || wo.back() != (int)U.size()) ++bad;
+  if (wo.size() != (size_t)NP * (nw + 1) || wo.front() != 0 || wo.back() != (int)U.size()) ++bad;
   for (size_t i = 1; i < wo.size(); ++i)
     if (wo[i] < wo[i - 1]) ++bad;
   for (const CGUnit& d : U)
@@ -59,8 +62,8 @@ int emulate(const CoarseFactor& cf, const GatherLayout& gl, int sh, int nw, cons
   u.assign(n, nan);
   std::vector<int> ny(n, 0), nu(n, 0);
   int races = 0, nanreads = 0;
-  for (int ph = 0; ph < 2 * L; ++ph) {
-    const bool fwd = ph < L;
+  for (int ph = 0; ph < NP; ++ph) {
+    const bool fwd = ph < NF;
     std::vector<std::pair<int, double>> wrp, wy, wu;
     std::set<int> rd_rp, rd_y;
     for (int w = 0; w < nw; ++w)
@@ -107,8 +110,8 @@ int emulate(const CoarseFactor& cf, const GatherLayout& gl, int sh, int nw, cons
   int once = 0;
   for (int i = 0; i < n; ++i)
     if (ny[i] != 1 || nu[i] != 1) ++once;
-  printf("%s shape %d warps: n %d levels %d races %d nan-reads %d write-count %d\n", what, nw, n, L, races,
-         nanreads, once);
+  printf("%s shape %d warps: n %d phases %d (dense top of %d levels, %zu dofs) races %d nan-reads %d write-count %d\n",
+         what, nw, n, NP, cf.top_levels, cf.top_pos.size(), races, nanreads, once);
   return bad + races + nanreads + once;
 }
 
@@ -299,6 +302,27 @@ static int coarse_mode(int argc, char** argv) {
     printf("  A_c u = r residual %.2e\n", res);
     if (!(res < 1e-12)) ++bad;
     us.push_back(u);
+  }
+  {
+    // the per-level form of the same layout (one launch per phase)
+    GatherLayout one = gl;
+    one.units.assign(1, gl.seq);
+    one.wo.assign(1, std::vector<int32_t>());
+    for (size_t ph = 0; ph + 1 < gl.seq_off.size(); ++ph) {
+      one.wo[0].push_back((int32_t)gl.seq_off[ph]);
+      one.wo[0].push_back((int32_t)gl.seq_off[ph + 1]);
+    }
+    std::vector<double> u;
+    bad += emulate(cf, one, 0, 1, r, u, "coarse per-level form");
+    double en = 0, rn = 0;
+    for (int i = 0; i < n; ++i) {
+      double a = 0;
+      for (int64_t j = hs.Ac_ptr[i]; j < hs.Ac_ptr[i + 1]; ++j) a += hs.Ac_val[j] * u[perm[hs.Ac_col[j]]];
+      en += (a - r0[i]) * (a - r0[i]);
+      rn += r0[i] * r0[i];
+    }
+    printf("  A_c u = r residual %.2e\n", std::sqrt(en / rn));
+    if (!(std::sqrt(en / rn) < 1e-12)) ++bad;
   }
   for (size_t sh = 1; sh < us.size(); ++sh)
     for (int i = 0; i < n; ++i)

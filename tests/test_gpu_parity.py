@@ -139,14 +139,23 @@ def test_apply_sparse_coarse(name):
     assert _rel(uc.cpu().numpy(), want) < 1e-11
 
 
+def _coarse_level_launches(g, on):
+    t = g.get_tuning()
+    t["coarse_level_launches"] = 1 if on else 0
+    g.set_tuning(t)
+
+
+@pytest.mark.parametrize("level", [False, True])
 @pytest.mark.parametrize("name,blocks", [("cfg1_2d", 0), ("3d_24_3cubed", 0), ("3d_voronoi", 0),
                                          ("3d_corners_only", 0), ("3d_voronoi", 1)])
-def test_one_column_sparse_coarse(name, blocks):
+def test_one_column_sparse_coarse(name, blocks, level):
     """One right-hand side: the sweeps of the sparse coarse solve in their
-    gather form (one dot product per output value, warps assigned on the
-    host) give the oracle's exact u_c."""
+    gather form (one dot product per output value; one cooperative launch
+    with warps assigned on the host, or one launch per level with groups of
+    lanes sized to the rows) give the oracle's exact u_c."""
     p, mask, o = _case(name)
     g = _bddc(p, mask=mask, coarse="sparse", coarse_blocks=blocks)
+    _coarse_level_launches(g, level)
     r = synth.uniform(38, o.n_nodes)
     r[o.dir] = 0
     z = g.apply(_cuda(r)).cpu().numpy()
@@ -166,6 +175,7 @@ def test_one_column_sparse_coarse_many_levels(blocks):
     p = synth.make_problem(3, 48, 8, "lognormal", k=24)
     gs = _bddc(p, coarse="sparse", coarse_blocks=blocks)
     assert gs.info()["coarse_levels"] >= 3
+    _coarse_level_launches(gs, blocks == 3)   # the per-level launches once
     gd = _bddc(p, coarse="dense")
     gm = _bddc(p, coarse="sparse", nrhs_max=2)
     n = (p.ne + 1) ** 3
@@ -439,6 +449,11 @@ def test_full_size_config2_properties():
     _, uc_s = gs.coarse_vectors()
     assert float((uc_s - uc_d).abs().max() / uc_d.abs().max()) < 1e-11
     assert float((z_s - z_d).abs().max() / z_d.abs().max()) < 1e-11
+    _coarse_level_launches(gs, True)
+    z_l = gs.apply(r)
+    _, uc_l = gs.coarse_vectors()
+    assert float((uc_l - uc_d).abs().max() / uc_d.abs().max()) < 1e-11
+    assert float((z_l - z_d).abs().max() / z_d.abs().max()) < 1e-11
     gs.close()
     # the mixed forms reach the same solution to the solver tolerance
     for prec in ("fp32", "bf16"):
