@@ -583,7 +583,8 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
   CUDA_TRY(dev_alloc(h, &h->d_partials, (size_t)kRedBlocks * 3 * R));
   CUDA_TRY(dev_alloc(h, &h->d_counter, 1));
   CUDA_TRY(cudaMemset(h->d_counter, 0, sizeof(unsigned int)));
-  CUDA_TRY(dev_alloc(h, &h->d_stencil, (size_t)stencil_points(h->dim) * h->n_nodes));
+  CUDA_TRY(dev_alloc(h, &h->d_stencil,
+                     (size_t)stencil_points(h->dim) * (h->n_nodes + 2 * stencil_guard(h->dim, h->ne))));
   CUDA_TRY(launch_build_stencil(h, nullptr));
   CUDA_TRY(dev_alloc(h, &h->d_scal, (size_t)S_COUNT * R));
   CUDA_TRY(dev_alloc(h, &h->d_iscal, (size_t)I_COUNT * R + kGlobalFlags));

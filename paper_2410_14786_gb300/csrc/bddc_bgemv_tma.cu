@@ -629,8 +629,7 @@ template <typename T, int K>
 __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
     k_sgemv_tma(const WorkItem* __restrict__ items, int n_items, const T* __restrict__ arena,
                 const double* __restrict__ X, double* __restrict__ Y, const int32_t* __restrict__ yscatter,
-                int stage_bytes, int nst, int max_n, int32_t* __restrict__ err,
-                const int32_t* __restrict__ xgather) {
+                int stage_bytes, int nst, int max_n, int32_t* __restrict__ err) {
   constexpr int V = Op<T>::V;
   constexpr int P = SymVec<T>::P;   // float pairs per 16-byte vector
   extern __shared__ __align__(128) unsigned char smem[];
@@ -707,7 +706,7 @@ __global__ void __launch_bounds__(kTmaThreads) __maxnreg__(K <= 2 ? 72 : 96)
     const WorkItem wn = items[uu];
     for (int i = tid; i < npad; i += kCT) {
       if (i < wn.ncols)
-        cp_async8(xraw + i, X + (xgather ? (int64_t)__ldg(xgather + wn.xoff + i) : (int64_t)wn.xoff + i));
+        cp_async8(xraw + i, X + wn.xoff + i);
       else
         xraw[i] = 0.0;
     }
@@ -840,8 +839,7 @@ int64_t sym_min_stage(int max_n) {
 
 template <typename T, int K>
 cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* arena, const double* X, double* Y,
-                    const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb, int nst, int max_per_sm,
-                    const int32_t* xgather) {
+                    const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb, int nst, int max_per_sm) {
   // a stage holds at least one whole block-row (the widest), and the
   // block's shared memory stays within kSymSmemCap
   const int64_t minst = sym_min_stage<T>(max_n);
@@ -859,23 +857,22 @@ cudaError_t run_sym(const WorkItem* items, int n_items, int max_n, const T* aren
   per_sm = std::max(1, per_sm);
   if (max_per_sm > 0) per_sm = std::min(per_sm, max_per_sm);
   const int grid = std::max(1, std::min(n_items, num_sms() * per_sm));
-  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, nst, max_n, err,
-                                        xgather);
+  kern<<<grid, kTmaThreads, smem, st>>>(items, n_items, arena, X, Y, yscatter, stage_bytes, nst, max_n, err);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t dispatch_sym(const WorkItem* items, int n_items, int max_n, const void* arena, const double* X,
                          double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st, int stage_kb,
-                         int nst, int max_per_sm, const int32_t* xgather) {
+                         int nst, int max_per_sm) {
   constexpr int V = Op<T>::V;
   const T* A = static_cast<const T*>(arena);
   if (max_n <= 32 * V)
-    return run_sym<T, 1>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm, xgather);
+    return run_sym<T, 1>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   if (max_n <= 64 * V)
-    return run_sym<T, 2>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm, xgather);
+    return run_sym<T, 2>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   if (max_n <= kSymK * 32 * V)
-    return run_sym<T, kSymK>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm, xgather);
+    return run_sym<T, kSymK>(items, n_items, max_n, A, X, Y, yscatter, err, st, stage_kb, nst, max_per_sm);
   return cudaErrorInvalidValue;
 }
 
@@ -907,16 +904,16 @@ bool sgemv_tma_supported(int precision, int max_n) {
 
 cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
-                             int stage_kb, int n_stages, int max_per_sm, const int32_t* xgather) {
+                             int stage_kb, int n_stages, int max_per_sm) {
   if (n_items == 0) return cudaSuccess;
   if (stage_kb < 1 || stage_kb > 48 || n_stages < kSymMinStages || n_stages > kSymMaxStages)
     return cudaErrorInvalidValue;
   if (precision == BDDC_PREC_FP32)
     return dispatch_sym<float>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, n_stages,
-                               max_per_sm, xgather);
+                               max_per_sm);
   if (precision == BDDC_PREC_BF16)
     return dispatch_sym<__nv_bfloat16>(items, n_items, max_n, arena, X, Y, yscatter, err, st, stage_kb, n_stages,
-                                       max_per_sm, xgather);
+                                       max_per_sm);
   return cudaErrorInvalidValue;
 }
 

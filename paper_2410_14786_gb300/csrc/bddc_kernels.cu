@@ -528,18 +528,15 @@ cudaError_t interior_sweeps(bddc_handle_s* h, const ApplyWork& W, const double* 
 // One batched application of the interior (A_II^-1) or interface (K_GG)
 // operators of all subdomains.
 // Y = Op X over the interior or interface operators; counts its launches.
-// xgather (symmetric GEMV only): the operand is read through it (see
-// launch_sgemv_tma).
 cudaError_t local_op(bddc_handle_s* h, bool interior, const double* X, double* Y, const int32_t* yscatter, int nrhs,
-                     cudaStream_t st, int max_per_sm = 0, const int32_t* xgather = nullptr) {
+                     cudaStream_t st, int max_per_sm = 0) {
   if (interior && h->sparse_local) return interior_sweeps(h, h->w, X, Y, yscatter, nrhs, st);
   if (h->use_tc) return launch_tc_gemm(h, interior, X, Y, yscatter, nrhs, st);
   if (h->use_sym) {
     if (nrhs != 1) return cudaErrorInvalidValue;   // nrhs_max is 1 on this path
     h->launches += (interior ? h->n_wsy_I : h->n_wsy_G) > 0;
     return interior ? launch_sgemv_tma(h->precision, h->d_wsy_I, h->n_wsy_I, h->max_n_I, h->d_aii, X, Y, yscatter,
-                                       h->d_err, st, h->tune_stage_kb[0], h->tune_sym_stages[0], max_per_sm,
-                                       xgather)
+                                       h->d_err, st, h->tune_stage_kb[0], h->tune_sym_stages[0], max_per_sm)
                     : launch_sgemv_tma(h->precision, h->d_wsy_G, h->n_wsy_G, h->max_n_G, h->d_kgg, X, Y, yscatter,
                                        h->d_err, st, h->tune_stage_kb[1], h->tune_sym_stages[1], max_per_sm);
   }
@@ -608,20 +605,16 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
     if (ev) cudaEventRecord(ev[i], st);
   };
   mark(0);
-  // t_I = A_II^-1 r_I: the symmetric GEMV gathers r_I from r itself; the
-  // other engines read the compact r_I of the restriction
-  const bool gather_rI = h->use_sym && !h->sparse_local && nrhs == 1;
-  if (!gather_rI && h->nI_tot) {
+  // restriction: the compact r_I (W r_G is formed by the interface
+  // right-hand side, the Dirichlet rows of z by the prolongation)
+  if (h->nI_tot) {
     (nrhs == 1 ? k_restrict<true> : k_restrict<false>)<<<blocks_for(h->nI_tot * nrhs), kThreads, 0, st>>>(
         r, nrhs, h->d_inode, h->nI_tot, nullptr, nullptr, 0, W.rI, nullptr, nullptr, 0, nullptr);
     h->launches++;
   }
   mark(1);
-  if (gather_rI) {
-    if ((e = local_op(h, true, r, W.tI, nullptr, nrhs, st, 0, h->d_inode)) != cudaSuccess) return e;
-  } else {
-    if ((e = local_op(h, true, W.rI, W.tI, nullptr, nrhs, st)) != cudaSuccess) return e;
-  }
+  // t_I = A_II^-1 r_I
+  if ((e = local_op(h, true, W.rI, W.tI, nullptr, nrhs, st)) != cudaSuccess) return e;
   mark(2);
   if (h->nG_tot) {
     // y'_G = W r_G - A_GI t_I; z_G = K_GG y'_G

@@ -16,45 +16,55 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Stencil offsets with a nonzero coupling. 3D Q1: the centre, the 12 edge
-// diagonals (two coordinates differ) and the 8 cube diagonals; the 6 face
-// neighbours couple with weight 0 for every sigma (the Q1 element matrix has
-// a zero entry between nodes at Hamming distance 1). 2D: all 9 points.
-__constant__ int8_t c_off3[21][3] = {
-    {0, 0, 0},
-    {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0},
-    {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {1, 0, 1},
-    {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},
-    {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1},
+// Stencil offsets with a nonzero coupling, of which only the centre and the
+// forward half are stored (A is symmetric: the coupling of node n to n - o is
+// the forward coefficient of node n - o for offset o). 3D Q1: the centre, the
+// 12 edge diagonals (two coordinates differ) and the 8 cube diagonals; the 6
+// face neighbours couple with weight 0 for every sigma (the Q1 element
+// matrix has a zero entry between nodes at Hamming distance 1). 2D: all 9
+// points. Forward: a positive offset in node numbering (x fastest).
+__constant__ int8_t c_fwd3[10][3] = {
+    {-1, 1, 0}, {1, 1, 0}, {-1, 0, 1}, {1, 0, 1}, {0, -1, 1}, {0, 1, 1},
     {-1, -1, 1}, {1, -1, 1}, {-1, 1, 1}, {1, 1, 1}};
-__constant__ int8_t c_off2[9][2] = {{0, 0}, {-1, 0}, {1, 0}, {0, -1}, {0, 1}, {-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
+__constant__ int8_t c_fwd2[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
 
 template <int DIM> struct Stencil;
-template <> struct Stencil<3> { static constexpr int NS = 21; };
-template <> struct Stencil<2> { static constexpr int NS = 9; };
+template <> struct Stencil<3> { static constexpr int NH = 11; };   // centre + 10 forward offsets
+template <> struct Stencil<2> { static constexpr int NH = 5; };
 
 __device__ __forceinline__ bool on_boundary(int i, int ne) { return i == 0 || i == ne; }
 
-// coef[s * n_nodes + n] = A[n, n + offset_s]; zero on Dirichlet rows and for
-// Dirichlet neighbours. A[n, m] = sum over the elements holding both nodes of
-// sigma_e times the element-matrix entry for their Hamming distance.
+template <int DIM>
+__device__ __forceinline__ void fwd_offset(int s, int& dx, int& dy, int& dz) {
+  dx = DIM == 3 ? c_fwd3[s][0] : c_fwd2[s][0];
+  dy = DIM == 3 ? c_fwd3[s][1] : c_fwd2[s][1];
+  dz = DIM == 3 ? c_fwd3[s][2] : 0;
+}
+
+// coef[s * ld + guard + n] = A[n, n + offset_s] for the centre (s = 0) and
+// the forward offsets; zero on Dirichlet rows and for Dirichlet neighbours,
+// and in the guard zones of `guard` entries before and after every array.
+// A[n, m] = sum over the elements holding both nodes of sigma_e times the
+// element-matrix entry for their Hamming distance.
 template <int DIM>
 __global__ void k_build_stencil(int ne, const double* __restrict__ sigma, double k0, double k1, double k2, double k3,
-                                double* __restrict__ coef) {
-  constexpr int NS = Stencil<DIM>::NS;
+                                int64_t guard, double* __restrict__ coef) {
+  constexpr int NH = Stencil<DIM>::NH;
   const int64_t n1 = ne + 1;
   const int64_t n_nodes = DIM == 2 ? n1 * n1 : n1 * n1 * n1;
+  const int64_t ld = n_nodes + 2 * guard;
   const double kd[4] = {k0, k1, k2, k3};
-  for (int64_t nd = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nd < n_nodes;
-       nd += (int64_t)gridDim.x * blockDim.x) {
-    const int ix = (int)(nd % n1), iy = (int)((nd / n1) % n1), iz = DIM == 3 ? (int)(nd / (n1 * n1)) : 0;
-    const bool dir = on_boundary(ix, ne) || on_boundary(iy, ne) || (DIM == 3 && on_boundary(iz, ne));
-    for (int s = 0; s < NS; ++s) {
-      const int dx = DIM == 3 ? c_off3[s][0] : c_off2[s][0];
-      const int dy = DIM == 3 ? c_off3[s][1] : c_off2[s][1];
-      const int dz = DIM == 3 ? c_off3[s][2] : 0;
-      double c = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NH * ld;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / ld);
+    const int64_t nd = i - s * ld - guard;
+    double c = 0.0;
+    if (nd >= 0 && nd < n_nodes) {
+      const int ix = (int)(nd % n1), iy = (int)((nd / n1) % n1), iz = DIM == 3 ? (int)(nd / (n1 * n1)) : 0;
+      int dx = 0, dy = 0, dz = 0;
+      if (s > 0) fwd_offset<DIM>(s - 1, dx, dy, dz);
       const int mx = ix + dx, my = iy + dy, mz = iz + dz;
+      const bool dir = on_boundary(ix, ne) || on_boundary(iy, ne) || (DIM == 3 && on_boundary(iz, ne));
       const bool mdir = on_boundary(mx, ne) || on_boundary(my, ne) || (DIM == 3 && on_boundary(mz, ne));
       if (!dir && !mdir) {
         // elements with corner (ex, ey, ez) containing both nodes
@@ -67,8 +77,8 @@ __global__ void k_build_stencil(int ne, const double* __restrict__ sigma, double
               c += sigma[e] * kd[__popc(a ^ b)];
             }
       }
-      coef[(int64_t)s * n_nodes + nd] = c;
     }
+    coef[i] = c;
   }
 }
 
@@ -210,32 +220,38 @@ __device__ void reduce_and_finalize(double s[3], int nrhs, int op, const PcgStat
   }
 }
 
-// y = A x with the precomputed stencil; with op >= 0 also x.y per column and
-// finalize_op(op). Thread t: column t % nrhs, nodes strided over the grid.
+// y = A x with the precomputed half stencil; with op >= 0 also x.y per
+// column and finalize_op(op). Thread t: column t % nrhs, nodes strided over
+// the grid. Row n: the centre, A[n, n + o] = coef_o[n] and A[n, n - o] =
+// coef_o[n - o] for every forward offset o; a neighbour index outside the
+// vector is clamped into it and meets a zero coefficient (the guard zones,
+// or the zero couplings of the boundary nodes there), so every row takes
+// the same loads, none behind a branch.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t n_nodes, int ne, int nrhs,
+__global__ void __launch_bounds__(kThreads, 4) k_spmv(int64_t n_nodes, int ne, int nrhs, int64_t guard,
                                                    const double* __restrict__ coef, const double* __restrict__ x,
                                                    double* __restrict__ y, int op, PcgState S) {
-  constexpr int NS = Stencil<DIM>::NS;
+  constexpr int NH = Stencil<DIM>::NH;
   const int64_t n1 = ne + 1;
+  const int64_t ld = n_nodes + 2 * guard;
+  const double* c0 = coef + guard;
   const int per = kThreads / nrhs;
   const int sub = threadIdx.x / nrhs, k = threadIdx.x - sub * nrhs;
   double s[3] = {0, 0, 0};
   if (threadIdx.x < per * nrhs) {
     for (int64_t nd = blockIdx.x * (int64_t)per + sub; nd < n_nodes; nd += (int64_t)gridDim.x * per) {
-      // Dirichlet rows have an all-zero stencil, so every row is computed the
-      // same way: neighbour indices clamped into the vector keep the loads of
-      // boundary rows in bounds (their coefficients are 0), and no load waits
-      // on a branch. Three partial sums shorten the float64 FMA chain.
-      double part[3] = {0.0, 0.0, 0.0};
+      double part[4] = {__ldg(&c0[nd]) * __ldg(&x[nd * nrhs + k]), 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        const int64_t off = DIM == 3 ? c_off3[q][0] + n1 * (c_off3[q][1] + n1 * c_off3[q][2])
-                                     : c_off2[q][0] + n1 * c_off2[q][1];
-        const int64_t nb = min(max(nd + off, (int64_t)0), n_nodes - 1);
-        part[q % 3] = fma(__ldg(&coef[(int64_t)q * n_nodes + nd]), __ldg(&x[nb * nrhs + k]), part[q % 3]);
+      for (int q = 1; q < NH; ++q) {
+        int dx, dy, dz;
+        fwd_offset<DIM>(q - 1, dx, dy, dz);
+        const int64_t off = dx + n1 * (dy + n1 * dz);
+        const int64_t up = min(nd + off, n_nodes - 1), dn = max(nd - off, (int64_t)0);
+        const double* cq = c0 + (int64_t)q * ld;
+        part[q & 3] = fma(__ldg(&cq[nd]), __ldg(&x[up * nrhs + k]), part[q & 3]);
+        part[(q + 2) & 3] = fma(__ldg(&cq[nd - off]), __ldg(&x[dn * nrhs + k]), part[(q + 2) & 3]);
       }
-      const double acc = (part[0] + part[1]) + part[2];
+      const double acc = (part[0] + part[1]) + (part[2] + part[3]);
       y[nd * nrhs + k] = acc;
       s[0] = fma(x[nd * nrhs + k], acc, s[0]);
     }
@@ -293,26 +309,34 @@ void stencil_coefs(int dim, double h, double c[4]) {
 
 }  // namespace
 
-int stencil_points(int dim) { return dim == 3 ? Stencil<3>::NS : Stencil<2>::NS; }
+int stencil_points(int dim) { return dim == 3 ? Stencil<3>::NH : Stencil<2>::NH; }
+
+int64_t stencil_guard(int dim, int ne) {
+  const int64_t n1 = ne + 1;
+  return dim == 3 ? n1 * n1 + n1 + 1 : n1 + 1;   // the largest forward offset
+}
 
 cudaError_t launch_build_stencil(bddc_handle_s* h, cudaStream_t st) {
   double c[4];
   stencil_coefs(h->dim, h->h, c);
-  const int blocks = (int)std::min<int64_t>((h->n_nodes + kThreads - 1) / kThreads, 1 << 20);
+  const int64_t guard = stencil_guard(h->dim, h->ne);
+  const int64_t total = (int64_t)stencil_points(h->dim) * (h->n_nodes + 2 * guard);
+  const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 1 << 20);
   if (h->dim == 3)
-    k_build_stencil<3><<<blocks, kThreads, 0, st>>>(h->ne, h->d_sigma, c[0], c[1], c[2], c[3], h->d_stencil);
+    k_build_stencil<3><<<blocks, kThreads, 0, st>>>(h->ne, h->d_sigma, c[0], c[1], c[2], c[3], guard, h->d_stencil);
   else
-    k_build_stencil<2><<<blocks, kThreads, 0, st>>>(h->ne, h->d_sigma, c[0], c[1], c[2], c[3], h->d_stencil);
+    k_build_stencil<2><<<blocks, kThreads, 0, st>>>(h->ne, h->d_sigma, c[0], c[1], c[2], c[3], guard, h->d_stencil);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(bddc_handle_s* h, const double* x, double* y, int nrhs, int op, double rtol, int flexible,
                         cudaStream_t st) {
   const PcgState S = state(h, rtol, flexible);
+  const int64_t guard = stencil_guard(h->dim, h->ne);
   if (h->dim == 3)
-    k_spmv<3><<<h->n_red_blocks, kThreads, 0, st>>>(h->n_nodes, h->ne, nrhs, h->d_stencil, x, y, op, S);
+    k_spmv<3><<<h->n_red_blocks, kThreads, 0, st>>>(h->n_nodes, h->ne, nrhs, guard, h->d_stencil, x, y, op, S);
   else
-    k_spmv<2><<<h->n_red_blocks, kThreads, 0, st>>>(h->n_nodes, h->ne, nrhs, h->d_stencil, x, y, op, S);
+    k_spmv<2><<<h->n_red_blocks, kThreads, 0, st>>>(h->n_nodes, h->ne, nrhs, guard, h->d_stencil, x, y, op, S);
   h->launches++;
   return cudaGetLastError();
 }

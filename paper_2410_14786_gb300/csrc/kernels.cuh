@@ -28,10 +28,9 @@ bool bgemv_tma_supported(int precision, int max_lda);
 // ncols = n, xoff, yoff).
 int64_t sym_packed_elems(int precision, int n);
 bool sgemv_tma_supported(int precision, int max_n);
-// xgather: the operand entry i of an item is X[xgather[xoff + i]] (else X[xoff + i]).
 cudaError_t launch_sgemv_tma(int precision, const WorkItem* items, int n_items, int max_n, const void* arena,
                              const double* X, double* Y, const int32_t* yscatter, int32_t* err, cudaStream_t st,
-                             int stage_kb, int n_stages, int max_per_sm = 0, const int32_t* xgather = nullptr);
+                             int stage_kb, int n_stages, int max_per_sm = 0);
 // stage_kb: target bytes of one shared-memory stage, in KB (1..64; 12 by default,
 // the autotuner may choose another per operator family); max_per_sm > 0 caps
 // the blocks per SM (to leave room for a concurrent kernel).
@@ -124,10 +123,13 @@ cudaError_t launch_elem_grad(bddc_handle_s* h, const double* u, const double* la
 // PCG scalar updates applied by the last block of a reducing kernel.
 enum FinalizeOp { FIN_INIT = 0, FIN_RHO = 1, FIN_ALPHA = 2, FIN_CONV = 3, FIN_BETA = 4 };
 
-// Global SpMV (bddc_pcg.cu): coefficients of the assembled Q1 stencil,
-// built once per handle; y = A x, and with op >= 0 also x.y per column
-// followed by the PCG scalar update `op`.
+// Global SpMV (bddc_pcg.cu): coefficients of the assembled Q1 stencil
+// (the centre and the forward half of the symmetric couplings, each array
+// with zero guard zones of stencil_guard entries on both sides), built once
+// per handle; y = A x, and with op >= 0 also x.y per column followed by the
+// PCG scalar update `op`.
 int stencil_points(int dim);
+int64_t stencil_guard(int dim, int ne);
 cudaError_t launch_build_stencil(bddc_handle_s* h, cudaStream_t st);
 cudaError_t launch_spmv(bddc_handle_s* h, const double* x, double* y, int nrhs, int op, double rtol, int flexible,
                         cudaStream_t st);

@@ -36,6 +36,21 @@ def test_exports_every_declared_symbol(L):
     assert sorted(_lib.EXPORTED) == names
 
 
+def test_no_unresolved_library_symbols(L):
+    """Every function of the library's own namespace that one translation
+    unit calls is defined in another (a shared library links with unresolved
+    symbols and would fail only when loaded)."""
+    import shutil
+    import subprocess
+    from paper_2410_14786_gb300 import _lib
+    if not shutil.which("nm"):
+        pytest.skip("nm not available")
+    out = subprocess.run(["nm", "-D", "--undefined-only", _lib.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    ours = [ln for ln in out.splitlines() if "_ZN4bddc" in ln or " bddc_" in ln]
+    assert ours == [], ours
+
+
 def _structs(p, precision=0, constraints=0, nrhs_max=1, local_solver=0, local_leaf=0):
     from paper_2410_14786_gb300 import _lib
     sig = np.ascontiguousarray(p.elem_sigma, dtype=np.float64)
