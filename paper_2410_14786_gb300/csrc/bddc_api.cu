@@ -503,7 +503,10 @@ int build_device(bddc_handle_s* h, HostSetup& hs, const bddc_problem_t* P) {
     merge_forest(hs.ifac, ioff, forest);
     std::vector<CoarseFactor>().swap(hs.ifac);
     ifac_entries = forest.nnz;
-    CUDA_TRY(build_sweeps(h, forest, h->is, h->nrhs_max > 1, 0, kSweepBlock));
+    // the mixed forms sweep in float32 (an inexact interior solve inside
+    // flexible PCG, as the low-precision dense operators are); FP64 in float64
+    const bool c32 = h->precision != BDDC_PREC_FP64;
+    CUDA_TRY(build_sweeps(h, forest, h->is, h->nrhs_max > 1, 0, c32 ? kSweepLevel : kSweepBlock, c32));
     // one interior solve at one column reads its coefficients once
     opbytes_I = sweep_read_1col(h->is);
     arena_bytes += (size_t)(h->is.g_entries * 12 + ((h->is.multi || h->is.block_form) ? h->is.nnz * 8 : 0));

@@ -577,9 +577,16 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
 // within the group, and its first lane stores the result. Values of other
 // phases are read with plain loads (written by earlier launches);
 // coefficients and indices through the read-only path.
+// TC: the coefficients' type. double: float64 products and sums; float
+// (the mixed forms of the sparse local solver): float32 coefficients,
+// products and sums (operands rounded to float32; results stored in the
+// float64 vectors), which moves the products from the float64 pipe (a few
+// per SM and cycle on this GPU) to the float32 pipe and reads 8 bytes per
+// coefficient instead of 12.
+template <typename TC>
 struct LevelArgs {
   const CGUnit* units;       // the phase's descriptors
-  const double* C;
+  const TC* C;
   const int32_t* I;
   const double* xa;          // operand vector for indices < n (forward: r', backward: y)
   const double* xb;          // operand vector for indices n + i (forward: r, backward: u by position)
@@ -590,59 +597,60 @@ struct LevelArgs {
   int32_t cb[kLevelClasses + 1], bb[kLevelClasses + 1];
 };
 
-template <int G, int c>
-__device__ __forceinline__ void level_group(const LevelArgs& a, int b) {
+template <typename TC, int G, int c>
+__device__ __forceinline__ void level_group(const LevelArgs<TC>& a, int b) {
   const int grp = (int)threadIdx.x / G, gl = (int)threadIdx.x % G;
   const int k = a.cb[c] + (b - a.bb[c]) * (kLevelThreads / G) + grp;
   const bool valid = k < a.cb[c + 1];
   CGUnit d{0, 0, 0, -1, 0};
   if (valid) d = a.units[k];
-  const double* C = a.C + d.off;
+  const TC* C = a.C + d.off;
   const int32_t* I = a.I + d.off;
   auto X = [&](int ix) { return ix < a.n ? a.xa[ix] : a.xb[ix - a.n]; };
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  TC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   for (int j = gl; j < d.len; j += 4 * G) {
     const bool b1 = j + G < d.len, b2 = j + 2 * G < d.len, b3 = j + 3 * G < d.len;
-    const double c0 = __ldg(C + j);
-    const double c1 = b1 ? __ldg(C + j + G) : 0.0;
-    const double c2 = b2 ? __ldg(C + j + 2 * G) : 0.0;
-    const double c3 = b3 ? __ldg(C + j + 3 * G) : 0.0;
+    const TC c0 = __ldg(C + j);
+    const TC c1 = b1 ? __ldg(C + j + G) : TC(0);
+    const TC c2 = b2 ? __ldg(C + j + 2 * G) : TC(0);
+    const TC c3 = b3 ? __ldg(C + j + 3 * G) : TC(0);
     const int i0 = __ldg(I + j);
     const int i1 = b1 ? __ldg(I + j + G) : i0;
     const int i2 = b2 ? __ldg(I + j + 2 * G) : i0;
     const int i3 = b3 ? __ldg(I + j + 3 * G) : i0;
-    const double x0 = X(i0), x1 = X(i1), x2 = X(i2), x3 = X(i3);
+    const TC x0 = (TC)X(i0), x1 = (TC)X(i1), x2 = (TC)X(i2), x3 = (TC)X(i3);
     s0 = fma(c0, x0, s0);
     s1 = fma(c1, x1, s1);
     s2 = fma(c2, x2, s2);
     s3 = fma(c3, x3, s3);
   }
-  double s = (s0 + s1) + (s2 + s3);
+  TC s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (!valid || gl != 0) return;
   if (!a.fwd) {
-    a.rp[d.dst] = s;
-    a.u[d.aux] = s;
+    a.rp[d.dst] = (double)s;
+    a.u[d.aux] = (double)s;
   } else if (d.aux < 0) {
-    a.y[d.dst] = s;
+    a.y[d.dst] = (double)s;
   } else {
-    a.rp[d.dst] = X(d.aux) - s;
+    a.rp[d.dst] = X(d.aux) - (double)s;
   }
 }
 
-__global__ void __launch_bounds__(kLevelThreads) k_level_sweep(LevelArgs a) {
+template <typename TC>
+__global__ void __launch_bounds__(kLevelThreads) k_level_sweep(LevelArgs<TC> a) {
   const int b = blockIdx.x;
   int c = 0;   // the block's class (the block ranges ascend with the class)
 #pragma unroll
   for (int q = 1; q < kLevelClasses; ++q) c += b >= a.bb[q];
   switch (c) {
-    case 0: level_group<32, 0>(a, b); break;
-    case 1: level_group<16, 1>(a, b); break;
-    case 2: level_group<8, 2>(a, b); break;
-    case 3: level_group<4, 3>(a, b); break;
-    case 4: level_group<2, 4>(a, b); break;
-    default: level_group<1, 5>(a, b); break;
+    case 0: level_group<TC, 32, 0>(a, b); break;
+    case 1: level_group<TC, 16, 1>(a, b); break;
+    case 2: level_group<TC, 8, 2>(a, b); break;
+    case 3: level_group<TC, 4, 3>(a, b); break;
+    case 4: level_group<TC, 2, 4>(a, b); break;
+    default: level_group<TC, 1, 5>(a, b); break;
   }
 }
 
@@ -978,7 +986,8 @@ cudaError_t up(bddc_handle_s* h, T** dst, const std::vector<T>& v) {
 
 namespace {
 
-cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, int blocks, bool level_form) {
+cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, int blocks, bool level_form,
+                         bool coef32) {
   GatherLayout g;
   const int nb[2] = {blocks, blocks}, wpb[2] = {kGThreadsWide / 32, kGThreadsNarrow / 32};
   gather_layout(cf, level_form ? 0 : 2, nb, wpb, g);
@@ -995,8 +1004,15 @@ cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
       S.gbytes_h[ph < L ? ph : 2 * L - 1 - ph] += 12 * len;
     }
   cudaError_t e;
-  if ((e = up(h, &S.gC, g.C)) != cudaSuccess) return e;
-  std::vector<double>().swap(g.C);
+  if (coef32) {
+    // the per-level form only (the cooperative kernel reads float64)
+    std::vector<float> c32(g.C.begin(), g.C.end());
+    std::vector<double>().swap(g.C);
+    if ((e = up(h, &S.gC32, c32)) != cudaSuccess) return e;
+  } else {
+    if ((e = up(h, &S.gC, g.C)) != cudaSuccess) return e;
+    std::vector<double>().swap(g.C);
+  }
   if ((e = up(h, &S.gI, g.I)) != cudaSuccess) return e;
   std::vector<int32_t>().swap(g.I);
   // the per-level form always (for the cooperative form it is the
@@ -1029,7 +1045,8 @@ cudaError_t build_coarse_cg_device(bddc_handle_s* h) {
 }
 
 cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req,
-                         int form) {
+                         int form, bool coef32) {
+  if (coef32 && form == kSweepCoop) return cudaErrorInvalidValue;
   const int L = cf.n_levels;
   S.levels = L;
   S.n = cf.n;
@@ -1079,7 +1096,7 @@ cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
   // one-column form: the block form where every front fits in shared
   // memory, else the per-level gather form
   BlockLayout bl;
-  bool block = form == kSweepBlock;
+  bool block = form == kSweepBlock && !coef32;
   if (block) {
     block_layout(cf, kBlockTarget, bl);
     block = bl.max_front <= kBlockMaxFront;
@@ -1088,10 +1105,10 @@ cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
   }
   // the gather form (the block form keeps its per-level launches for the
   // low levels, whose nodes are too small for a block of their own)
-  if ((e = build_gather(h, cf, S, blocks_req > 0 ? std::min(blocks_req, sms) : sms, form != kSweepCoop)) !=
+  if ((e = build_gather(h, cf, S, blocks_req > 0 ? std::min(blocks_req, sms) : sms, form != kSweepCoop, coef32)) !=
       cudaSuccess)
     return e;
-  S.read_1col = S.g_entries * 12;
+  S.read_1col = S.g_entries * (coef32 ? 8 : 12);
   if (block) {
     S.block_form = true;
     S.bitem_off = bl.item_off;
@@ -1235,7 +1252,7 @@ cudaError_t build_coarse_device(bddc_handle_s* h, const CoarseFactor& cf) {
   cudaDeviceGetAttribute(&h->c_sms, cudaDevAttrMultiProcessorCount, dev);
   if (h->d_cbar == nullptr && (e = up(h, &h->d_cbar, std::vector<unsigned int>(2, 0u))) != cudaSuccess) return e;
   h->cs.bar = h->d_cbar;
-  if ((e = build_sweeps(h, cf, h->cs, true, h->g_blocks, kSweepCoop)) != cudaSuccess) return e;
+  if ((e = build_sweeps(h, cf, h->cs, true, h->g_blocks, kSweepCoop, false)) != cudaSuccess) return e;
   h->c_nnz = h->cs.nnz;
   return cudaSuccess;
 }
@@ -1284,10 +1301,11 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
       const SweepSet::LevelPhase& P = S.lv[ph];
       const int nblk = P.bb[kLevelClasses];
       if (nblk == 0) return;
-      LevelArgs la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : u, rp, y, u, (int)S.n, fwd ? 1 : 0, {}, {}};
+      LevelArgs<double> la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : u, rp, y, u, (int)S.n, fwd ? 1 : 0,
+                           {}, {}};
       std::memcpy(la.cb, P.cb, sizeof(la.cb));
       std::memcpy(la.bb, P.bb, sizeof(la.bb));
-      k_level_sweep<<<nblk, kLevelThreads, 0, st>>>(la);
+      k_level_sweep<double><<<nblk, kLevelThreads, 0, st>>>(la);
       h->launches++;
     };
     if (kmin > 0 &&
@@ -1319,10 +1337,19 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
       const int nblk = P.bb[kLevelClasses];
       if (nblk == 0) continue;
       const bool fwd = (int)ph < S.g_fwd;
-      LevelArgs la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n, fwd ? 1 : 0, {}, {}};
-      std::memcpy(la.cb, P.cb, sizeof(la.cb));
-      std::memcpy(la.bb, P.bb, sizeof(la.bb));
-      k_level_sweep<<<nblk, kLevelThreads, 0, st>>>(la);
+      if (S.gC32) {
+        LevelArgs<float> la{S.seq + P.u0, S.gC32, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n,
+                            fwd ? 1 : 0, {}, {}};
+        std::memcpy(la.cb, P.cb, sizeof(la.cb));
+        std::memcpy(la.bb, P.bb, sizeof(la.bb));
+        k_level_sweep<float><<<nblk, kLevelThreads, 0, st>>>(la);
+      } else {
+        LevelArgs<double> la{S.seq + P.u0, S.gC, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n,
+                             fwd ? 1 : 0, {}, {}};
+        std::memcpy(la.cb, P.cb, sizeof(la.cb));
+        std::memcpy(la.bb, P.bb, sizeof(la.bb));
+        k_level_sweep<double><<<nblk, kLevelThreads, 0, st>>>(la);
+      }
       h->launches++;
     }
     return cudaGetLastError();

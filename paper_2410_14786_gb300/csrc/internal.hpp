@@ -107,6 +107,7 @@ struct SweepSet {
   int32_t* lvl = nullptr;       // unit offsets: [L+1 forward][L+1 backward], then n
   int32_t* lvl4 = nullptr;
   double* gC = nullptr;
+  float* gC32 = nullptr;        // the gather form's coefficients in float32 (per-level form only), else null
   int32_t* gI = nullptr;
   CGUnit* gU[2] = {nullptr, nullptr};
   int32_t* gwo[2] = {nullptr, nullptr};   // [phases][warps + 1]

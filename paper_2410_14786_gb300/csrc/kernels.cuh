@@ -84,9 +84,10 @@ cudaError_t launch_scatter_rows(int64_t n, int nrhs, const int32_t* perm, const 
 // factors), kSweepLevel (gather form, one launch per phase, sub-warp groups
 // sized to the rows) or kSweepBlock (supernode by supernode with the dense
 // node matrices streamed, one launch per phase; the level form where a front
-// does not fit in shared memory).
+// does not fit in shared memory). coef32: the one-column form's coefficients
+// in float32 (products and sums in float32; the per-level form only).
 cudaError_t build_sweeps(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, bool multi, int blocks_req,
-                         int form);
+                         int form, bool coef32);
 // u = A^-1 r by the forward and backward sweeps of S, level by level, in one
 // cooperative launch (r and u: S.n x nrhs in dof order; rp and y: work
 // vectors of the same size). inject: the barriers take the handle's test
