@@ -171,32 +171,43 @@ def oracle_measure(budget_s: float, max_solves: int, warm_applies: int = 0) -> d
     return {"setup_s": setup_s, "solve_s": times, "iters": iters, "cores": cores, "blas_threads": _blas_threads()}
 
 
-def start_oracle_worker(reserve: int = 2):
-    """The oracle baseline in a fresh interpreter (exec, not fork), on the host
-    cores other than the first `reserve` ones, which the GPU process keeps."""
+ORACLE_CORES = 4   # the oracle's host cores and BLAS threads: its dense LAPACK calls are small
+                   # (one subdomain's saddle-point system each), and more threads only slow them
+
+
+def start_oracle_worker(budget_s: float = 0.0, max_solves: int = 1, warm_applies: int = 0):
+    """The oracle in a fresh interpreter (exec, not fork) on the last
+    ORACLE_CORES host cores with as many BLAS threads; the GPU process keeps
+    the others for its own host setup."""
     n = os.cpu_count() or 1
     env = dict(os.environ)
-    cores = list(range(reserve, n)) if n > reserve + 1 else list(range(n))
+    cores = list(range(max(0, n - ORACLE_CORES), n))
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(len(cores))
     env["BDDC_ORACLE_CORES"] = ",".join(map(str, cores))
+    env["BDDC_ORACLE_RUN"] = f"{budget_s},{max_solves},{warm_applies}"
     return subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker"], env=env,
                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
 
 
-def collect_oracle_worker(proc, timeout_s: float) -> dict:
+def read_oracle_worker(proc, timeout_s: float):
+    """(result dict, None) or (None, reason)."""
     try:
         out, err = proc.communicate(timeout=timeout_s)
     except subprocess.TimeoutExpired:
         proc.kill()
         proc.communicate()
-        return {"value": None, "unit": "solves/s", "kind": "oracle",
-                "sample": f"not measured: the oracle did not finish within {timeout_s:.0f} s"}
+        return None, f"the oracle did not finish within {timeout_s:.0f} s"
     lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     if proc.returncode != 0 or not lines:
-        return {"value": None, "unit": "solves/s", "kind": "oracle",
-                "sample": "not measured: oracle worker failed: " + (err.strip().splitlines() or ["?"])[-1][:200]}
-    r = json.loads(lines[-1])
+        return None, "oracle worker failed: " + (err.strip().splitlines() or ["?"])[-1][:200]
+    return json.loads(lines[-1]), None
+
+
+def collect_oracle_worker(proc, timeout_s: float) -> dict:
+    r, why = read_oracle_worker(proc, timeout_s)
+    if r is None:
+        return {"value": None, "unit": "solves/s", "kind": "oracle", "sample": "not measured: " + why}
     per = float(np.mean(r["solve_s"]))
     return {"value": 1.0 / per, "unit": "solves/s", "cores": r["cores"], "kind": "oracle",
             "blas_threads": r["blas_threads"], "setup_s": r["setup_s"], "solve_s": per, "iters": r["iters"],
@@ -208,7 +219,8 @@ def oracle_worker_main() -> int:
     cores = os.environ.get("BDDC_ORACLE_CORES")
     if cores and hasattr(os, "sched_setaffinity"):
         os.sched_setaffinity(0, {int(c) for c in cores.split(",")})
-    print(json.dumps(oracle_measure(budget_s=0.0, max_solves=1)))
+    budget, max_solves, warm = os.environ.get("BDDC_ORACLE_RUN", "0,1,0").split(",")
+    print(json.dumps(oracle_measure(budget_s=float(budget), max_solves=int(max_solves), warm_applies=int(warm))))
     return 0
 
 
@@ -216,7 +228,10 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    r = oracle_measure(budget_s=REF_BUDGET_S, max_solves=max(1, args.steps), warm_applies=1)
+    r, why = read_oracle_worker(start_oracle_worker(REF_BUDGET_S, max(1, args.steps), 1), timeout_s=3000.0)
+    if r is None:
+        print(json.dumps({"impl": "reference", "unavailable": why}))
+        return 0
     per = float(np.mean(r["solve_s"]))
     value = 1.0 / per
     n = len(r["solve_s"])
@@ -247,7 +262,7 @@ def run_gb300(args):
     # while the GPU forms are timed (started before any CUDA call)
     oracle_proc = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.config == 2:
-        oracle_proc = start_oracle_worker(reserve=2)
+        oracle_proc = start_oracle_worker()
     if ws > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl")
