@@ -625,16 +625,20 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   mark(3);
   // The interface operator (z_G = K_GG y'_G) and the coarse residual and
   // solve depend only on y'_G: with tune_overlap they run concurrently, the
-  // interface operator on a second stream capped at 2 blocks per SM, the
+  // interface operator on a second stream capped at `cap` blocks per SM, the
   // coarse sweeps on one block of 256 (one column) or 512 threads per SM, so
   // that both fit on every SM at once (the coarse kernel is cooperative: its
-  // grid must be resident).
+  // grid must be resident). Registers decide the cap: a symmetric-GEMV block
+  // holds 288 x 72 and a 256-thread sweep block 256 x 128 of the SM's 65536,
+  // so one of the former fits beside the latter; a streamed-GEMV block
+  // (288 x 56) fits twice.
   const int ax = h->aux_sel;
   const bool overlap = h->tune_overlap && h->nG_tot && h->n_c && !h->coarse_dense && h->aux_stream[ax];
+  const int cap = h->use_sym ? 1 : 2;
   if (overlap) {
     if ((e = cudaEventRecord(h->ev_fork[ax], st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->aux_stream[ax], h->ev_fork[ax], 0)) != cudaSuccess) return e;
-    if ((e = local_op(h, false, W.yG, W.zG, nullptr, nrhs, h->aux_stream[ax], 2)) != cudaSuccess) return e;
+    if ((e = local_op(h, false, W.yG, W.zG, nullptr, nrhs, h->aux_stream[ax], cap)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(h->ev_join[ax], h->aux_stream[ax])) != cudaSuccess) return e;
   } else if (h->nG_tot) {
     if ((e = local_op(h, false, W.yG, W.zG, nullptr, nrhs, st)) != cudaSuccess) return e;
@@ -643,7 +647,7 @@ cudaError_t launch_apply(bddc_handle_s* h, const double* r, double* z, int nrhs,
   if (h->n_c) {
     // coarse residual r_c = sum R_ci^T Phi_G^T y'_G
     if ((e = launch_bgemv_tma(h->phi_prec, h->d_wi_PT, h->n_wi_PT, h->max_ld_PT, h->d_phit, W.yG, W.g,
-                              nullptr, nrhs, h->d_err, st, 12, overlap ? 2 : 0)) != cudaSuccess)
+                              nullptr, nrhs, h->d_err, st, 12, overlap ? cap : 0)) != cudaSuccess)
       return e;
     (nrhs == 1 ? k_coarse_gather<true> : k_coarse_gather<false>)<<<blocks_for(h->n_c * nrhs), kThreads, 0, st>>>(
         h->n_c, nrhs, h->d_cg_ptr, h->d_cg_idx, W.g, W.rc);
