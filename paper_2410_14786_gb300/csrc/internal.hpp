@@ -166,14 +166,18 @@ constexpr int kBlockMaxFront = 16384;    // largest front of the block form (sha
 constexpr int kLevelThreads = 256;
 constexpr int kLevelClasses = 6;
 constexpr int kLevelGroup[kLevelClasses] = {32, 16, 8, 4, 2, 1};
-// The class of a unit of len coefficients: the narrowest group that still
-// reads about four coefficients per lane.
+// The class of a unit of len coefficients: groups of 32, 16, 8, 4, 2 and 1
+// lanes from 512, 192, 80, 32 and 12 coefficients on, i.e. 12 to 16 of them
+// per lane at most (measured on the interior sweeps of the 2D workloads, in
+// float64 and float32: groups twice as wide took 1.2 to 1.5x as long, half
+// as wide 1.04 to 1.11x; more units per warp hide the load latency, and
+// every shuffle step of a group's sum costs the float64 pipe)
 inline int level_class(int len) {
-  if (len >= 128) return 0;
-  if (len >= 48) return 1;
-  if (len >= 20) return 2;
-  if (len >= 8) return 3;
-  if (len >= 3) return 4;
+  if (len >= 512) return 0;
+  if (len >= 192) return 1;
+  if (len >= 80) return 2;
+  if (len >= 32) return 3;
+  if (len >= 12) return 4;
   return 5;
 }
 // The per-level form of a gather layout (seq, seq_off): every phase's class
