@@ -509,7 +509,7 @@ def run_sparse_local(args, barrier, peak, peak_kind) -> dict:
     """The sparse local solver on the paper's own 2D workloads (sigma = 1,
     corner and edge constraints, one right-hand side), where a dense A_II^-1
     does not fit (80 MB to 48 GB per subdomain in float64): FP64 and the
-    mixed form (BF16 K_GG, float64 interior sweeps) to rtol 1e-8, with
+    mixed form (BF16 K_GG, float32 interior sweeps) to rtol 1e-8, with
     setup time, iterations, true residual, the apply's phases and the
     interior sweeps' bytes per solve against the HBM peak."""
     import torch
@@ -567,7 +567,11 @@ def run_sparse_local(args, barrier, peak, peak_kind) -> dict:
             # plus the compact vectors (operand, two work vectors, result)
             sweep_bytes = 2 * (inf["interior_op_bytes"] + 8 * 4 * inf["n_interior"])
             ach = sweep_bytes / (sweep_ms * 1e-3) / 1e9
-            fm["sweeps_roofline"] = {"bound": "hbm", "kernel": "k_coarse_sweeps on the interior forest (2 per apply)",
+            fm["sweeps_roofline"] = {"bound": "hbm",
+                                     "kernel": ("interior sweeps, 2 per apply: k_level_sweep per level"
+                                                + (", k_block_fwd/bwd from the tuned split height on"
+                                                   if prec == "fp64" else " (float32 coefficients)")),
+                                     "note": "the float64 sweeps are bound by the float64 pipe, not HBM",
                                      "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                      "peak_kind": peak_kind, "bytes_per_apply": sweep_bytes, "traffic": None}
             if prec == "fp64":
