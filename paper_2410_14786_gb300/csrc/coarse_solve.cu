@@ -1,5 +1,8 @@
 // Coarse solve u_c = A_c^-1 r_c on the GPU from the supernodal factorisation
-// of coarse_sparse.cpp (float64 throughout).
+// of coarse_sparse.cpp (float64), and the same sweeps for the sparse local
+// solver's interior solves t = A_II^-1 r over the forest of all subdomains'
+// factors (per-level and block forms below; the mixed forms sweep with
+// float32 coefficients).
 //
 // Vectors r' (forward right-hand side) and y (forward result) are kept in
 // elimination order, so the pivots of every supernode are contiguous.
