@@ -24,7 +24,9 @@
 // is kept for the interior sweeps on the device.
 // The interior rows of Phi_i and z_i follow from the first block row,
 // x_I = A_II^-1 (y_I - A_IG x_G), and are never stored (see the apply).
-// Coarse: A_c = sum_i R_ci^T A_ci R_ci, inverted explicitly (SPD).
+// Coarse: A_c = sum_i R_ci^T A_ci R_ci, factorised by the sparse Cholesky of
+// coarse_sparse.cpp (default), inverted explicitly (dense option), or kept
+// in CSR for the inexact solve by plain CG.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
