@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "internal.hpp"
@@ -582,10 +583,15 @@ __global__ void __launch_bounds__(NT, kGThreadsWide / NT) k_coarse_sweeps(Gather
 // coefficients and indices through the read-only path.
 // TC: the coefficients' type. double: float64 products and sums; float
 // (the mixed forms of the sparse local solver): float32 coefficients,
-// products and sums (operands rounded to float32; results stored in the
-// float64 vectors), which moves the products from the float64 pipe (a few
+// products and sums, which moves the products from the float64 pipe (a few
 // per SM and cycle on this GPU) to the float32 pipe and reads 8 bytes per
-// coefficient instead of 12.
+// coefficient instead of 12. The operands are float32 copies of r', y and r
+// (xa32, xb32), each value rounded once where it is written (rp32, y32; r
+// by k_round_f32 before the forward sweep), because a float64 -> float32
+// conversion also runs on the float64 pipe and, done per coefficient, kept
+// that pipe as busy as the products did. The results are the same as with
+// the rounding at each read. The float64 vectors are still written: the
+// receiving units' r'_U - s and the result u stay in float64.
 template <typename TC>
 struct LevelArgs {
   const CGUnit* units;       // the phase's descriptors
@@ -598,7 +604,17 @@ struct LevelArgs {
   double* u;                 // u by dof (backward)
   int n, fwd;
   int32_t cb[kLevelClasses + 1], bb[kLevelClasses + 1];
+  const float* xa32 = nullptr;   // TC = float: float32 copies of xa and xb
+  const float* xb32 = nullptr;
+  float* rp32 = nullptr;         // TC = float: float32 copies of rp and y, written with them
+  float* y32 = nullptr;
 };
+
+// f[i] = r[i] rounded to float32 (the forward sweep's operand r in the
+// float32 form of the per-level sweeps)
+__global__ void k_round_f32(const double* __restrict__ r, float* __restrict__ f, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) f[i] = (float)r[i];
+}
 
 template <typename TC, int G, int c>
 __device__ __forceinline__ void level_group(const LevelArgs<TC>& a, int b) {
@@ -609,7 +625,15 @@ __device__ __forceinline__ void level_group(const LevelArgs<TC>& a, int b) {
   if (valid) d = a.units[k];
   const TC* C = a.C + d.off;
   const int32_t* I = a.I + d.off;
+  constexpr bool kF32 = std::is_same<TC, float>::value;
   auto X = [&](int ix) { return ix < a.n ? a.xa[ix] : a.xb[ix - a.n]; };
+  // operand of a coefficient in the coefficients' type
+  auto XO = [&](int ix) -> TC {
+    if constexpr (kF32)
+      return ix < a.n ? a.xa32[ix] : a.xb32[ix - a.n];
+    else
+      return X(ix);
+  };
   TC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   for (int j = gl; j < d.len; j += 4 * G) {
     const bool b1 = j + G < d.len, b2 = j + 2 * G < d.len, b3 = j + 3 * G < d.len;
@@ -621,7 +645,7 @@ __device__ __forceinline__ void level_group(const LevelArgs<TC>& a, int b) {
     const int i1 = b1 ? __ldg(I + j + G) : i0;
     const int i2 = b2 ? __ldg(I + j + 2 * G) : i0;
     const int i3 = b3 ? __ldg(I + j + 3 * G) : i0;
-    const TC x0 = (TC)X(i0), x1 = (TC)X(i1), x2 = (TC)X(i2), x3 = (TC)X(i3);
+    const TC x0 = XO(i0), x1 = XO(i1), x2 = XO(i2), x3 = XO(i3);
     s0 = fma(c0, x0, s0);
     s1 = fma(c1, x1, s1);
     s2 = fma(c2, x2, s2);
@@ -634,10 +658,14 @@ __device__ __forceinline__ void level_group(const LevelArgs<TC>& a, int b) {
   if (!a.fwd) {
     a.rp[d.dst] = (double)s;
     a.u[d.aux] = (double)s;
+    if constexpr (kF32) a.rp32[d.dst] = (float)s;
   } else if (d.aux < 0) {
     a.y[d.dst] = (double)s;
+    if constexpr (kF32) a.y32[d.dst] = (float)s;
   } else {
-    a.rp[d.dst] = X(d.aux) - (double)s;
+    const double v = X(d.aux) - (double)s;
+    a.rp[d.dst] = v;
+    if constexpr (kF32) a.rp32[d.dst] = (float)v;
   }
 }
 
@@ -1012,6 +1040,9 @@ cudaError_t build_gather(bddc_handle_s* h, const CoarseFactor& cf, SweepSet& S, 
     std::vector<float> c32(g.C.begin(), g.C.end());
     std::vector<double>().swap(g.C);
     if ((e = up(h, &S.gC32, c32)) != cudaSuccess) return e;
+    // float32 copies of the operand vectors r', y and r, so that the
+    // per-coefficient operand loads need no float64 -> float32 conversion
+    if ((e = up(h, &S.x32, std::vector<float>(3 * (size_t)cf.n, 0.0f))) != cudaSuccess) return e;
   } else {
     if ((e = up(h, &S.gC, g.C)) != cudaSuccess) return e;
     std::vector<double>().swap(g.C);
@@ -1335,6 +1366,15 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
   }
   if (nrhs == 1 && S.use_level && !S.lv.empty()) {
     // per-level form: one launch per phase, forward levels then backward
+    // (the float32 form first rounds r into its copy: [r' | y | r] of x32)
+    float* rp32 = S.gC32 ? S.x32 : nullptr;
+    float* y32 = S.gC32 ? S.x32 + S.n : nullptr;
+    float* r32 = S.gC32 ? S.x32 + 2 * S.n : nullptr;
+    if (S.gC32 && S.n > 0) {
+      const int grid = (int)std::min<int64_t>((S.n + 255) / 256, 4 * 1024);
+      k_round_f32<<<grid, 256, 0, st>>>(r, r32, (int)S.n);
+      h->launches++;
+    }
     for (size_t ph = 0; ph < S.lv.size(); ++ph) {
       const SweepSet::LevelPhase& P = S.lv[ph];
       const int nblk = P.bb[kLevelClasses];
@@ -1343,6 +1383,10 @@ cudaError_t launch_sweeps(bddc_handle_s* h, const SweepSet& S, const double* r, 
       if (S.gC32) {
         LevelArgs<float> la{S.seq + P.u0, S.gC32, S.gI, fwd ? rp : y, fwd ? r : rp, rp, y, u, (int)S.n,
                             fwd ? 1 : 0, {}, {}};
+        la.xa32 = fwd ? rp32 : y32;
+        la.xb32 = fwd ? r32 : rp32;
+        la.rp32 = rp32;
+        la.y32 = y32;
         std::memcpy(la.cb, P.cb, sizeof(la.cb));
         std::memcpy(la.bb, P.bb, sizeof(la.bb));
         k_level_sweep<float><<<nblk, kLevelThreads, 0, st>>>(la);

@@ -108,6 +108,7 @@ struct SweepSet {
   int32_t* lvl4 = nullptr;
   double* gC = nullptr;
   float* gC32 = nullptr;        // the gather form's coefficients in float32 (per-level form only), else null
+  float* x32 = nullptr;         // with gC32: float32 copies of r', y and r (n each), the operands the sweeps read
   int32_t* gI = nullptr;
   CGUnit* gU[2] = {nullptr, nullptr};
   int32_t* gwo[2] = {nullptr, nullptr};   // [phases][warps + 1]
