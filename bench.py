@@ -571,7 +571,8 @@ def run_sparse_local(args, barrier, peak, peak_kind) -> dict:
                                      "kernel": ("interior sweeps, 2 per apply: k_level_sweep per level"
                                                 + (", k_block_fwd/bwd from the tuned split height on"
                                                    if prec == "fp64" else " (float32 coefficients)")),
-                                     "note": "the float64 sweeps are bound by the float64 pipe, not HBM",
+                                     "note": ("bound by the float64 pipe, not HBM" if prec == "fp64" else
+                                              "latency-bound: each operand load waits for its index load"),
                                      "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                                      "peak_kind": peak_kind, "bytes_per_apply": sweep_bytes, "traffic": None}
             if prec == "fp64":
